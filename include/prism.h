@@ -1,0 +1,214 @@
+/*
+ * prism.h -- C ABI of the GB300 PRISM / multislice STEM simulation library (libprism.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the two halves of the PRISM
+ * algorithm of Ophus, "A Fast Image Simulation Algorithm for Scanning Transmission
+ * Electron Microscopy" (2017), and conventional per-probe multislice beside it:
+ *
+ *   (a) the compact S-matrix: multislice (Eq. Multislice) of every plane wave of the
+ *       f-subsampled probe aperture (PRISM Algorithm section, plane-wave set), stored in
+ *       real space at half resolution per axis when the anti-aliasing aperture allows it;
+ *   (b) the probe scan: coefficients alpha_mn(r0), the d/f window of Eq. RegionBounds,
+ *       the beam sum of Eq. PRISMfinal, window FFT, |psi|^2 and annular detector bins
+ *       (Fig. 1d-f);
+ *   (c) plain multislice of each probe (Multislice section) as the baseline form.
+ *
+ * Conventions (all calls):
+ *   - Units: lengths in Angstrom, angles in mrad, voltage in kV, potentials in V*Angstrom.
+ *   - Arrays are C row-major.  "device" pointers are CUDA device addresses in the current
+ *     device's context (e.g. from PyTorch); "host" pointers are ordinary CPU memory
+ *     (pinned memory makes the host variants asynchronous).
+ *   - FFT convention: forward exp(-2 pi i k.x / N) unnormalised, frequencies q = k / cell
+ *     for the signed index k (0..N/2-1, -N/2..-1).
+ *   - Asynchrony: calls that take a plan enqueue work on the plan's CUDA stream and return;
+ *     results are valid after prism_sync() (or any later synchronisation of that stream).
+ *   - Status: every int-returning call returns PRISM_OK (0) or a negative PRISM_ERR_* code;
+ *     prism_last_error() then describes the failure (thread-local string).
+ *   - Determinism: the same inputs give bitwise-identical outputs (no order-dependent
+ *     atomics; fixed reduction trees).
+ *   - Memory: the caller owns every pointer it passes in; the plan owns the transmission
+ *     functions, the S-matrix, its wave scratch and small tables, allocated with
+ *     stream-ordered cudaMallocAsync and released by prism_plan_destroy().
+ */
+#ifndef PRISM_H
+#define PRISM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PRISM_OK               0
+#define PRISM_ERR_INVALID     -1  /* bad argument: NULL pointer, N % (2f) != 0, nbins <= 0, ... */
+#define PRISM_ERR_BUDGET      -2  /* the plan does not fit the HBM budget given at creation     */
+#define PRISM_ERR_CUDA        -3  /* a CUDA runtime call failed (message has the CUDA error)     */
+#define PRISM_ERR_DEVICE      -4  /* a kernel raised the device error flag                      */
+#define PRISM_ERR_UNSUPPORTED -5  /* valid but not implemented here (e.g. non power-of-two N)   */
+
+/* Simulation grid and PRISM build parameters.
+ *   nx, ny       wave / potential grid, powers of two in [16, 2048].
+ *   n_slices     H >= 1 (Eq. Multislice is applied H times, propagation after each slice).
+ *   cell_x/_y    orthorhombic cell side (Angstrom); pixel = cell / n.
+ *   dz           uniform slice thickness t (Angstrom) when slice_dz == NULL; may be 0.
+ *   slice_dz     optional host array [n_slices] of per-slice thickness (copied at plan creation;
+ *                the paper allows unequal slices, Fig. 1a text).
+ *   kv           accelerating voltage; lambda and sigma are relativistic (CODATA 2018).
+ *   f            interpolation factor (PRISM Algorithm section), >= 1.
+ *   downsample   1 (S stored at full resolution) or 2 (S stored on the inner half of Fourier
+ *                space, the x4 storage saving enabled by the anti-aliasing aperture).
+ *   aa_frac      anti-aliasing aperture |q| < aa_frac * q_nyquist, q_nyquist = min(nx/2cx, ny/2cy);
+ *                must be <= 0.5 when downsample == 2; 0 < aa_frac.
+ *   alpha_max_mrad  radius of the plane-wave set: sqrt(m^2+n^2) f lambda dq <= alpha_max
+ *                (PRISM Algorithm section).  Must lie inside the anti-aliasing aperture.
+ */
+typedef struct prism_grid {
+    int nx, ny, n_slices;
+    double cell_x, cell_y;
+    double dz;
+    const double *slice_dz;
+    double kv;
+    int f;
+    int downsample;
+    double aa_frac;
+    double alpha_max_mrad;
+} prism_grid;
+
+/* Probe: aperture semi-angle (A(q) = 1 where lambda|q| <= alpha), defocus C1 and spherical
+ * aberration C3 (Angstrom) in chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3.
+ * tilt_x/tilt_y (rad) must be 0 in this version (PRISM_ERR_UNSUPPORTED otherwise). */
+typedef struct prism_probe {
+    double alpha_mrad, c1, c3, tilt_x, tilt_y;
+} prism_probe;
+
+/* Scan: px * py probe positions (Angstrom), host arrays x0[py*px], y0[py*px], row-major [py][px].
+ * Positions may lie anywhere; windows wrap periodically (Eq. RegionBounds). px*py may be 0. */
+typedef struct prism_scan {
+    int px, py;
+    const double *x0;
+    const double *y0;
+} prism_scan;
+
+/* Annular detector: bin b = floor((1000 lambda |q| - start_mrad) / step_mrad), kept when
+ * 0 <= b < nbins; a pixel on an edge goes to the upper bin; q is the pixel-centre frequency.
+ * step_mrad > 0, nbins in [1, 4096]. */
+typedef struct prism_detector {
+    double start_mrad, step_mrad;
+    int nbins;
+} prism_detector;
+
+/* Read-only facts about a plan (filled by prism_plan_info). */
+typedef struct prism_info {
+    int n_beams;              /* B: plane waves in the S-matrix                        */
+    int nx_s, ny_s;           /* stored grid (nx/downsample, ny/downsample)             */
+    int nw_x, nw_y;           /* scan window in stored pixels (nx_s/f, ny_s/f)          */
+    int beam_batch;           /* beams propagated together (limited by the HBM budget)  */
+    double wavelength;        /* lambda, Angstrom                                      */
+    double sigma;             /* interaction constant, rad/(V*Angstrom)                */
+    size_t device_bytes;      /* device memory held by the plan                        */
+} prism_info;
+
+typedef struct prism_plan prism_plan;
+
+/* ---- plan lifetime ------------------------------------------------------------------ */
+
+/* Validate the grid, build the beam set, the FFT/propagator tables and allocate the plan's
+ * device memory on `cuda_stream` (a cudaStream_t; NULL = legacy default stream) of the
+ * current device.  hbm_budget_bytes = 0 means "no budget"; otherwise the plan's device
+ * memory (transmission H*nx*ny*8, S-matrix B*nx_s*ny_s*8, wave scratch beam_batch*nx*ny*8)
+ * must fit, with at least one beam in flight, else PRISM_ERR_BUDGET.
+ * Errors: INVALID (NULL, non-positive sizes, nx % (2f) with downsample 2, aa_frac > 0.5 with
+ * downsample 2, beams outside the AA aperture), UNSUPPORTED (n not a power of two in
+ * [16, 2048]; window wider than 128 pixels), BUDGET, CUDA.  *out is NULL on failure. */
+int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes, void *cuda_stream,
+                      prism_plan **out);
+
+/* Release all device memory of the plan (stream-ordered) and the plan itself.  NULL is a no-op. */
+void prism_plan_destroy(prism_plan *plan);
+
+/* Wait for the plan's stream; returns DEVICE if a kernel raised the error flag, CUDA on a
+ * CUDA error, else OK. */
+int prism_sync(prism_plan *plan);
+
+/* Thread-local description of the last failure of a call on this thread ("" if none). */
+const char *prism_last_error(void);
+
+/* ---- hot path --------------------------------------------------------------------- */
+
+/* S-matrix build (PRISM Algorithm section, Fig. 1c; Eq. Multislice per beam and slice).
+ * V_dev: device float32 [n_slices][ny][nx] projected potentials V_p (V*Angstrom), read only,
+ * must stay valid until the call's work has run on the stream.  Computes t_p = exp(i sigma V_p)
+ * and propagates every beam exp(2 pi i q_mn . r) through all slices.  Result stays in the plan. */
+int prism_build_smatrix(prism_plan *plan, const float *V_dev);
+
+/* Same as prism_build_smatrix with V in host memory (copied to a plan-owned device buffer
+ * on the plan's stream; the host buffer may be reused once the call has run). */
+int prism_build_smatrix_host(prism_plan *plan, const float *V_host);
+
+/* Probe scan (Eq. RegionBounds, Eq. PRISMfinal, Fig. 1d-f) over the plan's S-matrix.
+ * out_dev: device float32 [py][px][nbins], intensities in units of the incident probe
+ * intensity.  Requires a completed prism_build_smatrix on this plan (else INVALID).
+ * The probe's alpha may differ from alpha_max: beams outside it get A(q) = 0. */
+int prism_scan_run(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
+                   const prism_detector *det, float *out_dev);
+
+/* Same as prism_scan_run with the result copied to host memory out_host [py][px][nbins]
+ * (asynchronous for pinned memory: read it after prism_sync). */
+int prism_scan_run_host(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
+                        const prism_detector *det, float *out_host);
+
+/* Conventional multislice STEM (Multislice section, Eq. Multislice) of every probe: the probe
+ * A(q) exp(-i chi) exp(-2 pi i q.r0) on the full grid, H slices, far-field |Psi|^2 divided by
+ * sum |Psi0|^2, annular bins.  Same grid rules as a plan (f, downsample and alpha_max are
+ * ignored).  V_dev as above, out_dev float32 [py][px][nbins].  Uses its own stream-ordered
+ * scratch on `cuda_stream`, sized to at most max(1, scratch_bytes / (8 nx ny)) probes in flight
+ * (scratch_bytes = 0: 1 GiB).  Asynchronous; synchronise the stream before reading out_dev. */
+int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
+                        const prism_scan *scan, const prism_detector *det, float *out_dev,
+                        void *cuda_stream, size_t scratch_bytes);
+
+/* ---- introspection (tests, tools) ----------------------------------------------- */
+
+int prism_plan_info(const prism_plan *plan, prism_info *out);
+
+/* Bytes of the stored S-matrix (B * nx_s * ny_s * 8). */
+int prism_plan_smatrix_bytes(const prism_plan *plan, size_t *out);
+
+/* Beam indices (m, n) of the plane-wave set, q_mn = (m f / cell_x, n f / cell_y), in the
+ * plan's order (n ascending, then m ascending).  capacity >= n_beams else INVALID. */
+int prism_plan_beams(const prism_plan *plan, int *m, int *n, int capacity);
+
+/* Device pointers owned by the plan (valid until destroy): the S-matrix complex64
+ * [B][ny_s][nx_s] (interleaved re, im) and the transmission functions complex64 [H][ny][nx]. */
+int prism_plan_smatrix(const prism_plan *plan, const void **dev_ptr);
+int prism_plan_transmission(const prism_plan *plan, const void **dev_ptr);
+
+/* Relativistic wavelength (Angstrom) and interaction constant (rad/(V*Angstrom)), CODATA 2018. */
+double prism_wavelength(double kv);
+double prism_interaction_constant(double kv);
+
+/* ---- per-kernel timing ------------------------------------------------------------ */
+
+/* Kernel classes timed by the plan when profiling is on. */
+#define PRISM_K_TRANSMIT   0  /* t_p = exp(i sigma V_p)                                    */
+#define PRISM_K_ROW_PLANE  1  /* first slice: plane wave x t_0, row FFT                     */
+#define PRISM_K_ROW        2  /* row IFFT, x t_p, row FFT                                   */
+#define PRISM_K_COL        3  /* column FFT, x propagator (AA-masked), column IFFT          */
+#define PRISM_K_ROW_OUT    4  /* last row IFFT, store S                                     */
+#define PRISM_K_SCAN       5  /* coefficients + window gather + beam sum + window FFT + bins */
+#define PRISM_K_COUNT      6
+
+/* profiling on: every launch of the plan is bracketed by CUDA events on the plan's stream. */
+int prism_plan_set_profiling(prism_plan *plan, int enable);
+/* Launch count and summed event time (ms) of one kernel class since profiling was enabled
+ * (synchronises the plan's stream).  Also counts launches while profiling is off. */
+int prism_plan_kernel_stats(prism_plan *plan, int kind, long *launches, double *total_ms);
+/* Total kernel launches issued by the plan since creation (or the last reset). */
+long prism_plan_launches(const prism_plan *plan);
+int prism_plan_reset_stats(prism_plan *plan);
+const char *prism_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRISM_H */

@@ -1,0 +1,947 @@
+// engine.cpp -- host side of libprism: the C ABI declared in include/prism.h.
+//
+// Plans, validation, FP64 tables (beam set, propagators, anti-aliasing bounds, FFT twiddles,
+// detector bin maps), stream-ordered device memory and kernel launch sequencing.  Compiled with
+// -ffp-contract=off: every FP64 decision made here (beam membership, anti-aliasing mask, aperture,
+// detector bin of a pixel) is evaluated with the same operations, in the same order, as its
+// definition, so the integer outcome does not depend on the compiler fusing multiply-adds.
+#include "prism.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "params.h"
+
+namespace prism {
+size_t scan_smem_bytes(int nw, int n_beams);
+}
+
+using namespace prism;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char *prism_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ physics (CODATA 2018)
+static const double H_PLANCK = 6.62607015e-34;
+static const double M_ELECTRON = 9.1093837015e-31;
+static const double Q_ELECTRON = 1.602176634e-19;
+static const double C_LIGHT = 299792458.0;
+static const double BEAM_SLACK = 1e-12;
+static const double PI = 3.141592653589793;
+
+// lambda = h / sqrt(2 m0 e V (1 + e V / (2 m0 c^2))), Angstrom
+extern "C" double prism_wavelength(double kv) {
+    const double ev = Q_ELECTRON * (kv * 1e3);
+    const double p2 = 2.0 * M_ELECTRON * ev * (1.0 + ev / (2.0 * M_ELECTRON * C_LIGHT * C_LIGHT));
+    return H_PLANCK / std::sqrt(p2) * 1e10;
+}
+
+// sigma = 2 pi m e lambda / h^2 with the relativistic mass m, rad/(V*Angstrom)
+extern "C" double prism_interaction_constant(double kv) {
+    const double ev = Q_ELECTRON * (kv * 1e3);
+    const double m = M_ELECTRON + ev / (C_LIGHT * C_LIGHT);
+    const double lam_m = prism_wavelength(kv) * 1e-10;
+    return 2.0 * PI * m * Q_ELECTRON * lam_m / (H_PLANCK * H_PLANCK) * 1e-10;
+}
+
+static inline int signed_index(int k, int n) { return k < n / 2 ? k : k - n; }
+static inline bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// W_N^m = exp(-2 pi i m / N)
+static float2 wN(long long m, int N) {
+    m %= N;
+    if (m < 0) m += N;
+    const double a = 2.0 * PI * (double)m / (double)N;
+    return make_float2((float)std::cos(a), (float)-std::sin(a));
+}
+
+// exp(-2 pi i c) for a phase in cycles, reduced before the trigonometric call
+static float2 phase_cycles(double c) {
+    c -= std::floor(c);
+    const double a = 2.0 * PI * c;
+    return make_float2((float)std::cos(a), (float)-std::sin(a));
+}
+
+static Tw64 make_tw64() {
+    Tw64 t;
+    for (int j = 0; j < 64; ++j) t.w[j] = wN(j, 64);
+    return t;
+}
+
+// inter-stage twiddles of a two-level FFT with split (A, B): table[k1 * B + n2] = W_N^{n2 k1}
+static std::vector<float2> stage_table(int N, int A, int B) {
+    std::vector<float2> t((size_t)A * B);
+    for (int k1 = 0; k1 < A; ++k1)
+        for (int n2 = 0; n2 < B; ++n2) t[(size_t)k1 * B + n2] = wN((long long)n2 * k1, N);
+    return t;
+}
+
+// A caller's device pointer must be device (or managed) memory of the current device; V is read
+// with 16-byte vector loads, so it must also be 16-byte aligned.
+static int check_dev_ptr(const void *p, size_t align, const char *what) {
+    if (!p) return fail(PRISM_ERR_INVALID, std::string(what) + " is NULL");
+    if (((uintptr_t)p) % align) return fail(PRISM_ERR_INVALID, std::string(what) + " is not " + std::to_string(align) + "-byte aligned");
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PRISM_ERR_INVALID, std::string(what) + " is not a CUDA pointer");
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (!(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) || at.device != dev)
+        return fail(PRISM_ERR_INVALID, std::string(what) + " is not device memory of the current device");
+    return PRISM_OK;
+}
+
+// ------------------------------------------------------------------ device memory helpers
+struct DevArena {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    int alloc(void **p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMallocAsync(p, n, stream);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return fail(PRISM_ERR_CUDA, std::string("cudaMallocAsync(") + std::to_string(n) + "): " + cudaGetErrorString(e));
+        }
+        ptrs.push_back(*p);
+        bytes += n;
+        return PRISM_OK;
+    }
+    template <class T>
+    int upload(T **p, const std::vector<T> &h) {
+        int rc = alloc((void **)p, h.size() * sizeof(T));
+        if (rc) return rc;
+        if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, stream));
+        return PRISM_OK;
+    }
+    void release() {
+        for (void *p : ptrs) cudaFreeAsync(p, stream);
+        ptrs.clear();
+        bytes = 0;
+    }
+    void forget(void *p, size_t n) {
+        auto it = std::find(ptrs.begin(), ptrs.end(), p);
+        if (it != ptrs.end()) {
+            cudaFreeAsync(p, stream);
+            ptrs.erase(it);
+            bytes -= n;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ grid validation and tables
+struct GridTables {
+    int nx, ny, H;
+    double lam, sigma;
+    std::vector<double> dz;           // per slice
+    std::vector<int> slice_prop;      // slice -> propagator table index
+    std::vector<double> prop_dz;      // distinct thicknesses
+    std::vector<float2> prop_x, prop_y;
+    std::vector<int> aa_kmax;
+    double q_aa;
+    std::vector<float2> twr_f, twr_i, twc_f, twc_i;
+};
+
+static int check_grid_common(const prism_grid *g) {
+    if (!g) return fail(PRISM_ERR_INVALID, "grid is NULL");
+    if (g->nx <= 0 || g->ny <= 0 || g->n_slices <= 0) return fail(PRISM_ERR_INVALID, "nx, ny and n_slices must be positive");
+    if (!(g->cell_x > 0) || !(g->cell_y > 0) || !std::isfinite(g->cell_x) || !std::isfinite(g->cell_y))
+        return fail(PRISM_ERR_INVALID, "cell sizes must be positive and finite");
+    if (!(g->kv > 0) || !std::isfinite(g->kv)) return fail(PRISM_ERR_INVALID, "kv must be positive");
+    if (!(g->aa_frac > 0) || g->aa_frac > 1.0) return fail(PRISM_ERR_INVALID, "aa_frac must be in (0, 1]");
+    if (!g->slice_dz && (!(g->dz >= 0) || !std::isfinite(g->dz))) return fail(PRISM_ERR_INVALID, "dz must be >= 0");
+    if (g->slice_dz)
+        for (int p = 0; p < g->n_slices; ++p)
+            if (!(g->slice_dz[p] >= 0) || !std::isfinite(g->slice_dz[p])) return fail(PRISM_ERR_INVALID, "slice_dz must be >= 0");
+    if (!pow2(g->nx) || !pow2(g->ny) || g->nx < 16 || g->ny < 16 || g->nx > 2048 || g->ny > 2048)
+        return fail(PRISM_ERR_UNSUPPORTED, "nx and ny must be powers of two in [16, 2048]");
+    return PRISM_OK;
+}
+
+static int build_grid_tables(const prism_grid *g, GridTables &T) {
+    T.nx = g->nx;
+    T.ny = g->ny;
+    T.H = g->n_slices;
+    T.lam = prism_wavelength(g->kv);
+    T.sigma = prism_interaction_constant(g->kv);
+    T.dz.resize(T.H);
+    for (int p = 0; p < T.H; ++p) T.dz[p] = g->slice_dz ? g->slice_dz[p] : g->dz;
+    T.slice_prop.resize(T.H);
+    for (int p = 0; p < T.H; ++p) {
+        int idx = -1;
+        for (size_t i = 0; i < T.prop_dz.size(); ++i)
+            if (T.prop_dz[i] == T.dz[p]) idx = (int)i;
+        if (idx < 0) {
+            idx = (int)T.prop_dz.size();
+            T.prop_dz.push_back(T.dz[p]);
+        }
+        T.slice_prop[p] = idx;
+    }
+    // Fresnel propagator exp(-i pi lambda t q^2) factored per axis; 1/(nx ny) of the inverse FFT
+    // folded into the y factor
+    const double inv = 1.0 / ((double)T.nx * (double)T.ny);
+    for (double dzv : T.prop_dz) {
+        for (int k = 0; k < T.nx; ++k) {
+            const double q = (double)signed_index(k, T.nx) / g->cell_x;
+            T.prop_x.push_back(phase_cycles(0.5 * T.lam * dzv * q * q));
+        }
+        for (int k = 0; k < T.ny; ++k) {
+            const double q = (double)signed_index(k, T.ny) / g->cell_y;
+            float2 w = phase_cycles(0.5 * T.lam * dzv * q * q);
+            T.prop_y.push_back(make_float2((float)(w.x * inv), (float)(w.y * inv)));
+        }
+    }
+    // anti-aliasing aperture |q| < aa_frac * q_nyquist, as a per-row bound on |kx|
+    const double q_nyq = std::min(0.5 * T.nx / g->cell_x, 0.5 * T.ny / g->cell_y);
+    T.q_aa = g->aa_frac * q_nyq;
+    const double qaa2 = T.q_aa * T.q_aa;
+    T.aa_kmax.assign(T.ny, -1);
+    for (int ky = 0; ky < T.ny; ++ky) {
+        const double qy = (double)signed_index(ky, T.ny) / g->cell_y;
+        int kmax = -1;
+        for (int kx = 0; kx < T.nx; ++kx) {
+            const int ks = signed_index(kx, T.nx);
+            const double qx = (double)ks / g->cell_x;
+            const bool in = qx * qx + qy * qy < qaa2;
+            if (in) kmax = std::max(kmax, std::abs(ks));
+        }
+        // the mask must be the symmetric interval |kx| <= kmax
+        for (int kx = 0; kx < T.nx; ++kx) {
+            const int ks = signed_index(kx, T.nx);
+            const double qx = (double)ks / g->cell_x;
+            const bool in = qx * qx + qy * qy < qaa2;
+            if (in != (std::abs(ks) <= kmax)) return fail(PRISM_ERR_INVALID, "anti-aliasing mask is not a symmetric interval");
+        }
+        T.aa_kmax[ky] = kmax;
+    }
+    int a1, a2;
+    fft_split(T.nx, &a1, &a2);
+    T.twr_f = stage_table(T.nx, a1, a2);
+    T.twr_i = stage_table(T.nx, a2, a1);
+    fft_split(T.ny, &a1, &a2);
+    T.twc_f = stage_table(T.ny, a1, a2);
+    T.twc_i = stage_table(T.ny, a2, a1);
+    return PRISM_OK;
+}
+
+// CSR of pixels grouped by detector bin: bin = floor((1000 lambda |q| - start) / step), q =
+// (k * mult) / cell, pixel index ky * nx + kx in FFT order.
+static void detector_csr(int nx, int ny, double cell_x, double cell_y, int mult, double lam,
+                         const prism_detector *det, std::vector<int> &off, std::vector<int> &idx) {
+    std::vector<int> bin((size_t)nx * ny);
+    off.assign(det->nbins + 1, 0);
+    for (int ky = 0; ky < ny; ++ky) {
+        const double qy = ((double)signed_index(ky, ny) * mult) / cell_y;
+        for (int kx = 0; kx < nx; ++kx) {
+            const double qx = ((double)signed_index(kx, nx) * mult) / cell_x;
+            const double theta = 1000.0 * lam * std::sqrt(qx * qx + qy * qy);
+            const double bf = std::floor((theta - det->start_mrad) / det->step_mrad);
+            int b = -1;
+            if (bf >= 0 && bf < det->nbins) b = (int)bf;
+            bin[(size_t)ky * nx + kx] = b;
+            if (b >= 0) off[b + 1]++;
+        }
+    }
+    for (int b = 0; b < det->nbins; ++b) off[b + 1] += off[b];
+    idx.assign(off[det->nbins], 0);
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (size_t i = 0; i < bin.size(); ++i)
+        if (bin[i] >= 0) idx[fill[bin[i]]++] = (int)i;
+}
+
+static int check_det(const prism_detector *det) {
+    if (!det) return fail(PRISM_ERR_INVALID, "detector is NULL");
+    if (det->nbins < 1 || det->nbins > 4096) return fail(PRISM_ERR_INVALID, "nbins must be in [1, 4096]");
+    if (!(det->step_mrad > 0) || !std::isfinite(det->step_mrad) || !std::isfinite(det->start_mrad))
+        return fail(PRISM_ERR_INVALID, "detector step must be positive and finite");
+    return PRISM_OK;
+}
+
+static int check_probe(const prism_probe *pr) {
+    if (!pr) return fail(PRISM_ERR_INVALID, "probe is NULL");
+    if (!(pr->alpha_mrad >= 0) || !std::isfinite(pr->alpha_mrad) || !std::isfinite(pr->c1) || !std::isfinite(pr->c3))
+        return fail(PRISM_ERR_INVALID, "probe parameters must be finite, alpha >= 0");
+    if (pr->tilt_x != 0.0 || pr->tilt_y != 0.0) return fail(PRISM_ERR_UNSUPPORTED, "probe tilt is not supported");
+    return PRISM_OK;
+}
+
+static int check_scan(const prism_scan *sc, double lim_x, double lim_y) {
+    if (!sc) return fail(PRISM_ERR_INVALID, "scan is NULL");
+    if (sc->px < 0 || sc->py < 0) return fail(PRISM_ERR_INVALID, "scan sizes must be >= 0");
+    const long long P = (long long)sc->px * sc->py;
+    if (P > (1LL << 30)) return fail(PRISM_ERR_INVALID, "too many probe positions");
+    if (P > 0 && (!sc->x0 || !sc->y0)) return fail(PRISM_ERR_INVALID, "scan positions are NULL");
+    for (long long i = 0; i < P; ++i)
+        if (!std::isfinite(sc->x0[i]) || !std::isfinite(sc->y0[i]) || std::fabs(sc->x0[i]) > lim_x || std::fabs(sc->y0[i]) > lim_y)
+            return fail(PRISM_ERR_INVALID, "probe position not finite or beyond 2^28 pixels");
+    return PRISM_OK;
+}
+
+// aperture A(q): lambda |q| <= alpha (inclusive, 1e-12 relative slack)
+static bool inside_aperture(double qx, double qy, double lam, double alpha_rad) {
+    const double ax = lam * qx;
+    const double ay = lam * qy;
+    return ax * ax + ay * ay <= alpha_rad * alpha_rad * (1.0 + BEAM_SLACK);
+}
+
+// chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3, returned in cycles (chi / 2 pi)
+static double chi_cycles(double q2, double lam, double c1, double c3) {
+    const double chi = PI * lam * q2 * c1 + 0.5 * PI * lam * lam * lam * q2 * q2 * c3;
+    return chi / (2.0 * PI);
+}
+
+// ------------------------------------------------------------------ plan
+struct PendingEv {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct prism_plan {
+    prism_grid g;
+    GridTables T;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nxs = 0, nys = 0, nw = 0, nbeams = 0, batch = 0;
+    std::vector<int> bm, bn;
+    bool built = false;
+    size_t budget = 0;
+    DevArena arena;
+    // device tables / buffers
+    float2 *t = nullptr, *wave = nullptr, *S = nullptr;
+    float2 *prop_x = nullptr, *prop_y = nullptr;
+    int *aa_kmax = nullptr;
+    float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr;
+    int *beam_mn = nullptr;
+    double *beam_q = nullptr;  // qx[B] then qy[B]
+    // grown on demand
+    double *pos = nullptr;
+    size_t pos_cap = 0;
+    float2 *base = nullptr;
+    int *bin_buf = nullptr;
+    size_t bin_cap = 0;
+    float *out_stage = nullptr;
+    size_t out_cap = 0;
+    float *v_stage = nullptr;
+    size_t v_cap = 0;
+    Tw64 tw64;
+    // cached detector map
+    double det_key[2] = {0, 0};
+    int det_nbins = -1;
+    // statistics
+    long launches = 0;
+    bool profiling = false;
+    std::vector<PendingEv> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double kms[PRISM_K_COUNT] = {0};
+    long kl[PRISM_K_COUNT] = {0};
+};
+
+template <class F>
+static int plan_launch(prism_plan *P, int kind, F &&fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (P->profiling) {
+        for (cudaEvent_t *e : {&a, &b}) {
+            if (!P->ev_pool.empty()) {
+                *e = P->ev_pool.back();
+                P->ev_pool.pop_back();
+            } else {
+                CUDA_TRY(cudaEventCreate(e));
+            }
+        }
+        CUDA_TRY(cudaEventRecord(a, P->stream));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string("kernel launch (") + prism_kernel_name(kind) + "): " + cudaGetErrorString(e));
+    if (P->profiling) {
+        CUDA_TRY(cudaEventRecord(b, P->stream));
+        P->pending.push_back({kind, a, b});
+    }
+    P->kl[kind]++;
+    P->launches++;
+    return PRISM_OK;
+}
+
+static int grow(DevArena &A, void **p, size_t *cap, size_t need) {
+    if (need <= *cap && *p) return PRISM_OK;
+    if (*p) A.forget(*p, *cap);
+    *p = nullptr;
+    *cap = 0;
+    int rc = A.alloc(p, need);
+    if (rc) return rc;
+    *cap = need;
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes, void *cuda_stream, prism_plan **out) {
+    if (!out) return fail(PRISM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = check_grid_common(grid);
+    if (rc) return rc;
+    const prism_grid &g = *grid;
+    if (g.f < 1) return fail(PRISM_ERR_INVALID, "f must be >= 1");
+    if (g.downsample != 1 && g.downsample != 2) return fail(PRISM_ERR_INVALID, "downsample must be 1 or 2");
+    if (g.downsample == 2 && g.aa_frac > 0.5) return fail(PRISM_ERR_INVALID, "downsample 2 needs aa_frac <= 0.5");
+    if (!(g.alpha_max_mrad > 0) || !std::isfinite(g.alpha_max_mrad)) return fail(PRISM_ERR_INVALID, "alpha_max_mrad must be positive");
+    if ((g.nx % (g.downsample * g.f)) || (g.ny % (g.downsample * g.f)))
+        return fail(PRISM_ERR_INVALID, "nx and ny must be divisible by downsample * f");
+    const int nxs = g.nx / g.downsample, nys = g.ny / g.downsample;
+    const int nwx = nxs / g.f, nwy = nys / g.f;
+    if (nwx != nwy || !scan_supported(nwx))
+        return fail(PRISM_ERR_UNSUPPORTED, "scan window must be square with 8, 16, 32, 64 or 128 pixels");
+
+    int device = 0;
+    CUDA_TRY(cudaGetDevice(&device));
+    prism_plan *P = new prism_plan();
+    P->device = device;
+    P->g = g;
+    P->g.slice_dz = nullptr;
+    P->stream = (cudaStream_t)cuda_stream;
+    P->arena.stream = P->stream;
+    P->budget = hbm_budget_bytes;
+    P->nxs = nxs;
+    P->nys = nys;
+    P->nw = nwx;
+    rc = build_grid_tables(&g, P->T);
+    if (rc) {
+        delete P;
+        return rc;
+    }
+    // plane-wave set (PRISM Algorithm section): q_mn = (m f / cx, n f / cy), lambda |q| <= alpha_max
+    const double lam = P->T.lam;
+    const double alpha = g.alpha_max_mrad * 1e-3;
+    const int mmax = (int)std::floor(alpha / (lam * g.f / g.cell_x)) + 1;
+    const int nmax = (int)std::floor(alpha / (lam * g.f / g.cell_y)) + 1;
+    std::vector<double> bq;
+    for (int n = -nmax; n <= nmax; ++n)
+        for (int m = -mmax; m <= mmax; ++m) {
+            const double qx = (double)(m * g.f) / g.cell_x;
+            const double qy = (double)(n * g.f) / g.cell_y;
+            if (inside_aperture(qx, qy, lam, alpha)) {
+                if (!(qx * qx + qy * qy < P->T.q_aa * P->T.q_aa)) {
+                    delete P;
+                    return fail(PRISM_ERR_INVALID, "beam outside the anti-aliasing aperture: alpha_max too large for the grid");
+                }
+                P->bm.push_back(m);
+                P->bn.push_back(n);
+            }
+        }
+    P->nbeams = (int)P->bm.size();
+    if (P->nbeams == 0) {
+        delete P;
+        return fail(PRISM_ERR_INVALID, "empty beam set");
+    }
+    if (scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
+        delete P;
+        return fail(PRISM_ERR_UNSUPPORTED, "too many beams for the scan kernel's shared memory");
+    }
+    std::vector<int> mn(2 * P->nbeams);
+    std::vector<double> q(2 * P->nbeams);
+    for (int b = 0; b < P->nbeams; ++b) {
+        mn[2 * b] = P->bm[b];
+        mn[2 * b + 1] = P->bn[b];
+        q[b] = (double)(P->bm[b] * g.f) / g.cell_x;
+        q[P->nbeams + b] = (double)(P->bn[b] * g.f) / g.cell_y;
+    }
+    // memory plan
+    const size_t px = (size_t)g.nx * g.ny;
+    const size_t t_bytes = (size_t)g.n_slices * px * 8;
+    const size_t s_bytes = (size_t)P->nbeams * nxs * nys * 8;
+    const size_t w_bytes = px * 8;
+    const size_t fixed = t_bytes + s_bytes + (1 << 20);
+    int batch = P->nbeams;
+    if (hbm_budget_bytes) {
+        if (fixed + w_bytes > hbm_budget_bytes) {
+            delete P;
+            return fail(PRISM_ERR_BUDGET, "plan needs " + std::to_string(fixed + w_bytes) + " bytes, budget " + std::to_string(hbm_budget_bytes));
+        }
+        batch = (int)std::min<size_t>(P->nbeams, (hbm_budget_bytes - fixed) / w_bytes);
+    }
+    P->batch = batch;
+    P->tw64 = make_tw64();
+    std::vector<float2> tww_f;
+    {
+        int a1, a2;
+        fft_split(P->nw, &a1, &a2);
+        tww_f = stage_table(P->nw, a1, a2);
+    }
+    DevArena &A = P->arena;
+    auto bail = [&](int code) {
+        A.release();
+        cudaStreamSynchronize(P->stream);
+        delete P;
+        return code;
+    };
+    if ((rc = A.alloc((void **)&P->t, t_bytes))) return bail(rc);
+    if ((rc = A.alloc((void **)&P->S, s_bytes))) return bail(rc);
+    if ((rc = A.alloc((void **)&P->wave, (size_t)batch * w_bytes))) return bail(rc);
+    if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
+    if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
+    if ((rc = A.upload(&P->aa_kmax, P->T.aa_kmax))) return bail(rc);
+    if ((rc = A.upload(&P->twr_f, P->T.twr_f))) return bail(rc);
+    if ((rc = A.upload(&P->twr_i, P->T.twr_i))) return bail(rc);
+    if ((rc = A.upload(&P->twc_f, P->T.twc_f))) return bail(rc);
+    if ((rc = A.upload(&P->twc_i, P->T.twc_i))) return bail(rc);
+    if ((rc = A.upload(&P->tww_f, tww_f))) return bail(rc);
+    if ((rc = A.upload(&P->beam_mn, mn))) return bail(rc);
+    if ((rc = A.upload(&P->beam_q, q))) return bail(rc);
+    if ((rc = A.alloc((void **)&P->base, (size_t)P->nbeams * sizeof(float2)))) return bail(rc);
+    // the uploads above read host vectors that die with this scope
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) {
+        fail(PRISM_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+        return bail(PRISM_ERR_CUDA);
+    }
+    *out = P;
+    return PRISM_OK;
+}
+
+extern "C" void prism_plan_destroy(prism_plan *P) {
+    if (!P) return;
+    cudaStreamSynchronize(P->stream);
+    for (auto &pe : P->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (auto e : P->ev_pool) cudaEventDestroy(e);
+    P->arena.release();
+    cudaStreamSynchronize(P->stream);
+    delete P;
+}
+
+extern "C" int prism_sync(prism_plan *P) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    CUDA_TRY(cudaGetLastError());
+    return PRISM_OK;
+}
+
+// ------------------------------------------------------------------ S-matrix build
+static RowArgs row_args(prism_plan *P) {
+    RowArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.wave = P->wave;
+    a.tw_fwd = P->twr_f;
+    a.tw_inv = P->twr_i;
+    a.s_out = P->S;
+    a.beam_mn = P->beam_mn;
+    a.ny = P->g.ny;
+    a.f = P->g.f;
+    a.downsample = P->g.downsample;
+    a.tw = P->tw64;
+    return a;
+}
+
+static ColArgs col_args(const GridTables &T, float2 *wave, const float2 *prop_x, const float2 *prop_y,
+                        const int *aa_kmax, const float2 *tf, const float2 *ti, const Tw64 &tw) {
+    ColArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.wave = wave;
+    a.prop_x = prop_x;
+    a.prop_y = prop_y;
+    a.aa_kmax = aa_kmax;
+    a.tw_fwd = tf;
+    a.tw_inv = ti;
+    a.nx = T.nx;
+    a.tw = tw;
+    (void)T;
+    return a;
+}
+
+extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(V_dev, 16, "V_dev"))) return rc;
+    const prism_grid &g = P->g;
+    const size_t px = (size_t)g.nx * g.ny;
+    // transmission functions t_p = exp(i sigma V_p) for all slices
+    const double sigma_cycles = P->T.sigma / (2.0 * PI);
+    rc = plan_launch(P, PRISM_K_TRANSMIT, [&] { return launch_transmission(V_dev, P->t, (size_t)g.n_slices * px, sigma_cycles, P->stream); });
+    if (rc) return rc;
+    for (int b0 = 0; b0 < P->nbeams; b0 += P->batch) {
+        const int nb = std::min(P->batch, P->nbeams - b0);
+        for (int p = 0; p < g.n_slices; ++p) {
+            RowArgs ra = row_args(P);
+            ra.trans = P->t + (size_t)p * px;
+            ra.n_rows = nb * g.ny;
+            ra.beam0 = b0;
+            rc = plan_launch(P, p == 0 ? PRISM_K_ROW_PLANE : PRISM_K_ROW,
+                             [&] { return launch_row(g.nx, p == 0 ? ROW_PLANE : ROW_STD, ra, P->stream); });
+            if (rc) return rc;
+            const int pi = P->T.slice_prop[p];
+            ColArgs ca = col_args(P->T, P->wave, P->prop_x + (size_t)pi * g.nx, P->prop_y + (size_t)pi * g.ny,
+                                  P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
+            ca.batch = nb;
+            rc = plan_launch(P, PRISM_K_COL, [&] { return launch_col(g.ny, COL_STD, ca, P->stream); });
+            if (rc) return rc;
+        }
+        RowArgs ro = row_args(P);
+        ro.n_rows = nb * (g.downsample == 2 ? g.ny / 2 : g.ny);
+        ro.beam0 = b0;
+        rc = plan_launch(P, PRISM_K_ROW_OUT, [&] { return launch_row(g.nx, ROW_OUT, ro, P->stream); });
+        if (rc) return rc;
+    }
+    P->built = true;
+    return PRISM_OK;
+}
+
+extern "C" int prism_build_smatrix_host(prism_plan *P, const float *V_host) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    if (!V_host) return fail(PRISM_ERR_INVALID, "V_host is NULL");
+    const size_t bytes = (size_t)P->g.n_slices * P->g.nx * P->g.ny * sizeof(float);
+    int rc = grow(P->arena, (void **)&P->v_stage, &P->v_cap, bytes);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(P->v_stage, V_host, bytes, cudaMemcpyHostToDevice, P->stream));
+    return prism_build_smatrix(P, P->v_stage);
+}
+
+// ------------------------------------------------------------------ scan
+static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_scan *sc, const prism_detector *det,
+                        ScanArgs &a) {
+    int rc;
+    if ((rc = check_probe(probe))) return rc;
+    if ((rc = check_det(det))) return rc;
+    const double pxs = P->g.cell_x / P->nxs, pys = P->g.cell_y / P->nys;
+    if ((rc = check_scan(sc, pxs * (double)(1 << 28), pys * (double)(1 << 28)))) return rc;
+    if (!P->built) return fail(PRISM_ERR_INVALID, "S-matrix not built");
+    const int B = P->nbeams;
+    const double lam = P->T.lam;
+    // A(q_b) exp(-i chi(q_b)) and sum_b A_b
+    std::vector<float2> base(B);
+    double count = 0;
+    for (int b = 0; b < B; ++b) {
+        const double qx = (double)(P->bm[b] * P->g.f) / P->g.cell_x;
+        const double qy = (double)(P->bn[b] * P->g.f) / P->g.cell_y;
+        if (inside_aperture(qx, qy, lam, probe->alpha_mrad * 1e-3)) {
+            base[b] = phase_cycles(chi_cycles(qx * qx + qy * qy, lam, probe->c1, probe->c3));
+            count += 1.0;
+        } else {
+            base[b] = make_float2(0.f, 0.f);
+        }
+    }
+    const long long Pn = (long long)sc->px * sc->py;
+    if ((rc = grow(P->arena, (void **)&P->pos, &P->pos_cap, std::max<size_t>(16, (size_t)Pn * 2 * sizeof(double))))) return rc;
+    if (Pn > 0) {
+        // pageable copy of the caller's arrays: cudaMemcpyAsync stages pageable memory before it returns
+        std::vector<double> xy((size_t)Pn * 2);
+        std::memcpy(xy.data(), sc->x0, Pn * sizeof(double));
+        std::memcpy(xy.data() + Pn, sc->y0, Pn * sizeof(double));
+        CUDA_TRY(cudaMemcpyAsync(P->pos, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(P->base, base.data(), B * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
+    // window bin map (q = k f / cell on the window grid), cached per detector
+    if (P->det_nbins != det->nbins || P->det_key[0] != det->start_mrad || P->det_key[1] != det->step_mrad) {
+        std::vector<int> off, idx;
+        detector_csr(P->nw, P->nw, P->g.cell_x, P->g.cell_y, P->g.f, lam, det, off, idx);
+        std::vector<int> all(off);
+        all.insert(all.end(), idx.begin(), idx.end());
+        if ((rc = grow(P->arena, (void **)&P->bin_buf, &P->bin_cap, all.size() * sizeof(int)))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(P->bin_buf, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+        P->det_nbins = det->nbins;
+        P->det_key[0] = det->start_mrad;
+        P->det_key[1] = det->step_mrad;
+    }
+    std::memset(&a, 0, sizeof(a));
+    a.S = P->S;
+    a.x0 = P->pos;
+    a.y0 = P->pos + Pn;
+    a.qx = P->beam_q;
+    a.qy = P->beam_q + B;
+    a.base = P->base;
+    a.tw_fwd = P->tww_f;
+    a.bin_off = P->bin_buf;
+    a.bin_idx = P->bin_buf + det->nbins + 1;
+    a.px_s = pxs;
+    a.py_s = pys;
+    const double nw2 = (double)P->nw * (double)P->nw;
+    a.inv_norm = count > 0 ? 1.0 / (nw2 * nw2 * count) : 0.0;
+    a.n_beams = B;
+    a.nx_s = P->nxs;
+    a.ny_s = P->nys;
+    a.nbins = det->nbins;
+    a.n_probes = (int)Pn;
+    a.probe0 = 0;
+    a.tw = P->tw64;
+    return PRISM_OK;
+}
+
+extern "C" int prism_scan_run(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
+                              const prism_detector *det, float *out_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    ScanArgs a;
+    int rc = scan_prepare(P, probe, sc, det, a);
+    if (rc) return rc;
+    if (a.n_probes == 0) return PRISM_OK;
+    if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
+    a.out = out_dev;
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+}
+
+extern "C" int prism_scan_run_host(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
+                                   const prism_detector *det, float *out_host) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    ScanArgs a;
+    int rc = scan_prepare(P, probe, sc, det, a);
+    if (rc) return rc;
+    if (a.n_probes == 0) return PRISM_OK;
+    if (!out_host) return fail(PRISM_ERR_INVALID, "out_host is NULL");
+    const size_t bytes = (size_t)a.n_probes * det->nbins * sizeof(float);
+    if ((rc = grow(P->arena, (void **)&P->out_stage, &P->out_cap, bytes))) return rc;
+    a.out = P->out_stage;
+    rc = plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out_host, P->out_stage, bytes, cudaMemcpyDeviceToHost, P->stream));
+    return PRISM_OK;
+}
+
+// ------------------------------------------------------------------ multislice baseline
+extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
+                                   const prism_scan *sc, const prism_detector *det, float *out_dev,
+                                   void *cuda_stream, size_t scratch_bytes) {
+    int rc;
+    if ((rc = check_grid_common(grid))) return rc;
+    if ((rc = check_probe(probe))) return rc;
+    if ((rc = check_det(det))) return rc;
+    const prism_grid &g = *grid;
+    if ((rc = check_scan(sc, g.cell_x / g.nx * (double)(1 << 28), g.cell_y / g.ny * (double)(1 << 28)))) return rc;
+    const long long Pn = (long long)sc->px * sc->py;
+    if (Pn == 0) return PRISM_OK;
+    if ((rc = check_dev_ptr(V_dev, 16, "V_dev"))) return rc;
+    if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GridTables T;
+    if ((rc = build_grid_tables(&g, T))) return rc;
+    const int nx = g.nx, ny = g.ny;
+    const size_t px = (size_t)nx * ny;
+    // probe A(q) exp(-i chi(q)) on the full grid, sum |Psi0|^2 = aperture pixel count
+    std::vector<float2> pbase(px);
+    double count = 0;
+    for (int ky = 0; ky < ny; ++ky) {
+        const double qy = (double)signed_index(ky, ny) / g.cell_y;
+        for (int kx = 0; kx < nx; ++kx) {
+            const double qx = (double)signed_index(kx, nx) / g.cell_x;
+            if (inside_aperture(qx, qy, T.lam, probe->alpha_mrad * 1e-3)) {
+                pbase[(size_t)ky * nx + kx] = phase_cycles(chi_cycles(qx * qx + qy * qy, T.lam, probe->c1, probe->c3));
+                count += 1.0;
+            } else {
+                pbase[(size_t)ky * nx + kx] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    std::vector<int> off, idx;
+    detector_csr(nx, ny, g.cell_x, g.cell_y, 1, T.lam, det, off, idx);
+    if (scratch_bytes == 0) scratch_bytes = (size_t)1 << 30;
+    const int Pb = (int)std::max<long long>(1, std::min<long long>(Pn, (long long)(scratch_bytes / (px * 8))));
+    const Tw64 tw = make_tw64();
+
+    DevArena A;
+    A.stream = st;
+    float2 *t, *wave, *prop_x, *prop_y, *twr_f, *twr_i, *twc_f, *twc_i, *pb, *shx, *shy;
+    float *inten;
+    int *aa, *d_off, *d_idx;
+    double *pos;
+    auto done = [&](int code) {
+        A.release();
+        if (code) cudaStreamSynchronize(st);
+        return code;
+    };
+    if ((rc = A.alloc((void **)&t, (size_t)g.n_slices * px * 8))) return done(rc);
+    if ((rc = A.alloc((void **)&wave, (size_t)Pb * px * 8))) return done(rc);
+    if ((rc = A.alloc((void **)&inten, (size_t)Pb * px * 4))) return done(rc);
+    if ((rc = A.alloc((void **)&shx, (size_t)Pb * nx * 8))) return done(rc);
+    if ((rc = A.alloc((void **)&shy, (size_t)Pb * ny * 8))) return done(rc);
+    if ((rc = A.upload(&prop_x, T.prop_x))) return done(rc);
+    if ((rc = A.upload(&prop_y, T.prop_y))) return done(rc);
+    if ((rc = A.upload(&aa, T.aa_kmax))) return done(rc);
+    if ((rc = A.upload(&twr_f, T.twr_f))) return done(rc);
+    if ((rc = A.upload(&twr_i, T.twr_i))) return done(rc);
+    if ((rc = A.upload(&twc_f, T.twc_f))) return done(rc);
+    if ((rc = A.upload(&twc_i, T.twc_i))) return done(rc);
+    if ((rc = A.upload(&pb, pbase))) return done(rc);
+    if ((rc = A.upload(&d_off, off))) return done(rc);
+    if ((rc = A.upload(&d_idx, idx))) return done(rc);
+    if ((rc = A.alloc((void **)&pos, (size_t)Pn * 2 * sizeof(double)))) return done(rc);
+    {
+        std::vector<double> xy((size_t)Pn * 2);
+        std::memcpy(xy.data(), sc->x0, Pn * sizeof(double));
+        std::memcpy(xy.data() + Pn, sc->y0, Pn * sizeof(double));
+        cudaError_t e = cudaMemcpyAsync(pos, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            fail(PRISM_ERR_CUDA, std::string("position upload: ") + cudaGetErrorString(e));
+            return done(PRISM_ERR_CUDA);
+        }
+    }
+    auto check = [&](cudaError_t err, const char *what) {
+        if (err != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
+        return PRISM_OK;
+    };
+    if ((rc = check(launch_transmission(V_dev, t, (size_t)g.n_slices * px, T.sigma / (2.0 * PI), st), "transmission"))) return done(rc);
+    for (long long p0 = 0; p0 < Pn; p0 += Pb) {
+        const int nb = (int)std::min<long long>(Pb, Pn - p0);
+        ShiftArgs sa;
+        sa.x0 = pos + p0;
+        sa.y0 = pos + Pn + p0;
+        sa.shift_x = shx;
+        sa.shift_y = shy;
+        sa.nx = nx;
+        sa.ny = ny;
+        sa.batch = nb;
+        sa.cell_x = g.cell_x;
+        sa.cell_y = g.cell_y;
+        if ((rc = check(launch_shift(sa, st), "shift phases"))) return done(rc);
+        ColArgs ci = col_args(T, wave, prop_x, prop_y, aa, twc_f, twc_i, tw);
+        ci.batch = nb;
+        ci.probe_base = pb;
+        ci.shift_x = shx;
+        ci.shift_y = shy;
+        ci.probe_scale = (float)(1.0 / ((double)nx * ny));
+        if ((rc = check(launch_col(ny, COL_PROBE, ci, st), "probe init"))) return done(rc);
+        for (int p = 0; p < g.n_slices; ++p) {
+            RowArgs ra;
+            std::memset(&ra, 0, sizeof(ra));
+            ra.wave = wave;
+            ra.trans = t + (size_t)p * px;
+            ra.tw_fwd = twr_f;
+            ra.tw_inv = twr_i;
+            ra.ny = ny;
+            ra.n_rows = nb * ny;
+            ra.tw = tw;
+            if ((rc = check(launch_row(nx, ROW_STD, ra, st), "row pass"))) return done(rc);
+            const int pi = T.slice_prop[p];
+            ColArgs ca = col_args(T, wave, prop_x + (size_t)pi * nx, prop_y + (size_t)pi * ny, aa, twc_f, twc_i, tw);
+            ca.batch = nb;
+            ca.inten = inten;
+            if ((rc = check(launch_col(ny, p + 1 == g.n_slices ? COL_DETECT : COL_STD, ca, st), "column pass"))) return done(rc);
+        }
+        BinArgs ba;
+        ba.inten = inten;
+        ba.bin_off = d_off;
+        ba.bin_idx = d_idx;
+        ba.out = out_dev + (size_t)p0 * det->nbins;
+        const double nn = (double)nx * ny;
+        ba.scale = count > 0 ? nn * nn / count : 0.0;
+        ba.npix = (int)px;
+        ba.nbins = det->nbins;
+        ba.batch = nb;
+        if ((rc = check(launch_bins(ba, st), "bins"))) return done(rc);
+    }
+    // pageable uploads were staged before their calls returned; the frees below are stream-ordered
+    return done(PRISM_OK);
+}
+
+// ------------------------------------------------------------------ introspection
+extern "C" int prism_plan_info(const prism_plan *P, prism_info *out) {
+    if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    out->n_beams = P->nbeams;
+    out->nx_s = P->nxs;
+    out->ny_s = P->nys;
+    out->nw_x = P->nw;
+    out->nw_y = P->nw;
+    out->beam_batch = P->batch;
+    out->wavelength = P->T.lam;
+    out->sigma = P->T.sigma;
+    out->device_bytes = P->arena.bytes;
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_smatrix_bytes(const prism_plan *P, size_t *out) {
+    if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    *out = (size_t)P->nbeams * P->nxs * P->nys * 8;
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_beams(const prism_plan *P, int *m, int *n, int capacity) {
+    if (!P || !m || !n) return fail(PRISM_ERR_INVALID, "NULL argument");
+    if (capacity < P->nbeams) return fail(PRISM_ERR_INVALID, "capacity < n_beams");
+    for (int b = 0; b < P->nbeams; ++b) {
+        m[b] = P->bm[b];
+        n[b] = P->bn[b];
+    }
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_smatrix(const prism_plan *P, const void **dev_ptr) {
+    if (!P || !dev_ptr) return fail(PRISM_ERR_INVALID, "NULL argument");
+    *dev_ptr = P->S;
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_transmission(const prism_plan *P, const void **dev_ptr) {
+    if (!P || !dev_ptr) return fail(PRISM_ERR_INVALID, "NULL argument");
+    *dev_ptr = P->t;
+    return PRISM_OK;
+}
+
+// ------------------------------------------------------------------ timing
+static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan"};
+
+extern "C" const char *prism_kernel_name(int kind) {
+    if (kind < 0 || kind >= PRISM_K_COUNT) return "?";
+    return k_names[kind];
+}
+
+extern "C" int prism_plan_set_profiling(prism_plan *P, int enable) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    P->profiling = enable != 0;
+    return PRISM_OK;
+}
+
+static int drain_events(prism_plan *P) {
+    if (P->pending.empty()) return PRISM_OK;
+    CUDA_TRY(cudaStreamSynchronize(P->stream));
+    for (auto &pe : P->pending) {
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, pe.a, pe.b));
+        P->kms[pe.kind] += ms;
+        P->ev_pool.push_back(pe.a);
+        P->ev_pool.push_back(pe.b);
+    }
+    P->pending.clear();
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_kernel_stats(prism_plan *P, int kind, long *launches, double *total_ms) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    if (kind < 0 || kind >= PRISM_K_COUNT) return fail(PRISM_ERR_INVALID, "bad kernel kind");
+    int rc = drain_events(P);
+    if (rc) return rc;
+    if (launches) *launches = P->kl[kind];
+    if (total_ms) *total_ms = P->kms[kind];
+    return PRISM_OK;
+}
+
+extern "C" long prism_plan_launches(const prism_plan *P) { return P ? P->launches : 0; }
+
+extern "C" int prism_plan_reset_stats(prism_plan *P) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    int rc = drain_events(P);
+    if (rc) return rc;
+    for (int k = 0; k < PRISM_K_COUNT; ++k) {
+        P->kms[k] = 0;
+        P->kl[k] = 0;
+    }
+    P->launches = 0;
+    return PRISM_OK;
+}

@@ -1,0 +1,252 @@
+// fft.cuh -- register-resident DFTs and a two-level block FFT for sm_103a.
+//
+// Convention (as in the rest of the library): forward X[k] = sum_n x[n] exp(-2 pi i n k / N),
+// inverse without normalisation (exp(+2 pi i n k / N)); callers fold 1/N where needed.
+//
+// Structure.  A length-N transform is split as N = N1 * N2 (four-step / Stockham form):
+//   X[k1 + N1 k2] = sum_{n2} W_N2^{n2 k2} * ( W_N^{n2 k1} * sum_{n1} x[N2 n1 + n2] W_N1^{n1 k1} ).
+// T = N / E threads cooperate on one transform, each holding E = max(N1, N2) elements in
+// registers.  Stage 1 is a radix-N1 DFT in registers, then the inter-stage twiddle, one
+// exchange through shared memory, and stage 2 is a radix-N2 DFT in registers.  Register DFTs of
+// size 16..64 are themselves split recursively at compile time with twiddles held in kernel
+// parameter space (constant bank), so every index below is a compile-time constant.
+//
+// Register layouts (thread t, J = E/N1, I = E/N2):
+//   input : reg n1*J + j  holds element  N2*n1 + t + T*j
+//   output: reg k2*I + i  holds element  t + T*i + N1*k2
+// A forward transform with split (A, B) leaves its output in exactly the input layout of an
+// inverse transform with split (B, A), and vice versa, so FFT -> pointwise -> IFFT chains need no
+// data movement between transforms.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "params.h"  // Tw64: W_64^j = exp(-2 pi i j / 64), computed on the host in double
+
+namespace prism {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// multiply by W_4 (forward: -i, inverse: +i)
+template <bool INV>
+__device__ __forceinline__ float2 rot4(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// multiply by W_64^J (forward) or W_64^-J (inverse); J is a compile-time constant.
+template <int J, bool INV>
+__device__ __forceinline__ float2 twiddle64(float2 a, const Tw64 &tw) {
+    constexpr int j = J & 63;
+    constexpr float r = 0.70710678118654752440f;  // sqrt(1/2)
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 16) {
+        return rot4<INV>(a);
+    } else if constexpr (j == 32) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (j == 48) {
+        return rot4<!INV>(a);
+    } else if constexpr (j == 8) {  // (1 - i)/sqrt2 forward
+        return INV ? make_float2((a.x - a.y) * r, (a.x + a.y) * r) : make_float2((a.x + a.y) * r, (a.y - a.x) * r);
+    } else if constexpr (j == 24) {  // (-1 - i)/sqrt2 forward
+        return INV ? make_float2(-(a.x + a.y) * r, (a.x - a.y) * r) : make_float2((a.y - a.x) * r, -(a.x + a.y) * r);
+    } else if constexpr (j == 40) {  // (-1 + i)/sqrt2 forward
+        return INV ? make_float2((a.y - a.x) * r, -(a.x + a.y) * r) : make_float2(-(a.x + a.y) * r, (a.x - a.y) * r);
+    } else if constexpr (j == 56) {  // (1 + i)/sqrt2 forward
+        return INV ? make_float2((a.x + a.y) * r, (a.y - a.x) * r) : make_float2((a.x - a.y) * r, (a.x + a.y) * r);
+    } else {
+        return INV ? cmulc(a, tw.w[j]) : cmul(a, tw.w[j]);
+    }
+}
+
+// In-place DFT of R elements x[0], x[S], ..., x[(R-1)S]; natural order in and out.
+template <int R, int S, bool INV>
+struct Dft;
+
+template <int S, bool INV>
+struct Dft<1, S, INV> {
+    __device__ __forceinline__ static void run(float2 *, const Tw64 &) {}
+};
+
+template <int S, bool INV>
+struct Dft<2, S, INV> {
+    __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
+        float2 a = x[0], b = x[S];
+        x[0] = cadd(a, b);
+        x[S] = csub(a, b);
+    }
+};
+
+template <int S, bool INV>
+struct Dft<4, S, INV> {
+    __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
+        float2 t0 = cadd(x[0], x[2 * S]);
+        float2 t1 = csub(x[0], x[2 * S]);
+        float2 t2 = cadd(x[S], x[3 * S]);
+        float2 t3 = rot4<INV>(csub(x[S], x[3 * S]));
+        x[0] = cadd(t0, t2);
+        x[2 * S] = csub(t0, t2);
+        x[S] = cadd(t1, t3);
+        x[3 * S] = csub(t1, t3);
+    }
+};
+
+template <int S, bool INV>
+struct Dft<8, S, INV> {
+    __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
+        // decimation in frequency: b_k = a_k + a_{k+4} (even outputs), c_k = (a_k - a_{k+4}) W8^k (odd)
+        float2 b[4], c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[k] = cadd(x[k * S], x[(k + 4) * S]);
+            c[k] = csub(x[k * S], x[(k + 4) * S]);
+        }
+        c[1] = twiddle64<8, INV>(c[1], tw);
+        c[2] = rot4<INV>(c[2]);
+        c[3] = twiddle64<24, INV>(c[3], tw);
+        Dft<4, 1, INV>::run(b, tw);
+        Dft<4, 1, INV>::run(c, tw);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            x[(2 * m) * S] = b[m];
+            x[(2 * m + 1) * S] = c[m];
+        }
+    }
+};
+
+template <int R>
+struct DftSplit {
+    static constexpr int R1 = (R == 16) ? 4 : (R == 32) ? 8 : (R == 64) ? 8 : 0;
+    static constexpr int R2 = R / R1;
+};
+
+template <int R1, int R2, int S, bool INV, int N2>
+struct DftTw {
+    // multiply element (R2*k1 + n2) by W_R^{n2 k1}, for all n2 < R2, k1 < R1
+    template <int K>
+    __device__ __forceinline__ static void go(float2 *x, const Tw64 &tw) {
+        if constexpr (K < R1 * R2) {
+            constexpr int k1 = K / R2, n2 = K % R2;
+            x[(R2 * k1 + n2) * S] = twiddle64<(n2 * k1 * (64 / (R1 * R2))) & 63, INV>(x[(R2 * k1 + n2) * S], tw);
+            go<K + 1>(x, tw);
+        }
+    }
+};
+
+template <int R, int S, bool INV>
+struct Dft {
+    static constexpr int R1 = DftSplit<R>::R1;
+    static constexpr int R2 = DftSplit<R>::R2;
+    static_assert(R1 > 0, "unsupported register DFT size");
+    __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
+        // stage 1: DFT over n1 of elements (R2 n1 + n2) for each n2
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) Dft<R1, R2 * S, INV>::run(x + n2 * S, tw);
+        DftTw<R1, R2, S, INV, R2>::template go<0>(x, tw);
+        // stage 2: DFT over n2 of elements (R2 k1 + n2) for each k1 -> X[k1 + R1 k2] at (R2 k1 + k2)
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV>::run(x + R2 * k1 * S, tw);
+        float2 tmp[R];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) tmp[k1 + R1 * k2] = x[(R2 * k1 + k2) * S];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k * S] = tmp[k];
+    }
+};
+
+// ----------------------------------------------------------------------------------------
+// Split of each supported length into (N1, N2) for the forward transform; the inverse uses
+// (N2, N1) so that forward-out == inverse-in layouts.
+template <int N>
+struct FftShape {
+    static constexpr int N1 = (N == 8) ? 4 : (N == 16) ? 4 : (N == 32) ? 8 : (N == 64) ? 8 : (N == 128) ? 16
+                            : (N == 256) ? 16 : (N == 512) ? 32 : (N == 1024) ? 32 : (N == 2048) ? 64 : 0;
+    static constexpr int N2 = N1 ? N / N1 : 0;
+    static constexpr int E = N1 > N2 ? N1 : N2;
+    static constexpr int T = N / E;
+    static_assert(N1 > 0, "unsupported FFT length");
+};
+
+// Two-level transform of length N = N1*N2 over T threads.  `stw` is the inter-stage twiddle
+// table laid out [k1][n2] = W_N^{n2 k1} (forward sign; the inverse conjugates it).  `Ex` is the
+// exchange: write(k1, n2, v), read(k1, n2), sync().
+template <int N1, int N2, bool INV>
+struct BlockFft {
+    static constexpr int N = N1 * N2;
+    static constexpr int E = N1 > N2 ? N1 : N2;
+    static constexpr int T = N / E;
+    static constexpr int J = E / N1;
+    static constexpr int I = E / N2;
+
+    template <class Ex>
+    __device__ __forceinline__ static void run(float2 (&x)[E], int t, const float2 *__restrict__ stw,
+                                               const Tw64 &tw, Ex &ex) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) Dft<N1, J, INV>::run(x + j, tw);
+        ex.sync();  // previous readers of the exchange are done
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int n2 = t + T * j;
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                float2 v = x[k1 * J + j];
+                if (k1 != 0) {
+                    const float2 w = __ldg(stw + k1 * N2 + n2);
+                    v = INV ? cmulc(v, w) : cmul(v, w);
+                }
+                ex.write(k1, n2, v);
+            }
+        }
+        ex.sync();
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            const int k1 = t + T * i;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) x[n2 * I + i] = ex.read(k1, n2);
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i) Dft<N2, I, INV>::run(x + i, tw);
+    }
+
+    // element index held in register r (input / output layouts)
+    __device__ __forceinline__ static int in_elem(int r, int t) { return N2 * (r / J) + t + T * (r % J); }
+    __device__ __forceinline__ static int out_elem(int r, int t) { return t + T * (r % I) + N1 * (r / I); }
+};
+
+template <int N>
+using FwdFft = BlockFft<FftShape<N>::N1, FftShape<N>::N2, false>;
+template <int N>
+using InvFft = BlockFft<FftShape<N>::N2, FftShape<N>::N1, true>;
+
+// Exchange for transforms held by T consecutive lanes of one warp (T <= 32); each transform
+// owns N1*(N2+1) float2 of shared memory (the +1 pad keeps stage-2 reads at two wavefronts).
+template <int N1, int N2, int T>
+struct WarpExchange {
+    float2 *buf;
+    __device__ __forceinline__ void write(int k1, int n2, float2 v) { buf[k1 * (N2 + 1) + n2] = v; }
+    __device__ __forceinline__ float2 read(int k1, int n2) const { return buf[k1 * (N2 + 1) + n2]; }
+    __device__ __forceinline__ void sync() { __syncwarp(); }
+    static constexpr int kFloats2 = N1 * (N2 + 1);
+};
+
+// Exchange for W interleaved columns handled by a whole CTA: layout [k1][n2][c].
+template <int N1, int N2, int W>
+struct ColExchange {
+    float2 *buf;
+    int c;
+    __device__ __forceinline__ void write(int k1, int n2, float2 v) { buf[(k1 * N2 + n2) * W + c] = v; }
+    __device__ __forceinline__ float2 read(int k1, int n2) const { return buf[(k1 * N2 + n2) * W + c]; }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
+}  // namespace prism

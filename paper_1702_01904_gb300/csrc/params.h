@@ -1,0 +1,107 @@
+// params.h -- kernel parameter blocks and launcher declarations shared by the host engine
+// (engine.cpp, plain C++) and the CUDA translation units.  Parameters travel by value in
+// kernel parameter space (__grid_constant__), which keeps the 64 register-DFT twiddles in the
+// constant bank.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace prism {
+
+struct Tw64 {
+    float2 w[64];  // W_64^j = exp(-2 pi i j / 64)
+};
+
+enum RowMode { ROW_STD = 0, ROW_PLANE = 1, ROW_OUT = 2 };
+enum ColMode { COL_STD = 0, COL_PROBE = 1, COL_DETECT = 2 };
+
+// Row pass over rows of length nx of a wave stack [batch][ny][nx] (x-Fourier between passes).
+struct RowArgs {
+    float2 *wave;              // [batch][ny][nx]
+    const float2 *trans;       // t_p, [ny][nx]   (STD, PLANE)
+    const float2 *tw_fwd;      // inter-stage twiddles of the forward split  [N1][N2]
+    const float2 *tw_inv;      // inter-stage twiddles of the inverse split  [N2][N1]
+    float2 *s_out;             // OUT: S-matrix [B][ny_s][nx_s]
+    const int *beam_mn;        // PLANE: [B][2] (m, n)
+    int ny;
+    int n_rows;                // rows processed by this launch
+    int f;                     // PLANE
+    int beam0;                 // first beam of this batch (PLANE, OUT)
+    int downsample;            // OUT
+    Tw64 tw;
+};
+
+// Column pass over columns of length ny.
+struct ColArgs {
+    float2 *wave;              // [batch][ny][nx]
+    float *inten;              // DETECT: [batch][ny][nx] |Psi|^2 (scaled later)
+    const float2 *prop_x;      // [nx]  exp(-i pi lambda dz qx^2)
+    const float2 *prop_y;      // [ny]  exp(-i pi lambda dz qy^2) / (nx ny)
+    const int *aa_kmax;        // [ny]  largest |kx| inside the AA aperture on row ky, -1 if none
+    const float2 *tw_fwd;
+    const float2 *tw_inv;
+    const float2 *probe_base;  // PROBE: [ny][nx] A(q) exp(-i chi(q))
+    const float2 *shift_x;     // PROBE: [batch][nx] exp(-2 pi i qx x0)
+    const float2 *shift_y;     // PROBE: [batch][ny] exp(-2 pi i qy y0)
+    int nx;
+    int batch;
+    float probe_scale;         // PROBE: 1 / (nx ny)
+    Tw64 tw;
+};
+
+// PRISM probe scan (coefficients, window gather, beam sum, window FFT, |.|^2, bins).
+struct ScanArgs {
+    const float2 *S;           // [B][ny_s][nx_s]
+    const double *x0;          // [P]
+    const double *y0;          // [P]
+    const double *qx;          // [B] beam qx = m f / cell_x
+    const double *qy;          // [B]
+    const float2 *base;        // [B] A(q_b) exp(-i chi(q_b))
+    const float2 *tw_fwd;      // window FFT inter-stage twiddles
+    const float2 *tw_inv;      // (unused by the forward-only window FFT; kept for symmetry)
+    const int *bin_off;        // [nbins+1] CSR offsets into bin_idx
+    const int *bin_idx;        // window pixel indices (ky*nw + kx) grouped by bin
+    float *out;                // [P][nbins]
+    double px_s, py_s;         // stored pixel size
+    double inv_norm;           // 1 / (nw^4 * sum_b A_b)
+    int n_beams;
+    int nx_s, ny_s;
+    int nbins;
+    int n_probes;
+    int probe0;
+    Tw64 tw;
+};
+
+struct ShiftArgs {
+    const double *x0, *y0;     // [batch]
+    float2 *shift_x;           // [batch][nx]
+    float2 *shift_y;           // [batch][ny]
+    int nx, ny, batch;
+    double cell_x, cell_y;
+};
+
+struct BinArgs {
+    const float *inten;        // [batch][npix]
+    const int *bin_off;        // [nbins+1]
+    const int *bin_idx;
+    float *out;                // [batch][nbins]
+    double scale;
+    int npix, nbins, batch;
+};
+
+// launchers (kernels_build.cu, kernels_scan.cu); return cudaSuccess or the launch error
+cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigma_cycles, cudaStream_t s);
+cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s);
+cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s);
+cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
+cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
+cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
+// smallest scan-window / FFT sizes the kernels are instantiated for
+bool row_supported(int n);
+bool col_supported(int n);
+bool scan_supported(int nw);
+// FFT split used by the kernels for length n: forward (n1, n2)
+void fft_split(int n, int *n1, int *n2);
+
+}  // namespace prism

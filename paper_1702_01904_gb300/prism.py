@@ -1,0 +1,273 @@
+"""ctypes binding of libprism.so (include/prism.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device buffers are passed as
+integers (CUDA device addresses) or as objects with ``data_ptr()`` (torch tensors); streams as
+integers (``torch.cuda.current_stream().cuda_stream``) or ``None`` for the legacy default stream.
+A non-zero status raises :class:`PrismError` carrying the status and ``prism_last_error()``.
+There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_long, c_size_t, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libprism.so")
+
+PRISM_OK = 0
+PRISM_ERR_INVALID = -1
+PRISM_ERR_BUDGET = -2
+PRISM_ERR_CUDA = -3
+PRISM_ERR_DEVICE = -4
+PRISM_ERR_UNSUPPORTED = -5
+
+PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN = range(6)
+PRISM_K_COUNT = 6
+
+# every entry point declared in include/prism.h
+EXPORTED = [
+    "prism_plan_create", "prism_plan_destroy", "prism_sync", "prism_last_error",
+    "prism_build_smatrix", "prism_build_smatrix_host", "prism_scan_run", "prism_scan_run_host",
+    "multislice_scan_run", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
+    "prism_plan_smatrix", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
+    "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
+    "prism_kernel_name",
+]
+
+
+class PrismError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libprism status {status}: {msg}")
+        self.status = status
+
+
+class PrismGrid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("n_slices", c_int),
+                ("cell_x", c_double), ("cell_y", c_double), ("dz", c_double),
+                ("slice_dz", POINTER(c_double)), ("kv", c_double), ("f", c_int),
+                ("downsample", c_int), ("aa_frac", c_double), ("alpha_max_mrad", c_double)]
+
+
+class PrismProbe(ctypes.Structure):
+    _fields_ = [("alpha_mrad", c_double), ("c1", c_double), ("c3", c_double),
+                ("tilt_x", c_double), ("tilt_y", c_double)]
+
+
+class PrismScan(ctypes.Structure):
+    _fields_ = [("px", c_int), ("py", c_int), ("x0", POINTER(c_double)), ("y0", POINTER(c_double))]
+
+
+class PrismDetector(ctypes.Structure):
+    _fields_ = [("start_mrad", c_double), ("step_mrad", c_double), ("nbins", c_int)]
+
+
+class PrismInfo(ctypes.Structure):
+    _fields_ = [("n_beams", c_int), ("nx_s", c_int), ("ny_s", c_int), ("nw_x", c_int), ("nw_y", c_int),
+                ("beam_batch", c_int), ("wavelength", c_double), ("sigma", c_double),
+                ("device_bytes", c_size_t)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libprism.so (built by ``paper_1702_01904_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libprism.so not found at {path}: run `python -m paper_1702_01904_gb300.build`")
+    L = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "prism_plan_create": (c_int, [POINTER(PrismGrid), c_size_t, P, POINTER(P)]),
+        "prism_plan_destroy": (None, [P]),
+        "prism_sync": (c_int, [P]),
+        "prism_last_error": (c_char_p, []),
+        "prism_build_smatrix": (c_int, [P, P]),
+        "prism_build_smatrix_host": (c_int, [P, P]),
+        "prism_scan_run": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
+        "prism_scan_run_host": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
+        "multislice_scan_run": (c_int, [POINTER(PrismGrid), P, POINTER(PrismProbe), POINTER(PrismScan),
+                                        POINTER(PrismDetector), P, P, c_size_t]),
+        "prism_plan_info": (c_int, [P, POINTER(PrismInfo)]),
+        "prism_plan_smatrix_bytes": (c_int, [P, POINTER(c_size_t)]),
+        "prism_plan_beams": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int]),
+        "prism_plan_smatrix": (c_int, [P, POINTER(P)]),
+        "prism_plan_transmission": (c_int, [P, POINTER(P)]),
+        "prism_wavelength": (c_double, [c_double]),
+        "prism_interaction_constant": (c_double, [c_double]),
+        "prism_plan_set_profiling": (c_int, [P, c_int]),
+        "prism_plan_kernel_stats": (c_int, [P, c_int, POINTER(c_long), POINTER(c_double)]),
+        "prism_plan_launches": (c_long, [P]),
+        "prism_plan_reset_stats": (c_int, [P]),
+        "prism_kernel_name": (c_char_p, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != PRISM_OK:
+        raise PrismError(status, load().prism_last_error().decode())
+    return status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return c_void_p(x.ctypes.data)
+    return c_void_p(int(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return c_void_p(s.cuda_stream)
+    return c_void_p(int(s))
+
+
+# ------------------------------------------------------------------ struct helpers
+def make_grid(nx, ny, n_slices, cell_x, cell_y, dz, kv, f=1, downsample=2, aa_frac=0.5,
+              alpha_max_mrad=20.0, slice_dz=None):
+    g = PrismGrid(nx, ny, n_slices, cell_x, cell_y, dz, None, kv, f, downsample, aa_frac, alpha_max_mrad)
+    if slice_dz is not None:
+        arr = np.ascontiguousarray(slice_dz, dtype=np.float64)
+        g._keep = arr
+        g.slice_dz = arr.ctypes.data_as(POINTER(c_double))
+    return g
+
+
+def grid_from_workload(w):
+    return make_grid(w.nx, w.ny, w.n_slices, w.cell_x, w.cell_y, w.dz, w.kv, w.f, w.downsample,
+                     w.aa_frac, w.alpha_mrad)
+
+
+def make_probe(alpha_mrad, c1=0.0, c3=0.0, tilt_x=0.0, tilt_y=0.0):
+    return PrismProbe(alpha_mrad, c1, c3, tilt_x, tilt_y)
+
+
+def make_scan(px, py, x0, y0):
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    s = PrismScan(px, py, x0.ctypes.data_as(POINTER(c_double)), y0.ctypes.data_as(POINTER(c_double)))
+    s._keep = (x0, y0)
+    return s
+
+
+def make_detector(start_mrad, step_mrad, nbins):
+    return PrismDetector(start_mrad, step_mrad, nbins)
+
+
+# ------------------------------------------------------------------ entry points (same names as C)
+def prism_plan_create(grid, hbm_budget_bytes=0, cuda_stream=None):
+    L = load()
+    plan = c_void_p()
+    _check(L.prism_plan_create(byref(grid), hbm_budget_bytes, _stream(cuda_stream), byref(plan)))
+    return plan
+
+
+def prism_plan_destroy(plan):
+    load().prism_plan_destroy(plan)
+
+
+def prism_sync(plan):
+    return _check(load().prism_sync(plan))
+
+
+def prism_last_error():
+    return load().prism_last_error().decode()
+
+
+def prism_build_smatrix(plan, V_dev):
+    return _check(load().prism_build_smatrix(plan, _ptr(V_dev)))
+
+
+def prism_build_smatrix_host(plan, V_host):
+    return _check(load().prism_build_smatrix_host(plan, _ptr(V_host)))
+
+
+def prism_scan_run(plan, probe, scan, det, out_dev):
+    return _check(load().prism_scan_run(plan, byref(probe), byref(scan), byref(det), _ptr(out_dev)))
+
+
+def prism_scan_run_host(plan, probe, scan, det, out_host):
+    return _check(load().prism_scan_run_host(plan, byref(probe), byref(scan), byref(det), _ptr(out_host)))
+
+
+def multislice_scan_run(grid, V_dev, probe, scan, det, out_dev, cuda_stream=None, scratch_bytes=0):
+    return _check(load().multislice_scan_run(byref(grid), _ptr(V_dev), byref(probe), byref(scan), byref(det),
+                                             _ptr(out_dev), _stream(cuda_stream), scratch_bytes))
+
+
+def prism_plan_info(plan):
+    info = PrismInfo()
+    _check(load().prism_plan_info(plan, byref(info)))
+    return info
+
+
+def prism_plan_smatrix_bytes(plan):
+    n = c_size_t()
+    _check(load().prism_plan_smatrix_bytes(plan, byref(n)))
+    return n.value
+
+
+def prism_plan_beams(plan):
+    nb = prism_plan_info(plan).n_beams
+    m = (c_int * nb)()
+    n = (c_int * nb)()
+    _check(load().prism_plan_beams(plan, m, n, nb))
+    return np.array(m[:], dtype=np.int64), np.array(n[:], dtype=np.int64)
+
+
+def prism_plan_smatrix(plan):
+    p = c_void_p()
+    _check(load().prism_plan_smatrix(plan, byref(p)))
+    return p.value
+
+
+def prism_plan_transmission(plan):
+    p = c_void_p()
+    _check(load().prism_plan_transmission(plan, byref(p)))
+    return p.value
+
+
+def prism_wavelength(kv):
+    return load().prism_wavelength(kv)
+
+
+def prism_interaction_constant(kv):
+    return load().prism_interaction_constant(kv)
+
+
+def prism_plan_set_profiling(plan, enable=True):
+    return _check(load().prism_plan_set_profiling(plan, 1 if enable else 0))
+
+
+def prism_plan_kernel_stats(plan, kind):
+    n = c_long()
+    ms = c_double()
+    _check(load().prism_plan_kernel_stats(plan, kind, byref(n), byref(ms)))
+    return n.value, ms.value
+
+
+def prism_plan_launches(plan):
+    return load().prism_plan_launches(plan)
+
+
+def prism_plan_reset_stats(plan):
+    return _check(load().prism_plan_reset_stats(plan))
+
+
+def prism_kernel_name(kind):
+    return load().prism_kernel_name(kind).decode()

@@ -1,0 +1,126 @@
+"""Torch-facing convenience layer over the C ABI (marshalling only; all arithmetic runs in libprism).
+
+PyTorch provides device memory and streams; every step of the simulation runs in the library's
+CUDA kernels.  Nothing here falls back to a CPU path: a missing library or GPU raises.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import prism as P
+
+
+class _CudaView:
+    """Expose a device pointer owned by the library as a zero-copy torch tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), True), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3}
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("libprism needs a CUDA device; none is available")
+
+
+class PrismSimulation:
+    """One PRISM plan: build the compact S-matrix once, scan probes against it many times."""
+
+    def __init__(self, grid: P.PrismGrid, hbm_budget_bytes: int = 0, stream=None):
+        _require_cuda()
+        P.load()
+        self.grid = grid
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.plan = P.prism_plan_create(grid, hbm_budget_bytes, self.stream)
+        self.info = P.prism_plan_info(self.plan)
+
+    # -- hot path
+    def build(self, V: torch.Tensor):
+        assert V.is_cuda and V.dtype == torch.float32 and V.is_contiguous()
+        assert tuple(V.shape) == (self.grid.n_slices, self.grid.ny, self.grid.nx)
+        self._V = V  # keep alive until the stream has consumed it
+        P.prism_build_smatrix(self.plan, V)
+
+    def build_host(self, V_host: torch.Tensor):
+        assert not V_host.is_cuda and V_host.dtype == torch.float32 and V_host.is_contiguous()
+        P.prism_build_smatrix_host(self.plan, V_host)
+
+    def scan(self, probe, x0, y0, det, out: torch.Tensor | None = None, px=None, py=None):
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        n = len(x0)
+        px = n if px is None else px
+        py = 1 if py is None else py
+        assert px * py == n
+        if out is None:
+            out = torch.empty((n, det.nbins), dtype=torch.float32, device="cuda")
+        P.prism_scan_run(self.plan, probe, P.make_scan(px, py, x0, y0), det, out)
+        return out
+
+    def scan_host(self, probe, x0, y0, det, out_host: torch.Tensor, px=None, py=None):
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        n = len(x0)
+        px = n if px is None else px
+        py = 1 if py is None else py
+        P.prism_scan_run_host(self.plan, probe, P.make_scan(px, py, x0, y0), det, out_host)
+        return out_host
+
+    def sync(self):
+        P.prism_sync(self.plan)
+
+    # -- introspection
+    def beams(self):
+        return P.prism_plan_beams(self.plan)
+
+    def smatrix(self) -> torch.Tensor:
+        """Copy of the S-matrix as complex64 [B][ny_s][nx_s]."""
+        i = self.info
+        v = torch.as_tensor(_CudaView(P.prism_plan_smatrix(self.plan), (i.n_beams, i.ny_s, i.nx_s, 2), "<f4"),
+                            device="cuda")
+        return torch.view_as_complex(v.clone())
+
+    def transmission(self) -> torch.Tensor:
+        g = self.grid
+        v = torch.as_tensor(_CudaView(P.prism_plan_transmission(self.plan), (g.n_slices, g.ny, g.nx, 2), "<f4"),
+                            device="cuda")
+        return torch.view_as_complex(v.clone())
+
+    def set_profiling(self, on=True):
+        P.prism_plan_set_profiling(self.plan, on)
+
+    def kernel_stats(self):
+        return {P.prism_kernel_name(k): P.prism_plan_kernel_stats(self.plan, k) for k in range(P.PRISM_K_COUNT)}
+
+    def launches(self):
+        return P.prism_plan_launches(self.plan)
+
+    def reset_stats(self):
+        P.prism_plan_reset_stats(self.plan)
+
+    def close(self):
+        if getattr(self, "plan", None) is not None:
+            P.prism_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def multislice(grid, V: torch.Tensor, probe, x0, y0, det, stream=None, scratch_bytes=0, out=None, px=None, py=None):
+    """Conventional multislice STEM of every probe position (device result [P][nbins])."""
+    _require_cuda()
+    x0 = np.ascontiguousarray(x0, np.float64)
+    y0 = np.ascontiguousarray(y0, np.float64)
+    n = len(x0)
+    px = n if px is None else px
+    py = 1 if py is None else py
+    if out is None:
+        out = torch.empty((n, det.nbins), dtype=torch.float32, device="cuda")
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    P.multislice_scan_run(grid, V, probe, P.make_scan(px, py, x0, y0), det, out, stream, scratch_bytes)
+    return out

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every entry point the
+header declares, and the ctypes binding matches the header's constants and struct layouts."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1702_01904_gb300 import build as B
+from paper_1702_01904_gb300 import prism as P
+
+HEADER = os.path.join(B.INCLUDE, "prism.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ctypes.CDLL(B.LIB)
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:prism|multislice)_\w+)\s*\(", src)))
+
+
+def test_header_declares_expected_entry_points():
+    names = header_functions()
+    assert "prism_plan_create" in names and "multislice_scan_run" in names
+    assert sorted(P.EXPORTED) == names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_loads_and_sets_signatures(lib):
+    L = P.load()
+    for name in P.EXPORTED:
+        assert getattr(L, name).argtypes is not None or name == "prism_last_error"
+
+
+def test_status_and_kernel_constants_match_header():
+    src = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(PRISM_\w+)\s+(-?\d+)", src))
+    for k, v in defs.items():
+        assert getattr(P, k) == int(v), k
+
+
+def test_struct_layout_matches_c(tmp_path):
+    probe = tmp_path / "layout.c"
+    probe.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "prism.h"
+#define F(s, m) printf(#s "." #m " %zu\\n", offsetof(s, m));
+int main(void) {
+  printf("prism_grid %zu\\n", sizeof(prism_grid));
+  printf("prism_probe %zu\\n", sizeof(prism_probe));
+  printf("prism_scan %zu\\n", sizeof(prism_scan));
+  printf("prism_detector %zu\\n", sizeof(prism_detector));
+  printf("prism_info %zu\\n", sizeof(prism_info));
+  F(prism_grid, cell_x) F(prism_grid, slice_dz) F(prism_grid, kv) F(prism_grid, f) F(prism_grid, aa_frac)
+  F(prism_grid, alpha_max_mrad) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
+  F(prism_info, wavelength) F(prism_info, device_bytes)
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", B.INCLUDE, str(probe), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                check=True).stdout.split("\n") if line)
+    cls = {"prism_grid": P.PrismGrid, "prism_probe": P.PrismProbe, "prism_scan": P.PrismScan,
+           "prism_detector": P.PrismDetector, "prism_info": P.PrismInfo}
+    for k, v in out.items():
+        if "." in k:
+            s, m = k.split(".")
+            assert getattr(cls[s], m).offset == int(v), k
+        else:
+            assert ctypes.sizeof(cls[k]) == int(v), k
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(P, "_lib", None)
+    with pytest.raises(RuntimeError):
+        P.load(str(tmp_path / "nope.so"))
