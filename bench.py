@@ -1,0 +1,418 @@
+"""Benchmark: PRISM STEM simulation on one GB300 (or N independent replicas under torchrun).
+
+A step is one pass of the whole PRISM hot path over one synthetic workload: transmission, the
+compact S-matrix build (multislice of all 129 beams through 50 slices of a 1024^2 grid) and the
+scan of all 200 x 200 probe positions (coefficients, window gather, beam sum, window FFT, bins).
+Inputs (potential slices, probe positions) are resident in HBM when the timed region starts.
+
+Printed (rank 0, one JSON line): probes/s of the PRISM step (value), plain GPU multislice probes/s
+on a probe subset of the same workload, the end-to-end figure through the C ABI with host buffers,
+the roofline of the dominant kernel (CUDA-event timed inside the timed region), the FP64 oracle
+timed on the host cores (cpu_baseline), SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 oracle instead (the only reference implementation: the paper
+ships none), on a bounded sample of the same workload, and prints the same line shape.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STEM probes/s, PRISM vs multislice on one GB300 at ≤1e-3 rel err; p99 latency"
+UNIT = "probes/s"
+DET = dict(start_mrad=0.0, step_mrad=1.0, nbins=100)
+
+
+def workload_config(w, B):
+    return {
+        "workload": f"amorphous carbon 50x50x100 A (25000 Z=6 atoms, seed 1), {w.nx}x{w.ny} grid, "
+                    f"{w.n_slices} slices of {w.dz} A, {w.kv:.0f} kV, {w.alpha_mrad:.0f} mrad, f={w.f}, "
+                    f"{w.scan_px}x{w.scan_py} probes at {w.scan_step} A, {DET['nbins']} x 1 mrad bins",
+        "nx": w.nx, "ny": w.ny, "slices": w.n_slices, "f": w.f, "beams": B,
+        "probes": w.scan_px * w.scan_py, "window_px": w.nx // w.downsample // w.f,
+        "l2": "no flush: inputs larger than L2 (V 210 MB, S-matrix 270 MB, wave stack 1.08 GB vs 129 MB L2)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ oracle timing (CPU)
+def oracle_sample(w, V, budget_s=20.0):
+    """Time the FP64 oracle as it stands on a bounded sample of the workload and extrapolate.
+
+    Sample: one beam of the S-matrix build (one oracle multislice of its plane wave through all
+    slices) and the oracle probe scan of a few probes against a 129-beam S-matrix tiled from that
+    beam (the scan's cost does not depend on the values).  Returns probes/s for the whole workload.
+    """
+    from oracle import prism_oracle as O
+
+    g = dict(nx=w.nx, ny=w.ny, cell_x=w.cell_x, cell_y=w.cell_y, n_slices=w.n_slices, dz=w.dz, kv=w.kv,
+             f=w.f, downsample=w.downsample, aa_frac=w.aa_frac, alpha_mrad=w.alpha_mrad)
+    m, n = O.beam_set(w.nx, w.ny, w.cell_x, w.cell_y, w.kv, w.f, w.alpha_mrad)
+    B = len(m)
+    t0 = time.perf_counter()
+    trans = O.transmission(V, w.kv)
+    prop = O.slice_propagators(g)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pw = O.plane_wave(w.nx, w.ny, w.cell_x, w.cell_y, m[0] * w.f / w.cell_x, n[0] * w.f / w.cell_y)
+    s0 = O.fourier_crop_half(O.multislice(pw, trans, prop))
+    t_beam = time.perf_counter() - t0
+    S = np.broadcast_to(s0, (B,) + s0.shape)
+    x0, y0 = w.scan_positions()
+    n_probe = 0
+    t0 = time.perf_counter()
+    while True:
+        O.prism_scan(S, m, n, g, dict(alpha_mrad=w.alpha_mrad), DET, x0[n_probe:n_probe + 4], y0[n_probe:n_probe + 4])
+        n_probe += 4
+        if time.perf_counter() - t0 > max(1.0, budget_s - t_beam - t_setup) or n_probe >= 400:
+            break
+    t_probe = (time.perf_counter() - t0) / n_probe
+    P = w.scan_px * w.scan_py
+    total = t_setup + B * t_beam + P * t_probe
+    return {
+        "value": P / total, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+        "sample": f"FP64 NumPy oracle: 1 of {B} S-matrix beams ({w.n_slices} slices, {w.nx}^2) in {t_beam:.2f} s, "
+                  f"{n_probe} of {P} probe scans in {t_probe * n_probe:.2f} s, transmission/propagator setup "
+                  f"{t_setup:.2f} s; extrapolated to the full workload ({total:.0f} s). numpy.fft single-threaded, "
+                  f"BLAS contraction with the library's default threads",
+        "seconds_measured": t_setup + t_beam + t_probe * n_probe,
+    }
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1702_01904_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1702_01904_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Bytes per launch from the committed ncu summary, if it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("bytes_per_launch_full")
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ms-probes", type=int, default=1024, help="probes timed for the multislice baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1702_01904_gb300 import specimens
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = specimens.workload_amorphous_carbon()
+        V = w.potential()
+        steps = []
+        last = None
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(w, V, budget_s=8.0 if args.steps > 2 else 15.0)
+            if i >= args.warmup:
+                steps.append(r)
+            last = r
+        val = statistics.median([r["value"] for r in steps]) if steps else last["value"]
+        P = w.scan_px * w.scan_py
+        out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * P / val,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": workload_config(w, 129),
+               "cpu_baseline": {"value": val, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                                "sample": last["sample"]},
+               "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return 0
+
+    import torch
+
+    from paper_1702_01904_gb300 import build as B
+    from paper_1702_01904_gb300 import prism as PR
+    from paper_1702_01904_gb300.runtime import PrismSimulation, multislice
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    B.build()  # no-op once built
+    dev = torch.cuda.current_device()
+
+    w = specimens.workload_amorphous_carbon()
+    V_host = torch.from_numpy(w.potential())
+    V = V_host.cuda()
+    x0, y0 = w.scan_positions()
+    P = len(x0)
+    grid = PR.grid_from_workload(w)
+    det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
+    probe = PR.make_probe(w.alpha_mrad)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        sim = PrismSimulation(grid, 0, stream)
+        Bn = sim.info.n_beams
+        out = torch.empty((P, DET["nbins"]), dtype=torch.float32, device="cuda")
+
+        def step():
+            sim.build(V)
+            sim.scan(probe, x0, y0, det, out=out, px=w.scan_px, py=w.scan_py)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        sim.reset_stats()
+        sim.set_profiling(True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        clocks = ClockSampler(gpu_smi_id(torch, dev))
+        clocks.start()
+        time.sleep(0.3)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clk = clocks.stop()
+        total_ms = evs[0].elapsed_time(evs[-1])
+        per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        sim.set_profiling(False)
+        stats = sim.kernel_stats()
+        launches = sim.launches()
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        V_pin = V_host.pin_memory()
+        out_pin = torch.empty((P, DET["nbins"]), dtype=torch.float32).pin_memory()
+
+        def step_host():
+            sim.build_host(V_pin)
+            sim.scan_host(probe, x0, y0, det, out_pin, px=w.scan_px, py=w.scan_py)
+            sim.sync()
+
+        step_host()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_e2e0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_host()
+        e1.record(stream)
+        stream.synchronize()
+        e2e_ms = (time.perf_counter() - t_e2e0) * 1000.0
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = V_host.numel() * 4 + P * 16
+        d2h = P * DET["nbins"] * 4
+
+        # multislice baseline on a probe subset of the same workload
+        nms = min(args.ms_probes, P)
+        sel = np.linspace(0, P - 1, nms).astype(np.int64)
+        ms_out = torch.empty((nms, DET["nbins"]), dtype=torch.float32, device="cuda")
+        multislice(grid, V, probe, x0[sel][:8], y0[sel][:8], det, stream=stream, out=ms_out[:8])
+        stream.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        multislice(grid, V, probe, x0[sel], y0[sel], det, stream=stream, out=ms_out, scratch_bytes=2 << 30)
+        m1.record(stream)
+        stream.synchronize()
+        ms_ms = m0.elapsed_time(m1)
+        sim.close()
+
+    value = world * P * args.steps / (total_ms / 1000.0)
+    ms_probes_s = nms / (ms_ms / 1000.0)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean event time per launch
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    px = w.nx * w.ny
+    # per-launch algorithmic bytes: wave stack read + write (8 B per complex64 pixel each way) for
+    # all beams, plus the slice's transmission function for the row pass
+    alg = {
+        "row": 2 * Bn * px * 8 + px * 8,
+        "col": 2 * Bn * px * 8,
+        "row_plane": Bn * px * 8 + px * 8,
+        "row_out": Bn * (px // 2) * 8 + Bn * (px // 4) * 8,
+        "transmission": w.n_slices * px * (4 + 8),
+    }
+    rows = {}
+    for name, (n_l, t_ms) in stats.items():
+        if n_l == 0:
+            continue
+        rows[name] = {"launches": n_l, "total_ms": t_ms, "mean_ms": t_ms / n_l}
+    dominant = max(rows, key=lambda k: rows[k]["total_ms"])
+    roof_all = {}
+    for name, r in rows.items():
+        if name in alg:
+            gbs = alg[name] / (r["mean_ms"] / 1000.0) / 1e9
+            roof_all[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": gbs / hbm_peak, "bytes_per_launch": alg[name], **r}
+        elif name == "scan":
+            # ALU-bound: 8 flops per complex MAC of the beam sum (a7) + window FFTs
+            nw = w.nx // w.downsample // w.f
+            flops = P * (8.0 * Bn * nw * nw + 2 * 5.0 * nw * nw * math.log2(nw))
+            clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            peak_tf = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+            tf = flops / (r["mean_ms"] / 1000.0) / 1e12
+            roof_all[name] = {"bound": "alu", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                              "frac": tf / peak_tf, "flops_per_launch": flops, **r}
+    dom = dominant if dominant in roof_all else max(roof_all, key=lambda k: roof_all[k]["total_ms"])
+    rd = roof_all[dom]
+    roofline = {"bound": rd["bound"], "achieved": rd["achieved"], "peak": rd["peak"], "unit": rd["unit"],
+                "frac": rd["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
+                "peak_source": f"{peak_note} ({'MEASURED_PEAKS.json hbm_gbs' if rd['unit'] == 'GB/s' else '152 SMs x 128 FP32 lanes x 2 x median SM clock'})"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, V_host.numpy(), budget_s=20.0)
+        cpu.pop("seconds_measured", None)
+
+    if rank == 0:
+        build_ms = sum(rows[k]["total_ms"] for k in rows if k != "scan") / args.steps
+        scan_ms = rows.get("scan", {}).get("total_ms", 0.0) / args.steps
+        lat = sorted(per_step)
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded amorphous-carbon phantom; the paper's Pt/a-C coordinates are not available)",
+            "config": {**workload_config(w, Bn), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": world * P * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "prism_build_smatrix_host + prism_scan_run_host, pinned host buffers, wall clock"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "roofline_all": roof_all,
+            "cpu_baseline": cpu,
+            "multislice": {"probes_per_s": ms_probes_s, "probes_timed": nms, "ms": ms_ms,
+                           "speedup_prism_vs_multislice": value / world / ms_probes_s},
+            "beams_slices_per_s": Bn * w.n_slices / (build_ms / 1000.0),
+            "phase_ms_per_step": {"s_matrix_build": build_ms, "scan": scan_ms},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+            "clocks": clk,
+        }
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

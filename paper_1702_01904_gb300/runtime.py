@@ -15,7 +15,7 @@ class _CudaView:
     """Expose a device pointer owned by the library as a zero-copy torch tensor."""
 
     def __init__(self, ptr, shape, typestr):
-        self.__cuda_array_interface__ = {"data": (int(ptr), True), "shape": tuple(shape),
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
                                          "typestr": typestr, "version": 3}
 
 
@@ -75,13 +75,16 @@ class PrismSimulation:
         return P.prism_plan_beams(self.plan)
 
     def smatrix(self) -> torch.Tensor:
-        """Copy of the S-matrix as complex64 [B][ny_s][nx_s]."""
+        """Copy of the S-matrix as complex64 [B][ny_s][nx_s] (waits for the plan's stream)."""
+        self.sync()
         i = self.info
         v = torch.as_tensor(_CudaView(P.prism_plan_smatrix(self.plan), (i.n_beams, i.ny_s, i.nx_s, 2), "<f4"),
                             device="cuda")
         return torch.view_as_complex(v.clone())
 
     def transmission(self) -> torch.Tensor:
+        """Copy of the transmission functions complex64 [H][ny][nx] (waits for the plan's stream)."""
+        self.sync()
         g = self.grid
         v = torch.as_tensor(_CudaView(P.prism_plan_transmission(self.plan), (g.n_slices, g.ny, g.nx, 2), "<f4"),
                             device="cuda")

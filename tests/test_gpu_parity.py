@@ -255,9 +255,11 @@ def test_carbon_workload_sampled(carbon_workload):
     sel = [0, 20101, 39999]
     ref = np.array([O.prism_probe_direct(V, g, dict(alpha_mrad=w.alpha_mrad), DET, x0[i], y0[i]) for i in sel])
     assert_images_close(out[sel], ref)
-    # every probe's intensity is a fraction of the incident one
+    # the binned intensity of every probe is the incident one up to the crop approximation of PRISM
+    # (the d/f window is not norm-preserving for the exit wave; the oracle shows the same excess)
     tot = out.sum(1)
-    assert np.all(tot > 0.5) and np.all(tot < 1.0 + 1e-4)
+    assert np.all(tot > 0.98) and np.all(tot < 1.01)
+    assert np.max(np.abs(tot[sel] - ref.sum(1))) < 1e-5
     sim.close()
 
 
