@@ -175,6 +175,28 @@ def ncu_traffic(kernel):
     return None if k is None else k.get("bytes_per_launch_full")
 
 
+def ncu_case():
+    import torch
+
+    from paper_1702_01904_gb300 import prism as PR
+    from paper_1702_01904_gb300 import specimens
+    from paper_1702_01904_gb300.runtime import PrismSimulation
+
+    w = specimens.workload_amorphous_carbon(n_slices=4, alpha_mrad=9.0)
+    V = torch.from_numpy(w.potential()).cuda()
+    x0, y0 = w.scan_positions()
+    sim = PrismSimulation(PR.grid_from_workload(w))
+    det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
+    probe = PR.make_probe(w.alpha_mrad)
+    for _ in range(2):  # launches per pass: transmission, 4 x (row, col), row_out, scan
+        sim.build(V)
+        sim.scan(probe, x0[:2000], y0[:2000], det)
+    sim.sync()
+    print(json.dumps({"ncu_case": "ok", "beams": sim.info.n_beams, "launches": sim.launches()}))
+    sim.close()
+    return 0
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -184,7 +206,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ms-probes", type=int, default=1024, help="probes timed for the multislice baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run the profiling case twice and exit: the same 1024^2 a-C grid, 4 slices, "
+                         "alpha_max 9 mrad (25 beams, 200 MB wave stack), 2000 probes")
     args = ap.parse_args()
+    if args.ncu_case:
+        return ncu_case()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
