@@ -167,6 +167,32 @@ int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_
                         const prism_scan *scan, const prism_detector *det, float *out_dev,
                         void *cuda_stream, size_t scratch_bytes);
 
+/* ---- fixed-scratch multislice ------------------------------------------------------ */
+
+/* Size of the library's fixed device scratch array used by multislice_scan_run_noalloc. */
+#define PRISM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Multislice STEM scan that allocates no device memory.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory themselves, e.g. a host application that
+ * owns the whole device-memory budget through its own pool and forbids other allocations, or a
+ * latency-critical loop in which cudaMalloc / cudaFree (which may synchronise the device) are not
+ * allowed.  It computes the same result as multislice_scan_run (same kernels, same arguments,
+ * same output layout, bitwise-identical output) and calls no cudaMalloc, cudaFree or allocating
+ * library routine; its transmission functions, wave and intensity buffers and tables live in one
+ * file-scope device array of PRISM_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the
+ * library holds until the process exits.  The caller still provides V_dev and out_dev.
+ * Limits: the grid must fit the array with at least one probe in flight, about
+ * nx*ny*(8*n_slices + 24) bytes plus 16 bytes per probe position (e.g. 256^2 with up to ~28
+ * slices); larger requests return PRISM_ERR_BUDGET with the required size in prism_last_error().
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls share the array and
+ * every call overwrites what it uses, so calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race: serialise them on one stream.  Asynchronous like
+ * multislice_scan_run: synchronise `cuda_stream` before reading out_dev. */
+int multislice_scan_run_noalloc(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
+                                const prism_scan *scan, const prism_detector *det, float *out_dev,
+                                void *cuda_stream);
+
 /* ---- introspection (tests, tools) ----------------------------------------------- */
 
 int prism_plan_info(const prism_plan *plan, prism_info *out);

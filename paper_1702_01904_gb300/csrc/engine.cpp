@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "internal.h"
 #include "params.h"
 
 namespace prism {
@@ -945,3 +946,60 @@ extern "C" int prism_plan_reset_stats(prism_plan *P) {
     P->launches = 0;
     return PRISM_OK;
 }
+
+// ------------------------------------------------------------------ helpers for the fixed-scratch entry point
+namespace prism {
+
+int internal_fail(int code, const char *msg) { return fail(code, msg); }
+
+int internal_check_dev_ptr(const void *p, size_t align, const char *what) { return check_dev_ptr(p, align, what); }
+
+int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe, const prism_scan *sc,
+                               const prism_detector *det, MsHostTables *out) {
+    int rc;
+    if ((rc = check_grid_common(grid))) return rc;
+    if ((rc = check_probe(probe))) return rc;
+    if ((rc = check_det(det))) return rc;
+    const prism_grid &g = *grid;
+    if ((rc = check_scan(sc, g.cell_x / g.nx * (double)(1 << 28), g.cell_y / g.ny * (double)(1 << 28)))) return rc;
+    GridTables T;
+    if ((rc = build_grid_tables(&g, T))) return rc;
+    MsHostTables &M = *out;
+    M.nx = g.nx;
+    M.ny = g.ny;
+    M.H = g.n_slices;
+    M.lam = T.lam;
+    M.sigma = T.sigma;
+    M.slice_prop = T.slice_prop;
+    M.prop_x = T.prop_x;
+    M.prop_y = T.prop_y;
+    M.aa_kmax = T.aa_kmax;
+    M.twr_f = T.twr_f;
+    M.twr_i = T.twr_i;
+    M.twc_f = T.twc_f;
+    M.twc_i = T.twc_i;
+    const size_t px = (size_t)g.nx * g.ny;
+    M.pbase.assign(px, make_float2(0.f, 0.f));
+    M.count = 0;
+    for (int ky = 0; ky < g.ny; ++ky) {
+        const double qy = (double)signed_index(ky, g.ny) / g.cell_y;
+        for (int kx = 0; kx < g.nx; ++kx) {
+            const double qx = (double)signed_index(kx, g.nx) / g.cell_x;
+            if (inside_aperture(qx, qy, T.lam, probe->alpha_mrad * 1e-3)) {
+                M.pbase[(size_t)ky * g.nx + kx] = phase_cycles(chi_cycles(qx * qx + qy * qy, T.lam, probe->c1, probe->c3));
+                M.count += 1.0;
+            }
+        }
+    }
+    detector_csr(g.nx, g.ny, g.cell_x, g.cell_y, 1, T.lam, det, M.bin_off, M.bin_idx);
+    const long long Pn = (long long)sc->px * sc->py;
+    M.pos.resize((size_t)Pn * 2);
+    if (Pn > 0) {
+        std::memcpy(M.pos.data(), sc->x0, Pn * sizeof(double));
+        std::memcpy(M.pos.data() + Pn, sc->y0, Pn * sizeof(double));
+    }
+    M.tw = make_tw64();
+    return PRISM_OK;
+}
+
+}  // namespace prism

@@ -30,7 +30,7 @@ PRISM_K_COUNT = 6
 EXPORTED = [
     "prism_plan_create", "prism_plan_destroy", "prism_sync", "prism_last_error",
     "prism_build_smatrix", "prism_build_smatrix_host", "prism_scan_run", "prism_scan_run_host",
-    "multislice_scan_run", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
+    "multislice_scan_run", "multislice_scan_run_noalloc", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
     "prism_plan_smatrix", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         "prism_scan_run_host": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
         "multislice_scan_run": (c_int, [POINTER(PrismGrid), P, POINTER(PrismProbe), POINTER(PrismScan),
                                         POINTER(PrismDetector), P, P, c_size_t]),
+        "multislice_scan_run_noalloc": (c_int, [POINTER(PrismGrid), P, POINTER(PrismProbe), POINTER(PrismScan),
+                                                POINTER(PrismDetector), P, P]),
         "prism_plan_info": (c_int, [P, POINTER(PrismInfo)]),
         "prism_plan_smatrix_bytes": (c_int, [P, POINTER(c_size_t)]),
         "prism_plan_beams": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int]),
@@ -208,6 +210,16 @@ def prism_scan_run_host(plan, probe, scan, det, out_host):
 def multislice_scan_run(grid, V_dev, probe, scan, det, out_dev, cuda_stream=None, scratch_bytes=0):
     return _check(load().multislice_scan_run(byref(grid), _ptr(V_dev), byref(probe), byref(scan), byref(det),
                                              _ptr(out_dev), _stream(cuda_stream), scratch_bytes))
+
+
+def multislice_scan_run_noalloc(grid, V_dev, probe, scan, det, out_dev, cuda_stream=None):
+    """Same as multislice_scan_run, using the library's fixed 16 MiB device scratch instead of
+    allocating (for callers that may not allocate device memory; see include/prism.h)."""
+    return _check(load().multislice_scan_run_noalloc(byref(grid), _ptr(V_dev), byref(probe), byref(scan),
+                                                     byref(det), _ptr(out_dev), _stream(cuda_stream)))
+
+
+PRISM_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def prism_plan_info(plan):
