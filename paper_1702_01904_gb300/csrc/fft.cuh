@@ -178,8 +178,9 @@ struct FftShape {
 };
 
 // Two-level transform of length N = N1*N2 over T threads.  `stw` is the inter-stage twiddle
-// table laid out [k1][n2] = W_N^{n2 k1} (forward sign; the inverse conjugates it).  `Ex` is the
-// exchange: write(k1, n2, v), read(k1, n2), sync().
+// table laid out [k1][n2] = W_N^{n2 k1} (forward sign; the inverse conjugates it); kernels keep
+// it in shared memory (lanes read consecutive n2: conflict-free).  `Ex` is the exchange:
+// write(k1, n2, v), read(k1, n2), sync().
 template <int N1, int N2, bool INV>
 struct BlockFft {
     static constexpr int N = N1 * N2;
@@ -188,23 +189,48 @@ struct BlockFft {
     static constexpr int J = E / N1;
     static constexpr int I = E / N2;
 
-    template <class Ex>
+    // GTW: the twiddle table is in global memory (read through the read-only path); otherwise it
+    // is in shared memory
+    template <class Ex, bool GTW = false>
     __device__ __forceinline__ static void run(float2 (&x)[E], int t, const float2 *__restrict__ stw,
                                                const Tw64 &tw, Ex &ex) {
 #pragma unroll
         for (int j = 0; j < J; ++j) Dft<N1, J, INV>::run(x + j, tw);
-        ex.sync();  // previous readers of the exchange are done
+        if constexpr (!GTW) {
+            // shared-memory table: all twiddle loads before any exchange store (the table and the
+            // exchange share the address space, and this order lets the loads issue back to back)
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int n2 = t + T * j;
+            for (int j = 0; j < J; ++j) {
+                const int n2 = t + T * j;
 #pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) {
-                float2 v = x[k1 * J + j];
-                if (k1 != 0) {
-                    const float2 w = __ldg(stw + k1 * N2 + n2);
-                    v = INV ? cmulc(v, w) : cmul(v, w);
+                for (int k1 = 1; k1 < N1; ++k1) {
+                    const float2 w = stw[k1 * N2 + n2];
+                    x[k1 * J + j] = INV ? cmulc(x[k1 * J + j], w) : cmul(x[k1 * J + j], w);
                 }
-                ex.write(k1, n2, v);
+            }
+            ex.sync();  // previous readers of the exchange are done
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int n2 = t + T * j;
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) ex.write(k1, n2, x[k1 * J + j]);
+            }
+        } else {
+            // global table (read-only path, L1-resident): interleave load, multiply and store, which
+            // keeps register pressure at the level of one element
+            ex.sync();
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int n2 = t + T * j;
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    float2 v = x[k1 * J + j];
+                    if (k1 != 0) {
+                        const float2 w = __ldg(stw + k1 * N2 + n2);
+                        v = INV ? cmulc(v, w) : cmul(v, w);
+                    }
+                    ex.write(k1, n2, v);
+                }
             }
         }
         ex.sync();
@@ -239,14 +265,24 @@ struct WarpExchange {
     static constexpr int kFloats2 = N1 * (N2 + 1);
 };
 
-// Exchange for W interleaved columns handled by a whole CTA: layout [k1][n2][c].
+// Exchange for W interleaved columns handled by a whole CTA: layout [k1][n2][c], each k1 block
+// padded by W float2 so that the thread groups of a warp reading consecutive k1 in stage 2 fall on
+// different banks.  Size: N1 * (N2 + 1) * W float2.
 template <int N1, int N2, int W>
 struct ColExchange {
     float2 *buf;
     int c;
-    __device__ __forceinline__ void write(int k1, int n2, float2 v) { buf[(k1 * N2 + n2) * W + c] = v; }
-    __device__ __forceinline__ float2 read(int k1, int n2) const { return buf[(k1 * N2 + n2) * W + c]; }
+    __device__ __forceinline__ void write(int k1, int n2, float2 v) { buf[(k1 * (N2 + 1) + n2) * W + c] = v; }
+    __device__ __forceinline__ float2 read(int k1, int n2) const { return buf[(k1 * (N2 + 1) + n2) * W + c]; }
     __device__ __forceinline__ void sync() { __syncthreads(); }
+    static constexpr int kFloats2 = N1 * (N2 + 1) * W;
+};
+
+// float2 count of a column exchange serving both the forward and the inverse split of length N
+template <int N, int W>
+struct ColExSize {
+    static constexpr int a = FftShape<N>::N1, b = FftShape<N>::N2;
+    static constexpr int value = (a * (b + 1) > b * (a + 1) ? a * (b + 1) : b * (a + 1)) * W;
 };
 
 }  // namespace prism

@@ -24,10 +24,10 @@ struct ScanCfg {
     static constexpr int RSLOTS = BLOCK / T;          // window rows transformed at once
     static constexpr int CW = BLOCK / T;              // window columns transformed at once
     static constexpr int EXR = RSLOTS * FS::N1 * (FS::N2 + 1);
-    static constexpr int EXC = NW * CW;
+    static constexpr int EXC = FS::N1 * (FS::N2 + 1) * CW;
     static constexpr int EX = EXR > EXC ? EXR : EXC;
     static_assert(2 * EX >= NW * NW, "exchange region doubles as the intensity buffer");
-    static constexpr size_t SMEM_FIXED = (size_t)(NW * NW + EX) * sizeof(float2);
+    static constexpr size_t SMEM_FIXED = (size_t)(NW * NW + EX + NW) * sizeof(float2);
 };
 
 template <int NW>
@@ -39,10 +39,12 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
     extern __shared__ float2 smem[];
     float2 *win = smem;                 // [NW][NW]
     float2 *ex = win + NW * NW;         // exchange, later |Psi|^2 as float
-    float2 *alpha = ex + C::EX;         // [n_beams]
+    float2 *twf = ex + C::EX;           // window FFT stage twiddles [NW]
+    float2 *alpha = twf + NW;           // [n_beams]
     const int tid = threadIdx.x;
     const int p = a.probe0 + blockIdx.x;
     if (p >= a.n_probes) return;
+    for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
     const double x0 = a.x0[p], y0 = a.y0[p];
 
     // 1. coefficients
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
             float2 v[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = win[rr * NW + Fwd::in_elem(r, t)];
-            Fwd::run(v, t, a.tw_fwd, a.tw, exr);
+            Fwd::run(v, t, twf, a.tw, exr);
             if (row < NW) {
 #pragma unroll
                 for (int r = 0; r < E; ++r) win[rr * NW + Fwd::out_elem(r, t)] = v[r];
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
             float2 v[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = win[Fwd::in_elem(r, t) * NW + cc];
-            Fwd::run(v, t, a.tw_fwd, a.tw, exc);
+            Fwd::run(v, t, twf, a.tw, exc);
             __syncthreads();  // all reads of win for this pass done before any write
             if (col < NW) {
 #pragma unroll
@@ -133,12 +135,12 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     for (int k = warp; k < a.nbins; k += BLOCK / 32) {
-        double s = 0.0;
+        float s = 0.f;
         const int e = __ldg(a.bin_off + k + 1);
-        for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) s += (double)inten[__ldg(a.bin_idx + i)];
+        for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) s += inten[__ldg(a.bin_idx + i)];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) a.out[(size_t)p * a.nbins + k] = (float)(s * a.inv_norm);
+        if (lane == 0) a.out[(size_t)p * a.nbins + k] = (float)((double)s * a.inv_norm);
     }
 }
 
@@ -154,12 +156,292 @@ static cudaError_t scan_dispatch(const ScanArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------ grouped scan
+// G consecutive probes share one CTA.  Adjacent probes of a raster are a few stored pixels apart,
+// so their windows overlap: per beam, the union tile of the group's windows is staged once in
+// shared memory (a STAGES-deep cp.async pipeline of 16-byte pixel pairs keeps the next beams in
+// flight while one is summed) and every thread owns tile pixels, so one shared-memory load feeds
+// the complex MACs of all G probes.  A group whose windows do not fit the tile is processed one
+// probe at a time.
+template <int NW>
+struct GroupCfg {
+    using FS = FftShape<NW>;
+    static constexpr int G = 4;
+    static constexpr int D = 16;                              // tile may exceed a window by D pixels
+    static constexpr int BLOCK = NW >= 64 ? 512 : NW >= 16 ? 256 : 64;
+    static constexpr int MAXTILE = NW * (NW + D);             // tile pixels
+    static constexpr int PIX = (MAXTILE + BLOCK - 1) / BLOCK; // tile pixels per thread
+    static constexpr int PAIRS = (MAXTILE / 2 + BLOCK - 1) / BLOCK;  // 16-byte copies per thread
+    static constexpr int PW = NW + 8;                         // window row pitch (bank spread)
+    static constexpr int T = FS::T;
+    static constexpr int RSLOTS = BLOCK / T;
+    static constexpr int CW = BLOCK / T;
+    static constexpr int EXR = RSLOTS * FS::N1 * (FS::N2 + 1);
+    static constexpr int EXC = FS::N1 * (FS::N2 + 1) * CW;
+    static constexpr int EX = EXR > EXC ? EXR : EXC;
+    static constexpr int STAGES = 4;                          // cp.async pipeline depth (beams in flight)
+    static constexpr int BIG = (STAGES * MAXTILE > G * NW * PW) ? STAGES * MAXTILE : G * NW * PW;
+    static constexpr size_t SMEM_FIXED = (size_t)(BIG + EX + NW) * sizeof(float2) + 64 * sizeof(int);
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Sum over one warp of per-lane FP32 partial sums, fixed xor-shuffle tree (every lane gets the
+// total).  Pairwise: relative error <= (terms per lane + 5) * 2^-24 for non-negative terms.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __grid_constant__ ScanArgs a) {
+    using C = GroupCfg<NW>;
+    using FS = FftShape<NW>;
+    using Fwd = FwdFft<NW>;
+    constexpr int BLOCK = C::BLOCK, PIX = C::PIX, G = C::G, T = C::T, E = FS::E, PW = C::PW;
+    extern __shared__ float2 smem[];
+    float2 *big = smem;                    // staging tiles [STAGES][MAXTILE], later windows [G][NW][PW]
+    float2 *ex = big + C::BIG;             // FFT exchange
+    float2 *twf = ex + C::EX;              // window FFT stage twiddles [NW]
+    int *meta = reinterpret_cast<int *>(twf + NW);  // group geometry
+    float2 *alpha = reinterpret_cast<float2 *>(meta + 64);  // [G][n_beams]
+    const int tid = threadIdx.x;
+    const int p0 = a.probe0 + blockIdx.x * G;
+    if (p0 >= a.n_probes) return;
+    const int gn = min(G, a.n_probes - p0);
+    for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
+
+    // coefficients of the group's probes
+    for (int i = tid; i < G * a.n_beams; i += BLOCK) {
+        const int p = i / a.n_beams, b = i - p * a.n_beams;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < gn) {
+            double c = a.qx[b] * a.x0[p0 + p] + a.qy[b] * a.y0[p0 + p];
+            c -= rint(c);
+            float s, co;
+            sincospif(-2.0f * (float)c, &s, &co);
+            v = cmul(__ldg(a.base + b), make_float2(co, s));
+        }
+        alpha[i] = v;
+    }
+    // window origins (FP64, Eq. RegionBounds) and the union tile relative to probe 0; the tile
+    // starts on an even column and has an even width so that pixel pairs are 16-byte aligned
+    if (tid == 0) {
+        int sx[G], sy[G];
+        for (int p = 0; p < gn; ++p) {
+            sx[p] = ((int)floor(a.x0[p0 + p] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
+            sy[p] = ((int)floor(a.y0[p0 + p] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
+        }
+        int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0, dx[G], dy[G];
+        for (int p = 0; p < gn; ++p) {
+            dx[p] = ((sx[p] - sx[0] + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2;
+            dy[p] = ((sy[p] - sy[0] + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2;
+            dxmin = min(dxmin, dx[p]);
+            dxmax = max(dxmax, dx[p]);
+            dymin = min(dymin, dy[p]);
+            dymax = max(dymax, dy[p]);
+        }
+        const int tx0 = (sx[0] + dxmin) & (a.nx_s - 1);
+        const int shift = tx0 & 1;                       // extra leading column to reach an even origin
+        const int tw = (dxmax - dxmin + NW + shift + 1) & ~1;
+        const int th = dymax - dymin + NW;
+        const bool fits = tw <= NW + C::D && th <= NW + C::D && tw * th <= C::MAXTILE;
+        meta[0] = fits ? 1 : gn;  // number of sub-groups
+        for (int p = 0; p < G; ++p) {
+            meta[8 + p] = sx[p < gn ? p : 0];
+            meta[16 + p] = sy[p < gn ? p : 0];
+            meta[24 + p] = p < gn ? dx[p] - dxmin + shift : 0;
+            meta[32 + p] = p < gn ? dy[p] - dymin : 0;
+        }
+        meta[1] = tw;
+        meta[2] = th;
+        meta[3] = tx0 - shift;
+        meta[4] = (sy[0] + dymin) & (a.ny_s - 1);
+    }
+    __syncthreads();
+    const int nsub = meta[0];
+    const size_t bstride = (size_t)a.ny_s * a.nx_s;
+
+    for (int sg = 0; sg < nsub; ++sg) {
+        // geometry of this sub-group: all gn probes (tile = union), or probe sg alone (its window,
+        // widened by one column on the left if it starts on an odd column)
+        const bool all = nsub == 1;
+        int tw, th, tx0, ty0, ox1 = 0;
+        if (all) {
+            tw = meta[1];
+            th = meta[2];
+            tx0 = meta[3];
+            ty0 = meta[4];
+        } else {
+            ox1 = meta[8 + sg] & 1;
+            tw = NW + 2 * ox1;
+            th = NW;
+            tx0 = meta[8 + sg] - ox1;
+            ty0 = meta[16 + sg];
+        }
+        const int npx = tw * th;
+        const int hw = tw >> 1;  // pixel pairs per tile row
+        // global offsets of this thread's pixel pairs (fixed for all beams)
+        int off[C::PAIRS];
+#pragma unroll
+        for (int k = 0; k < C::PAIRS; ++k) {
+            const int q = tid + k * BLOCK;
+            const int ty = q / hw, tp = q - ty * hw;
+            off[k] = q < (npx >> 1) ? ((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + 2 * tp) & (a.nx_s - 1)) : -1;
+        }
+        const float2 *al = alpha + (all ? 0 : sg * a.n_beams);
+        float2 acc[PIX][G];
+#pragma unroll
+        for (int k = 0; k < PIX; ++k)
+#pragma unroll
+            for (int p = 0; p < G; ++p) acc[k][p] = make_float2(0.f, 0.f);
+
+        // beam loop: STAGES-1 beam tiles in flight while one is summed; one barrier per beam
+        // (after it every thread is done with the previous tile, whose buffer is then refilled)
+        constexpr int S = C::STAGES;
+        auto stage = [&](int b) {
+            if (b < a.n_beams) {
+                const float2 *Sb = a.S + (size_t)b * bstride;
+                float2 *buf = big + (b % S) * C::MAXTILE;
+#pragma unroll
+                for (int k = 0; k < C::PAIRS; ++k)
+                    if (off[k] >= 0) cp_async16(buf + 2 * (tid + k * BLOCK), Sb + off[k]);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int b = 0; b < S - 1; ++b) stage(b);
+        for (int b = 0; b < a.n_beams; ++b) {
+            cp_async_wait<S - 2>();
+            __syncthreads();
+            stage(b + S - 1);
+            const float2 *cur = big + (b % S) * C::MAXTILE;
+            float2 av[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) av[p] = al[(all ? p : 0) * a.n_beams + b];
+            float2 sv[PIX];
+#pragma unroll
+            for (int k = 0; k < PIX; ++k) sv[k] = cur[tid + k * BLOCK];
+#pragma unroll
+            for (int k = 0; k < PIX; ++k)
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    acc[k][p].x = fmaf(av[p].x, sv[k].x, fmaf(-av[p].y, sv[k].y, acc[k][p].x));
+                    acc[k][p].y = fmaf(av[p].x, sv[k].y, fmaf(av[p].y, sv[k].x, acc[k][p].y));
+                }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        // scatter the accumulators into the windows: tile pixel (ty, tx) is pixel
+        // (ty - oy_p, tx - ox_p) of probe p's window
+        float2 *win = big;
+#pragma unroll
+        for (int k = 0; k < PIX; ++k) {
+            const int i = tid + k * BLOCK;
+            const int ty = i / tw, tx = i - ty * tw;
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+                const bool act = all ? p < gn : p == 0;
+                const int wy = ty - (all ? meta[32 + p] : 0), wx = tx - (all ? meta[24 + p] : ox1);
+                if (act && i < npx && wy >= 0 && wy < NW && wx >= 0 && wx < NW) win[(p * NW + wy) * PW + wx] = acc[k][p];
+            }
+        }
+        __syncthreads();
+        const int nwin = all ? gn : 1;
+
+        // window FFTs: rows of all windows, then columns
+        {
+            const int slot = tid / T, t = tid % T;
+            WarpExchange<FS::N1, FS::N2, T> exr{ex + slot * (FS::N1 * (FS::N2 + 1))};
+#pragma unroll 1
+            for (int r0 = 0; r0 < G * NW; r0 += C::RSLOTS) {
+                const int row = r0 + slot;
+                const bool ok = row < nwin * NW;
+                const int rr = ok ? row : row % NW;
+                float2 v[E];
+#pragma unroll
+                for (int r = 0; r < E; ++r) v[r] = win[rr * PW + Fwd::in_elem(r, t)];
+                Fwd::run(v, t, twf, a.tw, exr);
+                if (ok) {
+#pragma unroll
+                    for (int r = 0; r < E; ++r) win[rr * PW + Fwd::out_elem(r, t)] = v[r];
+                }
+            }
+        }
+        __syncthreads();
+        {
+            const int c = tid % C::CW, t = tid / C::CW;
+            ColExchange<FS::N1, FS::N2, C::CW> exc{ex, c};
+#pragma unroll 1
+            for (int c0 = 0; c0 < G * NW; c0 += C::CW) {
+                const int col = c0 + c;
+                const bool ok = col < nwin * NW;
+                const int cc = ok ? col : col % NW;
+                float2 *w = win + (cc / NW) * NW * PW;
+                const int x = cc % NW;
+                float2 v[E];
+#pragma unroll
+                for (int r = 0; r < E; ++r) v[r] = w[Fwd::in_elem(r, t) * PW + x];
+                Fwd::run(v, t, twf, a.tw, exc);
+                __syncthreads();
+                if (ok) {
+#pragma unroll
+                    for (int r = 0; r < E; ++r) w[Fwd::out_elem(r, t) * PW + x] = v[r];
+                }
+            }
+        }
+        __syncthreads();
+        // |Psi|^2 and bins: one warp per (probe, bin); FP32 pairwise sums, FP64 scale
+        const int warp = tid >> 5, lane = tid & 31;
+        constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
+        for (int j = warp; j < nwin * a.nbins; j += BLOCK / 32) {
+            const int p = j / a.nbins, k = j - p * a.nbins;
+            const float2 *w = win + p * NW * PW;
+            float sum = 0.f;
+            const int e = __ldg(a.bin_off + k + 1);
+            for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) {
+                const int u = __ldg(a.bin_idx + i);
+                const float2 z = w[(u >> LNW) * PW + (u & (NW - 1))];
+                sum += z.x * z.x + z.y * z.y;
+            }
+            sum = warp_sum(sum);
+            if (lane == 0) a.out[(size_t)(p0 + (all ? p : sg)) * a.nbins + k] = (float)((double)sum * a.inv_norm);
+        }
+        __syncthreads();  // windows and staging buffers are reused by the next sub-group
+    }
+}
+
+template <int NW>
+static cudaError_t scan_grouped_dispatch(const ScanArgs &a, cudaStream_t s) {
+    using C = GroupCfg<NW>;
+    const int n = a.n_probes - a.probe0;
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = C::SMEM_FIXED + (size_t)C::G * a.n_beams * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_scan_grouped<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_scan_grouped<NW><<<(n + C::G - 1) / C::G, C::BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NW>
+static bool grouped_fits(int n_beams) {
+    return GroupCfg<NW>::SMEM_FIXED + (size_t)GroupCfg<NW>::G * n_beams * sizeof(float2) <= 227 * 1024;
+}
+
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s) {
     switch (nw) {
-        case 8: return scan_dispatch<8>(a, s);
-        case 16: return scan_dispatch<16>(a, s);
-        case 32: return scan_dispatch<32>(a, s);
-        case 64: return scan_dispatch<64>(a, s);
+        case 8: return grouped_fits<8>(a.n_beams) ? scan_grouped_dispatch<8>(a, s) : scan_dispatch<8>(a, s);
+        case 16: return grouped_fits<16>(a.n_beams) ? scan_grouped_dispatch<16>(a, s) : scan_dispatch<16>(a, s);
+        case 32: return grouped_fits<32>(a.n_beams) ? scan_grouped_dispatch<32>(a, s) : scan_dispatch<32>(a, s);
+        case 64: return grouped_fits<64>(a.n_beams) ? scan_grouped_dispatch<64>(a, s) : scan_dispatch<64>(a, s);
         case 128: return scan_dispatch<128>(a, s);
         default: return cudaErrorInvalidValue;
     }
