@@ -215,28 +215,29 @@ static int build_grid_tables(const prism_grid *g, GridTables &T) {
             T.prop_y.push_back(make_float2((float)(w.x * inv), (float)(w.y * inv)));
         }
     }
-    // anti-aliasing aperture |q| < aa_frac * q_nyquist, as a per-row bound on |kx|
+    // anti-aliasing aperture |q| < aa_frac * q_nyquist, as a per-column bound on |ky| (the column
+    // pass applies it along each column kx)
     const double q_nyq = std::min(0.5 * T.nx / g->cell_x, 0.5 * T.ny / g->cell_y);
     T.q_aa = g->aa_frac * q_nyq;
     const double qaa2 = T.q_aa * T.q_aa;
-    T.aa_kmax.assign(T.ny, -1);
-    for (int ky = 0; ky < T.ny; ++ky) {
-        const double qy = (double)signed_index(ky, T.ny) / g->cell_y;
+    T.aa_kmax.assign(T.nx, -1);
+    for (int kx = 0; kx < T.nx; ++kx) {
+        const double qx = (double)signed_index(kx, T.nx) / g->cell_x;
         int kmax = -1;
-        for (int kx = 0; kx < T.nx; ++kx) {
-            const int ks = signed_index(kx, T.nx);
-            const double qx = (double)ks / g->cell_x;
+        for (int ky = 0; ky < T.ny; ++ky) {
+            const int ks = signed_index(ky, T.ny);
+            const double qy = (double)ks / g->cell_y;
             const bool in = qx * qx + qy * qy < qaa2;
             if (in) kmax = std::max(kmax, std::abs(ks));
         }
-        // the mask must be the symmetric interval |kx| <= kmax
-        for (int kx = 0; kx < T.nx; ++kx) {
-            const int ks = signed_index(kx, T.nx);
-            const double qx = (double)ks / g->cell_x;
+        // the mask must be the symmetric interval |ky| <= kmax
+        for (int ky = 0; ky < T.ny; ++ky) {
+            const int ks = signed_index(ky, T.ny);
+            const double qy = (double)ks / g->cell_y;
             const bool in = qx * qx + qy * qy < qaa2;
             if (in != (std::abs(ks) <= kmax)) return fail(PRISM_ERR_INVALID, "anti-aliasing mask is not a symmetric interval");
         }
-        T.aa_kmax[ky] = kmax;
+        T.aa_kmax[kx] = kmax;
     }
     int a1, a2;
     fft_split(T.nx, &a1, &a2);

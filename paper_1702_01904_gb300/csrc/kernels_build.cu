@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k_col(c
         int b, kx0;
         locate(tile, b, kx0);
         const int kx = kx0 + c;
+
         float2 *col = a.wave + (size_t)b * NY * a.nx + kx;
         float2 v[E];
         if constexpr (MODE == COL_PROBE) {
@@ -386,14 +387,16 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k_col(c
                 for (int r = 0; r < E; ++r) v[r] = col[(size_t)Fwd::in_elem(r, t) * a.nx];
             }
             Fwd::template run<decltype(exF), !C::SMEM_TW>(v, t, twf, a.tw, exF);
-            // Fresnel propagator exp(-i pi lambda t |q|^2) (separable) inside the anti-aliasing aperture
-            const int kxs = kx < (a.nx >> 1) ? kx : kx - a.nx;
-            const int akx = kxs < 0 ? -kxs : kxs;
+            // Fresnel propagator exp(-i pi lambda t |q|^2) (separable) inside the anti-aliasing
+            // aperture, which on column kx is |ky| <= aa_kmax[kx]
             const float2 px = __ldg(a.prop_x + kx);
+            const int kymax = __ldg(a.aa_kmax + kx);
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const int ky = Fwd::out_elem(r, t);
-                v[r] = (akx <= __ldg(a.aa_kmax + ky)) ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
+                const int kys = ky < (NY >> 1) ? ky : ky - NY;
+                const int aky = kys < 0 ? -kys : kys;
+                v[r] = aky <= kymax ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
             }
             if constexpr (MODE == COL_DETECT) {
                 if (valid) {

@@ -38,7 +38,7 @@ struct ColArgs {
     float *inten;              // DETECT: [batch][ny][nx] |Psi|^2 (scaled later)
     const float2 *prop_x;      // [nx]  exp(-i pi lambda dz qx^2)
     const float2 *prop_y;      // [ny]  exp(-i pi lambda dz qy^2) / (nx ny)
-    const int *aa_kmax;        // [ny]  largest |kx| inside the AA aperture on row ky, -1 if none
+    const int *aa_kmax;        // [nx]  largest |ky| inside the AA aperture on column kx, -1 if none
     const float2 *tw_fwd;
     const float2 *tw_inv;
     const float2 *probe_base;  // PROBE: [ny][nx] A(q) exp(-i chi(q))
