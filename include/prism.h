@@ -75,14 +75,18 @@ typedef struct prism_grid {
 } prism_grid;
 
 /* Probe: aperture semi-angle (A(q) = 1 where lambda|q| <= alpha), defocus C1 and spherical
- * aberration C3 (Angstrom) in chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3.
- * tilt_x/tilt_y (rad) must be 0 in this version (PRISM_ERR_UNSUPPORTED otherwise). */
+ * aberration C3 (Angstrom) in chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3, and tilt
+ * (rad, |tilt| <= 0.5).  A tilted probe has its aperture and chi centred on q_t = tilt / lambda
+ * and its coefficients evaluated at r0 - h tan(tilt), h = cell thickness, which brings it back to
+ * the centre of the cut-out region (PRISM Algorithm section); the beam set must reach |tilt| +
+ * alpha (alpha_max_mrad of the grid), else the probe is truncated to the beams present. */
 typedef struct prism_probe {
     double alpha_mrad, c1, c3, tilt_x, tilt_y;
 } prism_probe;
 
 /* Scan: px * py probe positions (Angstrom), host arrays x0[py*px], y0[py*px], row-major [py][px].
- * Positions may lie anywhere; windows wrap periodically (Eq. RegionBounds). px*py may be 0. */
+ * Positions may lie anywhere; windows wrap periodically (Eq. RegionBounds). px*py may be 0.
+ * The arrays are read before the call returns. */
 typedef struct prism_scan {
     int px, py;
     const double *x0;
@@ -156,6 +160,18 @@ int prism_scan_run(prism_plan *plan, const prism_probe *probe, const prism_scan 
  * (asynchronous for pinned memory: read it after prism_sync). */
 int prism_scan_run_host(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
                         const prism_detector *det, float *out_host);
+
+/* Full diffraction patterns instead of annular bins (Fig. 1f, "full probe diffraction pattern";
+ * 4D-STEM): out_dev float32 [py][px][nw_y][nw_x], |FFT(window)|^2 in units of the incident
+ * intensity, window frequencies in FFT order (index k <-> q = k f / cell for k < nw/2, k - nw
+ * above).  Same requirements and asynchrony as prism_scan_run. */
+int prism_scan_run_cbed(prism_plan *plan, const prism_probe *probe, const prism_scan *scan, float *out_dev);
+
+/* Accumulating scan: out_dev[p][k] += weight * I[p][k] (in place; out_dev must hold the running
+ * sum).  Frozen-phonon averaging (Simulation and Analysis Implementation section) is one
+ * prism_build_smatrix per displaced-atom configuration followed by this call with weight 1/n. */
+int prism_scan_run_accumulate(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
+                              const prism_detector *det, float weight, float *out_dev);
 
 /* Conventional multislice STEM (Multislice section, Eq. Multislice) of every probe: the probe
  * A(q) exp(-i chi) exp(-2 pi i q.r0) on the full grid, H slices, far-field |Psi|^2 divided by

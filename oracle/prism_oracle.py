@@ -200,16 +200,36 @@ def chi(q2, lam, c1, c3):
     return math.pi * lam * q2 * c1 + 0.5 * math.pi * lam ** 3 * q2 * q2 * c3
 
 
+def cell_height(grid):
+    """Total thickness h of the simulation cell (sum of the slice thicknesses)."""
+    dzs = grid.get("slice_dz")
+    return float(grid["dz"]) * grid["n_slices"] if dzs is None else float(np.sum(dzs))
+
+
+def tilt_terms(grid, probe):
+    """Probe tilt (PRISM Algorithm section): the aperture and chi are centred on q_t = theta / lambda
+    (the probe centre moved away from q = 0), and the coefficients use r0 - h tan(theta), which
+    brings the tilted probe back to the centre of the cut-out region at the exit surface."""
+    lam = wavelength(grid["kv"])
+    tx, ty = probe.get("tilt_x", 0.0), probe.get("tilt_y", 0.0)
+    h = cell_height(grid)
+    return tx / lam, ty / lam, h * math.tan(tx), h * math.tan(ty)
+
+
 def probe_coefficients(m, n, grid, probe, x0, y0):
-    """alpha_mn(r0) = A(q) exp(-i chi(q)) exp(-2 pi i q.r0)  (PRISM Algorithm section; tilt 0)."""
+    """alpha_mn(r0) = A(q - q_t) exp(-i chi(q - q_t)) exp(-2 pi i q.(r0 - h tan theta))
+    (PRISM Algorithm section, coefficients and tilt)."""
     lam = wavelength(grid["kv"])
     f = grid["f"]
+    qtx, qty, sx, sy = tilt_terms(grid, probe)
     qx = (m * f).astype(np.float64) / grid["cell_x"]
     qy = (n * f).astype(np.float64) / grid["cell_y"]
-    a = inside_aperture(qx, qy, lam, probe["alpha_mrad"] * 1e-3)
-    q2 = qx * qx + qy * qy
+    dqx = qx - qtx
+    dqy = qy - qty
+    a = inside_aperture(dqx, dqy, lam, probe["alpha_mrad"] * 1e-3)
+    q2 = dqx * dqx + dqy * dqy
     return a * np.exp(-1j * chi(q2, lam, probe.get("c1", 0.0), probe.get("c3", 0.0))) \
-        * np.exp(-2j * math.pi * (qx * x0 + qy * y0))
+        * np.exp(-2j * math.pi * (qx * (x0 - sx) + qy * (y0 - sy)))
 
 
 def window_origin(x0, cell, n_ds, nw):
@@ -270,6 +290,36 @@ def prism_scan(S, m, n, grid, probe, det, x0s, y0s, full_window=False):
     return out
 
 
+def prism_cbed(S, m, n, grid, probe, x0s, y0s):
+    """Full diffraction pattern of each probe's window (Fig. 1f, "full probe diffraction pattern"):
+    |FFT_Nw(psi)|^2 in units of the incident intensity, window frequencies in FFT order.
+    Returns [P][nw_y][nw_x] float64."""
+    nb, nyd, nxd = S.shape
+    f = grid["f"]
+    nwx, nwy = nxd // f, nyd // f
+    out = np.zeros((len(x0s), nwy, nwx))
+    for p in range(len(x0s)):
+        a = probe_coefficients(m, n, grid, probe, x0s[p], y0s[p])
+        sx = window_origin(x0s[p], grid["cell_x"], nxd, nwx)
+        sy = window_origin(y0s[p], grid["cell_y"], nyd, nwy)
+        win = S[:, ((sy + np.arange(nwy)) % nyd)[:, None], ((sx + np.arange(nwx)) % nxd)[None, :]]
+        psi = np.tensordot(a, win, axes=(0, 0))
+        norm = float(np.sum(np.abs(a) ** 2))
+        out[p] = np.abs(fft2(psi)) ** 2 / ((nwx * nwy) ** 2 * norm) if norm > 0 else 0.0
+    return out
+
+
+def frozen_phonon_scan(v_configs, grid, probe, det, x0s, y0s):
+    """Frozen-phonon average (Simulation and Analysis Implementation section): the PRISM result of
+    each displaced-atom configuration, summed incoherently with equal weights."""
+    acc = None
+    for v in v_configs:
+        S, m, n = smatrix_build(v, grid)
+        r = prism_scan(S, m, n, grid, probe, det, x0s, y0s)
+        acc = r if acc is None else acc + r
+    return acc / len(v_configs)
+
+
 def prism_probe_direct(v_slices, grid, probe, det, x0, y0):
     """One PRISM probe by linearity of Eq. PRISMfinal, without the S-matrix.
 
@@ -299,13 +349,17 @@ def prism_probe_direct(v_slices, grid, probe, det, x0, y0):
 
 # ------------------------------------------------------- multislice baseline
 def probe_spectrum(grid, probe, x0, y0):
-    """Psi0(q) = A(q) exp(-i chi(q)) exp(-2 pi i q.r0) on the full Fourier grid."""
+    """Psi0(q) = A(q - q_t) exp(-i chi(q - q_t)) exp(-2 pi i q.(r0 - h tan theta)) on the full
+    Fourier grid (the same probe definition as the PRISM coefficients)."""
     lam = wavelength(grid["kv"])
+    qtx, qty, sx, sy = tilt_terms(grid, probe)
     qx, qy = freq_grid(grid["nx"], grid["ny"], grid["cell_x"], grid["cell_y"])
-    a = inside_aperture(qx, qy, lam, probe["alpha_mrad"] * 1e-3)
-    q2 = qx * qx + qy * qy
+    dqx = qx - qtx
+    dqy = qy - qty
+    a = inside_aperture(dqx, dqy, lam, probe["alpha_mrad"] * 1e-3)
+    q2 = dqx * dqx + dqy * dqy
     return a * np.exp(-1j * chi(q2, lam, probe.get("c1", 0.0), probe.get("c3", 0.0))) \
-        * np.exp(-2j * math.pi * (qx * x0 + qy * y0))
+        * np.exp(-2j * math.pi * (qx * (x0 - sx) + qy * (y0 - sy)))
 
 
 def multislice_probe(v_slices, grid, probe, det, x0, y0, trans=None, props=None):

@@ -286,7 +286,8 @@ static int check_probe(const prism_probe *pr) {
     if (!pr) return fail(PRISM_ERR_INVALID, "probe is NULL");
     if (!(pr->alpha_mrad >= 0) || !std::isfinite(pr->alpha_mrad) || !std::isfinite(pr->c1) || !std::isfinite(pr->c3))
         return fail(PRISM_ERR_INVALID, "probe parameters must be finite, alpha >= 0");
-    if (pr->tilt_x != 0.0 || pr->tilt_y != 0.0) return fail(PRISM_ERR_UNSUPPORTED, "probe tilt is not supported");
+    if (!std::isfinite(pr->tilt_x) || !std::isfinite(pr->tilt_y) || std::fabs(pr->tilt_x) > 0.5 || std::fabs(pr->tilt_y) > 0.5)
+        return fail(PRISM_ERR_INVALID, "probe tilt must be finite and below 0.5 rad");
     return PRISM_OK;
 }
 
@@ -313,6 +314,17 @@ static bool inside_aperture(double qx, double qy, double lam, double alpha_rad) 
 static double chi_cycles(double q2, double lam, double c1, double c3) {
     const double chi = PI * lam * q2 * c1 + 0.5 * PI * lam * lam * lam * q2 * q2 * c3;
     return chi / (2.0 * PI);
+}
+
+// Probe tilt (PRISM Algorithm section): aperture and chi centred on q_t = theta / lambda, and the
+// coefficients evaluated at r0 - h tan(theta) with h the cell thickness.
+struct Tilt {
+    double qtx, qty, sx, sy;
+};
+static Tilt tilt_terms(const prism_probe *pr, double lam, const std::vector<double> &dz) {
+    double h = 0;
+    for (double d : dz) h += d;
+    return {pr->tilt_x / lam, pr->tilt_y / lam, h * std::tan(pr->tilt_x), h * std::tan(pr->tilt_y)};
 }
 
 // ------------------------------------------------------------------ plan
@@ -624,20 +636,23 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
                         ScanArgs &a) {
     int rc;
     if ((rc = check_probe(probe))) return rc;
-    if ((rc = check_det(det))) return rc;
+    if (det && (rc = check_det(det))) return rc;
     const double pxs = P->g.cell_x / P->nxs, pys = P->g.cell_y / P->nys;
     if ((rc = check_scan(sc, pxs * (double)(1 << 28), pys * (double)(1 << 28)))) return rc;
     if (!P->built) return fail(PRISM_ERR_INVALID, "S-matrix not built");
     const int B = P->nbeams;
     const double lam = P->T.lam;
-    // A(q_b) exp(-i chi(q_b)) and sum_b A_b
+    const Tilt tl = tilt_terms(probe, lam, P->T.dz);
+    // A(q_b - q_t) exp(-i chi(q_b - q_t)) and sum_b A_b
     std::vector<float2> base(B);
     double count = 0;
     for (int b = 0; b < B; ++b) {
         const double qx = (double)(P->bm[b] * P->g.f) / P->g.cell_x;
         const double qy = (double)(P->bn[b] * P->g.f) / P->g.cell_y;
-        if (inside_aperture(qx, qy, lam, probe->alpha_mrad * 1e-3)) {
-            base[b] = phase_cycles(chi_cycles(qx * qx + qy * qy, lam, probe->c1, probe->c3));
+        const double dqx = qx - tl.qtx;
+        const double dqy = qy - tl.qty;
+        if (inside_aperture(dqx, dqy, lam, probe->alpha_mrad * 1e-3)) {
+            base[b] = phase_cycles(chi_cycles(dqx * dqx + dqy * dqy, lam, probe->c1, probe->c3));
             count += 1.0;
         } else {
             base[b] = make_float2(0.f, 0.f);
@@ -654,7 +669,7 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     }
     CUDA_TRY(cudaMemcpyAsync(P->base, base.data(), B * sizeof(float2), cudaMemcpyHostToDevice, P->stream));
     // window bin map (q = k f / cell on the window grid), cached per detector
-    if (P->det_nbins != det->nbins || P->det_key[0] != det->start_mrad || P->det_key[1] != det->step_mrad) {
+    if (det && (P->det_nbins != det->nbins || P->det_key[0] != det->start_mrad || P->det_key[1] != det->step_mrad)) {
         std::vector<int> off, idx;
         detector_csr(P->nw, P->nw, P->g.cell_x, P->g.cell_y, P->g.f, lam, det, off, idx);
         std::vector<int> all(off);
@@ -673,16 +688,18 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     a.qy = P->beam_q + B;
     a.base = P->base;
     a.tw_fwd = P->tww_f;
-    a.bin_off = P->bin_buf;
-    a.bin_idx = P->bin_buf + det->nbins + 1;
+    a.bin_off = det ? P->bin_buf : nullptr;
+    a.bin_idx = det ? P->bin_buf + det->nbins + 1 : nullptr;
     a.px_s = pxs;
     a.py_s = pys;
+    a.shift_x = tl.sx;
+    a.shift_y = tl.sy;
     const double nw2 = (double)P->nw * (double)P->nw;
     a.inv_norm = count > 0 ? 1.0 / (nw2 * nw2 * count) : 0.0;
     a.n_beams = B;
     a.nx_s = P->nxs;
     a.ny_s = P->nys;
-    a.nbins = det->nbins;
+    a.nbins = det ? det->nbins : 0;
     a.n_probes = (int)Pn;
     a.probe0 = 0;
     a.tw = P->tw64;
@@ -718,6 +735,33 @@ extern "C" int prism_scan_run_host(prism_plan *P, const prism_probe *probe, cons
     return PRISM_OK;
 }
 
+extern "C" int prism_scan_run_cbed(prism_plan *P, const prism_probe *probe, const prism_scan *sc, float *out_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    ScanArgs a;
+    int rc = scan_prepare(P, probe, sc, nullptr, a);
+    if (rc) return rc;
+    if (a.n_probes == 0) return PRISM_OK;
+    if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
+    a.out = nullptr;
+    a.cbed = out_dev;
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+}
+
+extern "C" int prism_scan_run_accumulate(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
+                                         const prism_detector *det, float weight, float *out_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    if (!std::isfinite(weight)) return fail(PRISM_ERR_INVALID, "weight must be finite");
+    ScanArgs a;
+    int rc = scan_prepare(P, probe, sc, det, a);
+    if (rc) return rc;
+    if (a.n_probes == 0) return PRISM_OK;
+    if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
+    a.out = out_dev;
+    a.accumulate = 1;
+    a.acc_w = weight;
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+}
+
 // ------------------------------------------------------------------ multislice baseline
 extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
                                    const prism_scan *sc, const prism_detector *det, float *out_dev,
@@ -737,15 +781,18 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
     if ((rc = build_grid_tables(&g, T))) return rc;
     const int nx = g.nx, ny = g.ny;
     const size_t px = (size_t)nx * ny;
-    // probe A(q) exp(-i chi(q)) on the full grid, sum |Psi0|^2 = aperture pixel count
+    // probe A(q - q_t) exp(-i chi(q - q_t)) on the full grid, sum |Psi0|^2 = aperture pixel count
+    const Tilt tl = tilt_terms(probe, T.lam, T.dz);
     std::vector<float2> pbase(px);
     double count = 0;
     for (int ky = 0; ky < ny; ++ky) {
         const double qy = (double)signed_index(ky, ny) / g.cell_y;
         for (int kx = 0; kx < nx; ++kx) {
             const double qx = (double)signed_index(kx, nx) / g.cell_x;
-            if (inside_aperture(qx, qy, T.lam, probe->alpha_mrad * 1e-3)) {
-                pbase[(size_t)ky * nx + kx] = phase_cycles(chi_cycles(qx * qx + qy * qy, T.lam, probe->c1, probe->c3));
+            const double dqx = qx - tl.qtx;
+            const double dqy = qy - tl.qty;
+            if (inside_aperture(dqx, dqy, T.lam, probe->alpha_mrad * 1e-3)) {
+                pbase[(size_t)ky * nx + kx] = phase_cycles(chi_cycles(dqx * dqx + dqy * dqy, T.lam, probe->c1, probe->c3));
                 count += 1.0;
             } else {
                 pbase[(size_t)ky * nx + kx] = make_float2(0.f, 0.f);
@@ -786,9 +833,12 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
     if ((rc = A.upload(&d_idx, idx))) return done(rc);
     if ((rc = A.alloc((void **)&pos, (size_t)Pn * 2 * sizeof(double)))) return done(rc);
     {
+        // the probe phase uses r0 - h tan(theta) (zero without tilt)
         std::vector<double> xy((size_t)Pn * 2);
-        std::memcpy(xy.data(), sc->x0, Pn * sizeof(double));
-        std::memcpy(xy.data() + Pn, sc->y0, Pn * sizeof(double));
+        for (long long i = 0; i < Pn; ++i) {
+            xy[i] = sc->x0[i] - tl.sx;
+            xy[Pn + i] = sc->y0[i] - tl.sy;
+        }
         cudaError_t e = cudaMemcpyAsync(pos, xy.data(), xy.size() * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
             fail(PRISM_ERR_CUDA, std::string("position upload: ") + cudaGetErrorString(e));
@@ -980,14 +1030,17 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
     M.twc_f = T.twc_f;
     M.twc_i = T.twc_i;
     const size_t px = (size_t)g.nx * g.ny;
+    const Tilt tl = tilt_terms(probe, T.lam, T.dz);
     M.pbase.assign(px, make_float2(0.f, 0.f));
     M.count = 0;
     for (int ky = 0; ky < g.ny; ++ky) {
         const double qy = (double)signed_index(ky, g.ny) / g.cell_y;
         for (int kx = 0; kx < g.nx; ++kx) {
             const double qx = (double)signed_index(kx, g.nx) / g.cell_x;
-            if (inside_aperture(qx, qy, T.lam, probe->alpha_mrad * 1e-3)) {
-                M.pbase[(size_t)ky * g.nx + kx] = phase_cycles(chi_cycles(qx * qx + qy * qy, T.lam, probe->c1, probe->c3));
+            const double dqx = qx - tl.qtx;
+            const double dqy = qy - tl.qty;
+            if (inside_aperture(dqx, dqy, T.lam, probe->alpha_mrad * 1e-3)) {
+                M.pbase[(size_t)ky * g.nx + kx] = phase_cycles(chi_cycles(dqx * dqx + dqy * dqy, T.lam, probe->c1, probe->c3));
                 M.count += 1.0;
             }
         }
@@ -995,9 +1048,9 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
     detector_csr(g.nx, g.ny, g.cell_x, g.cell_y, 1, T.lam, det, M.bin_off, M.bin_idx);
     const long long Pn = (long long)sc->px * sc->py;
     M.pos.resize((size_t)Pn * 2);
-    if (Pn > 0) {
-        std::memcpy(M.pos.data(), sc->x0, Pn * sizeof(double));
-        std::memcpy(M.pos.data() + Pn, sc->y0, Pn * sizeof(double));
+    for (long long i = 0; i < Pn; ++i) {
+        M.pos[i] = sc->x0[i] - tl.sx;
+        M.pos[Pn + i] = sc->y0[i] - tl.sy;
     }
     M.tw = make_tw64();
     return PRISM_OK;

@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
     for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
     const double x0 = a.x0[p], y0 = a.y0[p];
 
-    // 1. coefficients
+    // 1. coefficients (a tilted probe uses r0 - h tan(theta))
     for (int b = tid; b < a.n_beams; b += BLOCK) {
-        double c = a.qx[b] * x0 + a.qy[b] * y0;
+        double c = a.qx[b] * (x0 - a.shift_x) + a.qy[b] * (y0 - a.shift_y);
         c -= rint(c);
         float s, co;
         sincospif(-2.0f * (float)c, &s, &co);
@@ -125,14 +125,18 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
     }
     __syncthreads();
 
-    // 5. |Psi|^2 and annular bins
+    // 5. |Psi|^2 (full pattern if requested) and annular bins
     float *inten = reinterpret_cast<float *>(ex);
+    const float fnorm = (float)a.inv_norm;
 #pragma unroll
     for (int k = 0; k < PIX; ++k) {
         const float2 z = win[tid + k * BLOCK];
-        inten[tid + k * BLOCK] = z.x * z.x + z.y * z.y;
+        const float i2 = z.x * z.x + z.y * z.y;
+        inten[tid + k * BLOCK] = i2;
+        if (a.cbed) a.cbed[(size_t)p * NW * NW + tid + k * BLOCK] = i2 * fnorm;
     }
     __syncthreads();
+    if (!a.out) return;
     const int warp = tid >> 5, lane = tid & 31;
     for (int k = warp; k < a.nbins; k += BLOCK / 32) {
         float s = 0.f;
@@ -140,7 +144,11 @@ __global__ void __launch_bounds__(ScanCfg<NW>::BLOCK) k_scan(const __grid_consta
         for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) s += inten[__ldg(a.bin_idx + i)];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) a.out[(size_t)p * a.nbins + k] = (float)((double)s * a.inv_norm);
+        if (lane == 0) {
+            const float val = (float)((double)s * a.inv_norm);
+            float *o = a.out + (size_t)p * a.nbins + k;
+            *o = a.accumulate ? *o + a.acc_w * val : val;
+        }
     }
 }
 
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
         const int p = i / a.n_beams, b = i - p * a.n_beams;
         float2 v = make_float2(0.f, 0.f);
         if (p < gn) {
-            double c = a.qx[b] * a.x0[p0 + p] + a.qy[b] * a.y0[p0 + p];
+            double c = a.qx[b] * (a.x0[p0 + p] - a.shift_x) + a.qy[b] * (a.y0[p0 + p] - a.shift_y);
             c -= rint(c);
             float s, co;
             sincospif(-2.0f * (float)c, &s, &co);
@@ -399,10 +407,19 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
             }
         }
         __syncthreads();
+        constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
+        // full diffraction patterns, if requested
+        if (a.cbed) {
+            const float fnorm = (float)a.inv_norm;
+            for (int i = tid; i < nwin * NW * NW; i += BLOCK) {
+                const int p = i >> (2 * LNW), u = i & (NW * NW - 1);
+                const float2 z = win[(p * NW + (u >> LNW)) * PW + (u & (NW - 1))];
+                a.cbed[(size_t)(p0 + (all ? p : sg)) * NW * NW + u] = (z.x * z.x + z.y * z.y) * fnorm;
+            }
+        }
         // |Psi|^2 and bins: one warp per (probe, bin); FP32 pairwise sums, FP64 scale
         const int warp = tid >> 5, lane = tid & 31;
-        constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
-        for (int j = warp; j < nwin * a.nbins; j += BLOCK / 32) {
+        for (int j = (a.out ? warp : nwin * a.nbins); j < nwin * a.nbins; j += BLOCK / 32) {
             const int p = j / a.nbins, k = j - p * a.nbins;
             const float2 *w = win + p * NW * PW;
             float sum = 0.f;
@@ -413,7 +430,11 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
                 sum += z.x * z.x + z.y * z.y;
             }
             sum = warp_sum(sum);
-            if (lane == 0) a.out[(size_t)(p0 + (all ? p : sg)) * a.nbins + k] = (float)((double)sum * a.inv_norm);
+            if (lane == 0) {
+                const float val = (float)((double)sum * a.inv_norm);
+                float *o = a.out + (size_t)(p0 + (all ? p : sg)) * a.nbins + k;
+                *o = a.accumulate ? *o + a.acc_w * val : val;
+            }
         }
         __syncthreads();  // windows and staging buffers are reused by the next sub-group
     }

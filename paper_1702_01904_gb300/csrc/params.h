@@ -62,8 +62,12 @@ struct ScanArgs {
     const float2 *tw_inv;      // (unused by the forward-only window FFT; kept for symmetry)
     const int *bin_off;        // [nbins+1] CSR offsets into bin_idx
     const int *bin_idx;        // window pixel indices (ky*nw + kx) grouped by bin
-    float *out;                // [P][nbins]
+    float *out;                // [P][nbins] annular bins, or NULL
+    float *cbed;               // [P][nw][nw] full window diffraction patterns (FFT order), or NULL
+    float acc_w;               // accumulate: out += acc_w * I (else out = I)
+    int accumulate;
     double px_s, py_s;         // stored pixel size
+    double shift_x, shift_y;   // h tan(theta): the coefficients use r0 - shift (probe tilt)
     double inv_norm;           // 1 / (nw^4 * sum_b A_b)
     int n_beams;
     int nx_s, ny_s;

@@ -30,6 +30,7 @@ PRISM_K_COUNT = 6
 EXPORTED = [
     "prism_plan_create", "prism_plan_destroy", "prism_sync", "prism_last_error",
     "prism_build_smatrix", "prism_build_smatrix_host", "prism_scan_run", "prism_scan_run_host",
+    "prism_scan_run_cbed", "prism_scan_run_accumulate",
     "multislice_scan_run", "multislice_scan_run_noalloc", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
     "prism_plan_smatrix", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
@@ -90,6 +91,9 @@ def load(path: str = LIB_PATH):
         "prism_build_smatrix_host": (c_int, [P, P]),
         "prism_scan_run": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
         "prism_scan_run_host": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
+        "prism_scan_run_cbed": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), P]),
+        "prism_scan_run_accumulate": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector),
+                                              ctypes.c_float, P]),
         "multislice_scan_run": (c_int, [POINTER(PrismGrid), P, POINTER(PrismProbe), POINTER(PrismScan),
                                         POINTER(PrismDetector), P, P, c_size_t]),
         "multislice_scan_run_noalloc": (c_int, [POINTER(PrismGrid), P, POINTER(PrismProbe), POINTER(PrismScan),
@@ -205,6 +209,20 @@ def prism_scan_run(plan, probe, scan, det, out_dev):
 
 def prism_scan_run_host(plan, probe, scan, det, out_host):
     return _check(load().prism_scan_run_host(plan, byref(probe), byref(scan), byref(det), _ptr(out_host)))
+
+
+def prism_scan_run_cbed(plan, probe, scan, out_dev):
+    return _check(load().prism_scan_run_cbed(plan, byref(probe), byref(scan), _ptr(out_dev)))
+
+
+def prism_scan_run_accumulate(plan, probe, scan, det, weight, out_dev):
+    return _check(load().prism_scan_run_accumulate(plan, byref(probe), byref(scan), byref(det), weight, _ptr(out_dev)))
+
+
+def recommended_alpha_max(probe_alpha_mrad, f, cell, kv, tilt_mrad=0.0):
+    """alpha_max = largest probe semi-angle + f * lambda * dq (PRISM Algorithm section), plus any
+    probe tilt, in mrad: the beam set that keeps the whole (tilted) aperture."""
+    return probe_alpha_mrad + abs(tilt_mrad) + 1000.0 * prism_wavelength(kv) * f / cell
 
 
 def multislice_scan_run(grid, V_dev, probe, scan, det, out_dev, cuda_stream=None, scratch_bytes=0):

@@ -67,6 +67,24 @@ class PrismSimulation:
         P.prism_scan_run_host(self.plan, probe, P.make_scan(px, py, x0, y0), det, out_host)
         return out_host
 
+    def scan_cbed(self, probe, x0, y0, out: torch.Tensor | None = None):
+        """Full window diffraction patterns [P][nw][nw] (FFT order), units of incident intensity."""
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        n = len(x0)
+        nw = self.info.nw_x
+        if out is None:
+            out = torch.empty((n, self.info.nw_y, nw), dtype=torch.float32, device="cuda")
+        P.prism_scan_run_cbed(self.plan, probe, P.make_scan(n, 1, x0, y0), out)
+        return out
+
+    def scan_accumulate(self, probe, x0, y0, det, weight, out: torch.Tensor):
+        """out += weight * (annular bins of this S-matrix), e.g. frozen-phonon averaging."""
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        P.prism_scan_run_accumulate(self.plan, probe, P.make_scan(len(x0), 1, x0, y0), det, weight, out)
+        return out
+
     def sync(self):
         P.prism_sync(self.plan)
 

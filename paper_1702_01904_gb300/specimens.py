@@ -248,3 +248,11 @@ def workload_nanoparticle(f=4, **over) -> Workload:
 
 def potential_stats(v: np.ndarray) -> dict:
     return {"min": float(v.min()), "max": float(v.max()), "mean": float(v.mean())}
+
+
+def displaced(spec: Specimen, u_rms: float, seed: int) -> Specimen:
+    """One frozen-phonon configuration: every atom moved by an independent Gaussian displacement of
+    standard deviation ``u_rms`` (Angstrom) along x, y and z.  PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xyz = spec.xyz + rng.normal(scale=u_rms, size=spec.xyz.shape)
+    return Specimen(xyz, spec.z_number.copy(), spec.cell, note=spec.note + f" displaced u_rms={u_rms} seed={seed}")

@@ -338,7 +338,7 @@ def test_error_codes():
     assert code(lambda: P.prism_scan_run(plan, P.make_probe(20.0), sc, P.make_detector(0, 1, 10), out)) == P.PRISM_ERR_INVALID
     V0 = torch.zeros((1, 64, 64), device="cuda")
     P.prism_build_smatrix(plan, V0)
-    assert code(lambda: P.prism_scan_run(plan, P.make_probe(20.0, tilt_x=0.01), sc, P.make_detector(0, 1, 10), out)) == P.PRISM_ERR_UNSUPPORTED
+    assert code(lambda: P.prism_scan_run(plan, P.make_probe(20.0, tilt_x=0.9), sc, P.make_detector(0, 1, 10), out)) == P.PRISM_ERR_INVALID
     assert code(lambda: P.prism_scan_run(plan, P.make_probe(20.0), sc, P.make_detector(0, 1, 0), out)) == P.PRISM_ERR_INVALID
     bad = P.make_scan(1, 1, [float("nan")], [0.0])
     assert code(lambda: P.prism_scan_run(plan, P.make_probe(20.0), bad, P.make_detector(0, 1, 10), out)) == P.PRISM_ERR_INVALID

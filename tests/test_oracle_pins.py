@@ -394,3 +394,85 @@ def test_defocus_minus_thickness_refocuses_at_exit():
     psi1 = O.ifft2(O.probe_spectrum(g, dict(alpha_mrad=20.0, c1=z, c3=0.0), x0, y0))
     out1 = O.multislice(psi1, t, O.propagator(64, 64, 8.0, 8.0, 300.0, 12.5))
     assert np.max(np.abs(out1 - focused)) > 1e-3
+
+
+# ------------------------------------------------------------------ probe tilt, CBED, frozen phonons
+def test_tilted_empty_sample_counts_shifted_aperture():
+    # a tilted probe is the aperture disc centred on q_t = theta / lambda; with V = 0 each of its
+    # pixels keeps its intensity and lands in the bin of its own |q| (lattice-point count)
+    g = small_grid(n=64, cell=8.0, H=3)
+    lam = O.wavelength(300.0)
+    probe = dict(alpha_mrad=12.0, c1=0.0, c3=0.0, tilt_x=0.015, tilt_y=-0.008)
+    out = O.multislice_probe(np.zeros((3, 64, 64), np.float32), g, probe, DET, 2.5, 1.0)
+    counts = np.zeros(DET["nbins"])
+    total = 0
+    for ky in range(-32, 32):
+        for kx in range(-32, 32):
+            dx, dy = kx / 8.0 - 0.015 / lam, ky / 8.0 + 0.008 / lam
+            if (lam * dx) ** 2 + (lam * dy) ** 2 <= 0.012 ** 2 * (1 + 1e-12):
+                total += 1
+                counts[int(1000 * lam * math.sqrt(kx * kx + ky * ky) / 8.0)] += 1
+    assert total > 10
+    assert np.max(np.abs(out - counts / total)) < 1e-12
+
+
+def test_tilt_shift_recentres_exit_probe():
+    # coefficients at r0 - h tan(theta): the tilted probe walks h*theta through the cell and exits
+    # centred on r0 (to O(theta^3)); dropping the shift would leave it h tan(theta) away
+    # (256^2 over 24 A: anti-aliasing cutoff 52 mrad, above the 45 mrad reached by the tilted aperture)
+    g = small_grid(n=256, cell=24.0, H=5, dz=20.0)
+    h = 100.0
+    th = 0.02
+    probe = dict(alpha_mrad=25.0, c1=0.0, c3=0.0, tilt_x=th, tilt_y=0.0)
+    x0, y0 = 12.0, 12.0
+    psi = O.ifft2(O.probe_spectrum(g, probe, x0, y0))
+    x = np.arange(256) * (24.0 / 256)
+    inten = np.abs(psi) ** 2
+    assert abs(float(np.sum(inten * x[None, :]) / inten.sum()) - (x0 - h * math.tan(th))) < 0.1
+    psi = O.multislice(psi, np.ones((5, 256, 256), complex), O.propagator(256, 256, 24.0, 24.0, 300.0, 20.0))
+    inten = np.abs(psi) ** 2
+    cx = float(np.sum(inten * x[None, :]) / inten.sum())
+    cy = float(np.sum(inten * x[:, None]) / inten.sum())
+    assert abs(cx - x0) < 0.1 and abs(cy - y0) < 0.1  # Airy tails in a periodic box bias the centroid slightly
+    assert abs(h * math.tan(th) - 2.0) < 0.01  # the shift being tested is 2 A
+
+
+def test_prism_f1_equals_multislice_with_tilt_and_aberrations():
+    g = small_grid(n=64, cell=6.4, H=3, f=1, ds=2, alpha=28.0)
+    v = rand_potential(g, 12)
+    probe = dict(alpha_mrad=18.0, c1=40.0, c3=1.0e4, tilt_x=0.006, tilt_y=0.004)
+    S, m, n = O.smatrix_build(v, g)
+    xs, ys = np.array([0.3, 4.1]), np.array([5.5, 2.0])
+    pr = O.prism_scan(S, m, n, g, probe, DET, xs, ys)
+    ms = O.multislice_scan(v, g, probe, DET, xs, ys)
+    assert np.max(np.abs(pr - ms)) < 1e-12
+
+
+def test_cbed_empty_sample_one_pixel_per_beam_and_bins_consistent():
+    g = small_grid(n=64, cell=8.0, H=2, f=2)
+    S, m, n = O.smatrix_build(np.zeros((2, 64, 64), np.float32), g)
+    cb = O.prism_cbed(S, m, n, g, PROBE, np.array([1.1]), np.array([6.3]))[0]
+    ref = np.zeros((16, 16))
+    for b in range(len(m)):
+        ref[n[b] % 16, m[b] % 16] = 1.0 / len(m)
+    assert np.max(np.abs(cb - ref)) < 1e-12
+    v = rand_potential(g, 13)
+    S, m, n = O.smatrix_build(v, g)
+    xs, ys = np.array([0.7, 3.9]), np.array([2.2, 7.1])
+    cb = O.prism_cbed(S, m, n, g, PROBE, xs, ys)
+    bins = O.window_bins(g, DET, 16, 16, (2, 8.0), (2, 8.0))
+    for p in range(2):
+        assert np.allclose(O.bin_sum(cb[p], bins, DET["nbins"]), O.prism_scan(S, m, n, g, PROBE, DET, xs[p:p + 1], ys[p:p + 1])[0], atol=1e-14)
+
+
+def test_frozen_phonon_average():
+    g = small_grid(n=64, cell=8.0, H=2, f=2)
+    v1, v2 = rand_potential(g, 14), rand_potential(g, 15)
+    xs, ys = np.array([1.0]), np.array([2.0])
+    same = O.frozen_phonon_scan([v1, v1, v1], g, PROBE, DET, xs, ys)
+    S, m, n = O.smatrix_build(v1, g)
+    single = O.prism_scan(S, m, n, g, PROBE, DET, xs, ys)
+    assert np.max(np.abs(same - single)) < 1e-15
+    S2, _, _ = O.smatrix_build(v2, g)
+    mix = O.frozen_phonon_scan([v1, v2], g, PROBE, DET, xs, ys)
+    assert np.max(np.abs(mix - 0.5 * (single + O.prism_scan(S2, m, n, g, PROBE, DET, xs, ys)))) < 1e-15
