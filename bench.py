@@ -175,6 +175,68 @@ def ncu_traffic(kernel):
     return None if k is None else k.get("bytes_per_launch_full")
 
 
+def serving_run(w, V_host, n_requests=40, rate=20.0, seed=5):
+    """Poisson stream of simulation requests through the continuous-batching engine.
+
+    Half the requests are small cells (16 A simple-cubic Cu, 256^2, 8 slices, f=4, 16x16 probes,
+    private S-matrix each); half are scans of the amorphous-carbon cell at probe steps of
+    0.2-0.5 A over its 50 x 50 A field, all served by one resident S-matrix (key 1).
+    Returns latency percentiles (submission -> result in host memory) and throughput."""
+    import torch
+
+    from paper_1702_01904_gb300 import prism as PR
+    from paper_1702_01904_gb300 import specimens
+    from paper_1702_01904_gb300.runtime import Server
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    small = specimens.workload_small()
+    Vs = torch.from_numpy(small.potential()).pin_memory()
+    Vl = V_host.pin_memory()
+    gs, gl = PR.grid_from_workload(small), PR.grid_from_workload(w)
+    det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
+    probe = PR.make_probe(w.alpha_mrad)
+    xs_s, ys_s = small.scan_positions()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    kinds = rng.random(n_requests) < 0.5
+    steps = rng.choice([0.2, 0.25, 0.3, 0.4, 0.5], n_requests)
+    srv = Server(hbm_budget_bytes=64 << 30, max_inflight=8)
+    # warm the server's code paths (not timed)
+    t, _ = srv.submit(gs, Vs, probe, xs_s, ys_s, det)
+    srv.wait(t)
+    tickets = []
+    probes = 0
+    t0 = time.perf_counter()
+    for i in range(n_requests):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        if kinds[i]:
+            t, _ = srv.submit(gs, Vs, probe, xs_s, ys_s, det)
+            probes += len(xs_s)
+        else:
+            n = int(w.cell_x / steps[i])
+            g1 = np.arange(n) * steps[i]
+            yy, xx = np.meshgrid(g1, g1, indexing="ij")
+            t, _ = srv.submit(gl, Vl, probe, xx.ravel(), yy.ravel(), det, key=1, px=n, py=n)
+            probes += n * n
+        tickets.append(t)
+    lat, reused = [], 0
+    for t in tickets:
+        st = srv.wait(t)
+        lat.append(st.total_ms)
+        reused += st.smatrix_reused
+    wall = time.perf_counter() - t0
+    info = srv.stats()
+    srv.close()
+    lat = np.sort(np.array(lat))
+    return {"requests": n_requests, "poisson_rate_per_s": rate, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat[-1]), "requests_per_s": n_requests / wall, "probes_per_s": probes / wall,
+            "smatrix_reused": int(reused), "peak_device_bytes": int(info.peak_bytes),
+            "mix": "50% 16 A Cu cells (256^2, 8 slices, f=4, 256 probes, own S-matrix); 50% scans of the "
+                   "a-C cell at 0.2-0.5 A steps (up to 62500 probes) from one resident S-matrix"}
+
+
 def ncu_case():
     import torch
 
@@ -206,6 +268,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ms-probes", type=int, default=1024, help="probes timed for the multislice baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the profiling case twice and exit: the same 1024^2 a-C grid, 4 slices, "
                          "alpha_max 9 mrad (25 beams, 200 MB wave stack), 2000 probes")
@@ -405,6 +468,10 @@ def main():
                 "frac": rd["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
                 "peak_source": f"{peak_note} ({'MEASURED_PEAKS.json hbm_gbs' if rd['unit'] == 'GB/s' else '152 SMs x 128 FP32 lanes x 2 x median SM clock'})"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_run(w, V_host)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, V_host.numpy(), budget_s=20.0)
@@ -431,7 +498,9 @@ def main():
                            "speedup_prism_vs_multislice": value / world / ms_probes_s},
             "beams_slices_per_s": Bn * w.n_slices / (build_ms / 1000.0),
             "phase_ms_per_step": {"s_matrix_build": build_ms, "scan": scan_ms},
-            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                           "what": "one whole step (S-matrix build + 40000-probe scan), device time"},
+            "serving": serving,
             "clocks": clk,
         }
         print(json.dumps(res), flush=True)

@@ -209,6 +209,59 @@ int multislice_scan_run_noalloc(const prism_grid *grid, const float *V_dev, cons
                                 const prism_scan *scan, const prism_detector *det, float *out_dev,
                                 void *cuda_stream);
 
+/* ---- serving: continuous batching of simulation requests --------------------------------- */
+
+/* A request: one cell (grid + potential), one probe configuration, one scan and detector.
+ * Requests with the same non-zero smatrix_key (and the same grid) share one S-matrix, which stays
+ * resident between requests: V_host is read only when that S-matrix is not resident (the S-matrix
+ * serves every probe configuration, Varying Probe Size section).  smatrix_key = 0: private
+ * S-matrix, released after the request.  V_host [n_slices][ny][nx] should be pinned (pageable
+ * memory is copied synchronously by the worker) and must stay valid until the request completes;
+ * the scan arrays and grid.slice_dz are copied at submission; out_host [py][px][nbins] is written
+ * before prism_server_wait reports completion. */
+typedef struct prism_request {
+    prism_grid grid;
+    const float *V_host;
+    unsigned long long smatrix_key;
+    prism_probe probe;
+    prism_scan scan;
+    prism_detector det;
+    float *out_host;
+} prism_request;
+
+typedef struct prism_request_stats {
+    double queued_ms;   /* submission -> admission                       */
+    double total_ms;    /* submission -> result in out_host              */
+    int smatrix_reused; /* 1 if a resident S-matrix served the request  */
+    int status;         /* PRISM_OK or the request's error code          */
+} prism_request_stats;
+
+typedef struct prism_server_info {
+    int pending, running, resident;   /* queued / in flight / resident S-matrices */
+    long admitted, completed;
+    size_t used_bytes, peak_bytes;    /* device memory accounted to requests and S-matrices */
+} prism_server_info;
+
+typedef struct prism_server prism_server;
+
+/* Start a request engine on the current device.  A worker thread admits queued requests in
+ * arrival order whenever fewer than max_inflight are running and the request's device footprint
+ * (its S-matrix plan unless resident, output and positions) fits hbm_budget_bytes (0 = no
+ * budget), evicting idle resident S-matrices least-recently-used when needed; a request that does
+ * not fit yet does not hold back later ones.  Requests on different S-matrices run on different
+ * streams and overlap on the device.  Results equal those of the request run alone (the kernels
+ * are deterministic).  (No counterpart in the paper: this is the serving form of the method.) */
+int prism_server_create(size_t hbm_budget_bytes, int max_inflight, prism_server **out);
+/* Queue a request; returns a ticket.  Errors: INVALID for malformed requests. */
+int prism_server_submit(prism_server *server, const prism_request *req, unsigned long long *ticket);
+/* Wait at most timeout_s seconds for a ticket; OK when its result is in out_host, the request's
+ * error code if it failed (BUDGET if it can never fit), DEVICE on timeout.  A ticket is forgotten
+ * after a wait that does not time out.  stats may be NULL. */
+int prism_server_wait(prism_server *server, unsigned long long ticket, double timeout_s, prism_request_stats *stats);
+int prism_server_stats(prism_server *server, prism_server_info *out);
+/* Finish the queued and running requests, release every S-matrix and stop the worker. */
+void prism_server_destroy(prism_server *server);
+
 /* ---- introspection (tests, tools) ----------------------------------------------- */
 
 int prism_plan_info(const prism_plan *plan, prism_info *out);

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libprism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h")] + [os.path.join(INCLUDE, "prism.h")]
 CUDA_UNITS = ["kernels_build.cu", "kernels_scan.cu", "noalloc.cu"]
-HOST_UNITS = ["engine.cpp"]
+HOST_UNITS = ["engine.cpp", "server.cpp"]
 
 
 def cuda_home() -> str:
@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         src, obj = os.path.join(CSRC, u), os.path.join(BUILD, u + ".o")
         objs.append(obj)
         if force or _stale(src, obj):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-pthread",
                          "-I", os.path.join(home, "include"), *inc, "-c", src, "-o", obj])
     if jobs:
         with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                 f.result()
     if jobs or force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp"
-        _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], verbose)
+        _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp, *objs], verbose)
         os.replace(tmp, LIB)
     return LIB
 

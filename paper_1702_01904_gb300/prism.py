@@ -35,6 +35,7 @@ EXPORTED = [
     "prism_plan_smatrix", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
+    "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
 ]
 
 
@@ -68,6 +69,20 @@ class PrismInfo(ctypes.Structure):
     _fields_ = [("n_beams", c_int), ("nx_s", c_int), ("ny_s", c_int), ("nw_x", c_int), ("nw_y", c_int),
                 ("beam_batch", c_int), ("wavelength", c_double), ("sigma", c_double),
                 ("device_bytes", c_size_t)]
+
+
+class PrismRequest(ctypes.Structure):
+    _fields_ = [("grid", PrismGrid), ("V_host", c_void_p), ("smatrix_key", ctypes.c_ulonglong),
+                ("probe", PrismProbe), ("scan", PrismScan), ("det", PrismDetector), ("out_host", c_void_p)]
+
+
+class PrismRequestStats(ctypes.Structure):
+    _fields_ = [("queued_ms", c_double), ("total_ms", c_double), ("smatrix_reused", c_int), ("status", c_int)]
+
+
+class PrismServerInfo(ctypes.Structure):
+    _fields_ = [("pending", c_int), ("running", c_int), ("resident", c_int), ("admitted", c_long),
+                ("completed", c_long), ("used_bytes", c_size_t), ("peak_bytes", c_size_t)]
 
 
 _lib = None
@@ -110,6 +125,11 @@ def load(path: str = LIB_PATH):
         "prism_plan_launches": (c_long, [P]),
         "prism_plan_reset_stats": (c_int, [P]),
         "prism_kernel_name": (c_char_p, [c_int]),
+        "prism_server_create": (c_int, [c_size_t, c_int, POINTER(P)]),
+        "prism_server_submit": (c_int, [P, POINTER(PrismRequest), POINTER(ctypes.c_ulonglong)]),
+        "prism_server_wait": (c_int, [P, ctypes.c_ulonglong, c_double, POINTER(PrismRequestStats)]),
+        "prism_server_stats": (c_int, [P, POINTER(PrismServerInfo)]),
+        "prism_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -301,3 +321,32 @@ def prism_plan_reset_stats(plan):
 
 def prism_kernel_name(kind):
     return load().prism_kernel_name(kind).decode()
+
+
+# ------------------------------------------------------------------ serving
+def prism_server_create(hbm_budget_bytes=0, max_inflight=4):
+    srv = c_void_p()
+    _check(load().prism_server_create(hbm_budget_bytes, max_inflight, byref(srv)))
+    return srv
+
+
+def prism_server_submit(server, request):
+    t = ctypes.c_ulonglong()
+    _check(load().prism_server_submit(server, byref(request), byref(t)))
+    return t.value
+
+
+def prism_server_wait(server, ticket, timeout_s=600.0):
+    st = PrismRequestStats()
+    _check(load().prism_server_wait(server, ticket, timeout_s, byref(st)))
+    return st
+
+
+def prism_server_stats(server):
+    info = PrismServerInfo()
+    _check(load().prism_server_stats(server, byref(info)))
+    return info
+
+
+def prism_server_destroy(server):
+    load().prism_server_destroy(server)

@@ -145,3 +145,50 @@ def multislice(grid, V: torch.Tensor, probe, x0, y0, det, stream=None, scratch_b
     stream = stream if stream is not None else torch.cuda.current_stream()
     P.multislice_scan_run(grid, V, probe, P.make_scan(px, py, x0, y0), det, out, stream, scratch_bytes)
     return out
+
+
+class Server:
+    """Continuous-batching request engine (libprism's prism_server_*): submit simulation requests
+    from any thread; results arrive in host arrays.  S-matrices with a non-zero key stay resident
+    for later requests on the same cell."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=4):
+        _require_cuda()
+        P.load()
+        self.srv = P.prism_server_create(hbm_budget_bytes, max_inflight)
+        self._keep = {}
+
+    def submit(self, grid, V_host, probe, x0, y0, det, key=0, px=None, py=None):
+        """V_host: float32 [H][ny][nx] host tensor/array (pinned is best), kept alive until done.
+        Returns (ticket, out) where out is the numpy [P][nbins] array filled on completion."""
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        n = len(x0)
+        px = n if px is None else px
+        py = 1 if py is None else py
+        out = np.zeros((n, det.nbins), np.float32)
+        vp = V_host.data_ptr() if hasattr(V_host, "data_ptr") else V_host.ctypes.data
+        req = P.PrismRequest(grid, vp, key, probe, P.make_scan(px, py, x0, y0), det, out.ctypes.data)
+        t = P.prism_server_submit(self.srv, req)
+        self._keep[t] = (V_host, out, grid)
+        return t, out
+
+    def wait(self, ticket, timeout_s=600.0):
+        try:
+            return P.prism_server_wait(self.srv, ticket, timeout_s)
+        finally:
+            self._keep.pop(ticket, None)
+
+    def stats(self):
+        return P.prism_server_stats(self.srv)
+
+    def close(self):
+        if getattr(self, "srv", None) is not None:
+            P.prism_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
