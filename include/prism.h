@@ -278,6 +278,12 @@ int prism_plan_beams(const prism_plan *plan, int *m, int *n, int capacity);
 int prism_plan_smatrix(const prism_plan *plan, const void **dev_ptr);
 int prism_plan_transmission(const prism_plan *plan, const void **dev_ptr);
 
+/* Diagnostic of the tensor-core path (no counterpart in the paper): one tcgen05 MMA
+ * D[128][16] = A[128][16] B[16][16]^T on small-integer FP16 operands, A[m][k] = (m + 3k) % 7 - 3,
+ * B[n][k] = (5n + k) % 5 - 2, written to out_dev float32 [128][16]; status_dev[0] is set to 1 if the
+ * MMA did not complete within its poll limit (caller zeroes it).  Asynchronous on cuda_stream. */
+int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cuda_stream);
+
 /* Relativistic wavelength (Angstrom) and interaction constant (rad/(V*Angstrom)), CODATA 2018. */
 double prism_wavelength(double kv);
 double prism_interaction_constant(double kv);

@@ -946,6 +946,15 @@ extern "C" int prism_plan_transmission(const prism_plan *P, const void **dev_ptr
     return PRISM_OK;
 }
 
+extern "C" int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cuda_stream) {
+    int rc;
+    if ((rc = check_dev_ptr(out_dev, 16, "out_dev"))) return rc;
+    if ((rc = check_dev_ptr(status_dev, 4, "status_dev"))) return rc;
+    cudaError_t e = launch_tc_selftest(out_dev, status_dev, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string("tcgen05 self-test launch: ") + cudaGetErrorString(e));
+    return PRISM_OK;
+}
+
 // ------------------------------------------------------------------ timing
 static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan"};
 

@@ -101,6 +101,7 @@ cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s);
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
+cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);
 // smallest scan-window / FFT sizes the kernels are instantiated for
 bool row_supported(int n);
 bool col_supported(int n);

@@ -36,6 +36,7 @@ EXPORTED = [
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
+    "prism_selftest_tcgen05",
 ]
 
 
@@ -130,6 +131,7 @@ def load(path: str = LIB_PATH):
         "prism_server_wait": (c_int, [P, ctypes.c_ulonglong, c_double, POINTER(PrismRequestStats)]),
         "prism_server_stats": (c_int, [P, POINTER(PrismServerInfo)]),
         "prism_server_destroy": (None, [P]),
+        "prism_selftest_tcgen05": (c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -350,3 +352,7 @@ def prism_server_stats(server):
 
 def prism_server_destroy(server):
     load().prism_server_destroy(server)
+
+
+def prism_selftest_tcgen05(out_dev, status_dev, cuda_stream=None):
+    return _check(load().prism_selftest_tcgen05(_ptr(out_dev), _ptr(status_dev), _stream(cuda_stream)))
