@@ -61,6 +61,13 @@ extern "C" {
  *                must be <= 0.5 when downsample == 2; 0 < aa_frac.
  *   alpha_max_mrad  radius of the plane-wave set: sqrt(m^2+n^2) f lambda dq <= alpha_max
  *                (PRISM Algorithm section).  Must lie inside the anti-aliasing aperture.
+ *   precision    storage of the S-matrix and arithmetic of the beam sum (Eq. PRISMfinal):
+ *                PRISM_PRECISION_FP32 (complex64 S, FP32 CUDA-core sum), or
+ *                PRISM_PRECISION_FP16 / PRISM_PRECISION_BF16: S stored pixel-major in 16-bit
+ *                floats with one power-of-two scale per beam, the beam sum run on the tensor
+ *                cores with FP32 accumulation (scan windows of 16, 32 or 64 pixels).  The build
+ *                (transmission, FFTs, propagator) is FP32 in every mode.  Ignored by
+ *                multislice_scan_run.  Zero-initialised structs select FP32.
  */
 typedef struct prism_grid {
     int nx, ny, n_slices;
@@ -72,7 +79,12 @@ typedef struct prism_grid {
     int downsample;
     double aa_frac;
     double alpha_max_mrad;
+    int precision;
 } prism_grid;
+
+#define PRISM_PRECISION_FP32 0
+#define PRISM_PRECISION_FP16 1
+#define PRISM_PRECISION_BF16 2
 
 /* Probe: aperture semi-angle (A(q) = 1 where lambda|q| <= alpha), defocus C1 and spherical
  * aberration C3 (Angstrom) in chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3, and tilt
@@ -266,7 +278,8 @@ void prism_server_destroy(prism_server *server);
 
 int prism_plan_info(const prism_plan *plan, prism_info *out);
 
-/* Bytes of the stored S-matrix (B * nx_s * ny_s * 8). */
+/* Bytes of the stored S-matrix: B * nx_s * ny_s * 8 in FP32 mode; nx_s * ny_s * K * 2 + 4 * K / 2
+ * (16-bit values, K = 2 * roundup(B, 8), plus the per-beam scales) in FP16/BF16 mode. */
 int prism_plan_smatrix_bytes(const prism_plan *plan, size_t *out);
 
 /* Beam indices (m, n) of the plane-wave set, q_mn = (m f / cell_x, n f / cell_y), in the
@@ -274,9 +287,16 @@ int prism_plan_smatrix_bytes(const prism_plan *plan, size_t *out);
 int prism_plan_beams(const prism_plan *plan, int *m, int *n, int capacity);
 
 /* Device pointers owned by the plan (valid until destroy): the S-matrix complex64
- * [B][ny_s][nx_s] (interleaved re, im) and the transmission functions complex64 [H][ny][nx]. */
+ * [B][ny_s][nx_s] (interleaved re, im) and the transmission functions complex64 [H][ny][nx].
+ * prism_plan_smatrix fails with INVALID in FP16/BF16 mode (use prism_plan_smatrix_copy). */
 int prism_plan_smatrix(const prism_plan *plan, const void **dev_ptr);
 int prism_plan_transmission(const prism_plan *plan, const void **dev_ptr);
+
+/* Write the S-matrix as complex64 [B][ny_s][nx_s] into out_dev (caller-owned device buffer of
+ * B * nx_s * ny_s * 8 bytes), asynchronously on the plan's stream: a copy in FP32 mode, the
+ * 16-bit values times their beam scale in FP16/BF16 mode (the values the beam sum uses).
+ * INVALID before the S-matrix is built. */
+int prism_plan_smatrix_copy(prism_plan *plan, float *out_dev);
 
 /* Diagnostic of the tensor-core path (no counterpart in the paper): one tcgen05 MMA
  * D[128][16] = A[128][16] B[16][16]^T on small-integer FP16 operands, A[m][k] = (m + 3k) % 7 - 3,
@@ -297,7 +317,8 @@ double prism_interaction_constant(double kv);
 #define PRISM_K_COL        3  /* column FFT, x propagator (AA-masked), column IFFT          */
 #define PRISM_K_ROW_OUT    4  /* last row IFFT, store S                                     */
 #define PRISM_K_SCAN       5  /* coefficients + window gather + beam sum + window FFT + bins */
-#define PRISM_K_COUNT      6
+#define PRISM_K_QUANT      6  /* FP16/BF16 mode: per-beam scales, S to pixel-major 16-bit     */
+#define PRISM_K_COUNT      7
 
 /* profiling on: every launch of the plan is bracketed by CUDA events on the plan's stream. */
 int prism_plan_set_profiling(prism_plan *plan, int enable);

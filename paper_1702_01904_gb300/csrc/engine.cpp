@@ -344,7 +344,14 @@ struct prism_plan {
     size_t budget = 0;
     DevArena arena;
     // device tables / buffers
-    float2 *t = nullptr, *wave = nullptr, *S = nullptr;
+    float2 *t = nullptr, *wave = nullptr, *S = nullptr;  // S: all beams (FP32 mode) or one beam batch (16-bit)
+    int prec = PRISM_PRECISION_FP32;
+    void *S16 = nullptr;       // 16-bit mode: [ny_s * nx_s][kp]
+    float *scale = nullptr;    // 16-bit mode: [kp / 2] per-beam power-of-two scales
+    int kp = 0;
+    float2 *win = nullptr;     // 16-bit mode: scan window scratch
+    size_t win_cap = 0;
+    int *dev_err = nullptr;    // device error word
     float2 *prop_x = nullptr, *prop_y = nullptr;
     int *aa_kmax = nullptr;
     float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr;
@@ -425,6 +432,11 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     const int nwx = nxs / g.f, nwy = nys / g.f;
     if (nwx != nwy || !scan_supported(nwx))
         return fail(PRISM_ERR_UNSUPPORTED, "scan window must be square with 8, 16, 32, 64 or 128 pixels");
+    if (g.precision != PRISM_PRECISION_FP32 && g.precision != PRISM_PRECISION_FP16 && g.precision != PRISM_PRECISION_BF16)
+        return fail(PRISM_ERR_INVALID, "precision must be PRISM_PRECISION_FP32, _FP16 or _BF16");
+    const bool half = g.precision != PRISM_PRECISION_FP32;
+    if (half && !scan_tc_supported(nwx))
+        return fail(PRISM_ERR_UNSUPPORTED, "16-bit precision needs a scan window of 16, 32 or 64 pixels");
 
     int device = 0;
     CUDA_TRY(cudaGetDevice(&device));
@@ -438,6 +450,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     P->nxs = nxs;
     P->nys = nys;
     P->nw = nwx;
+    P->prec = g.precision;
     rc = build_grid_tables(&g, P->T);
     if (rc) {
         delete P;
@@ -467,7 +480,8 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
         delete P;
         return fail(PRISM_ERR_INVALID, "empty beam set");
     }
-    if (scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
+    P->kp = 2 * ((P->nbeams + 7) / 8 * 8);
+    if (half ? scan_tc_grid(P->nw, P->kp, P->prec == PRISM_PRECISION_BF16, 1, 1) <= 0 : scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
         delete P;
         return fail(PRISM_ERR_UNSUPPORTED, "too many beams for the scan kernel's shared memory");
     }
@@ -482,18 +496,23 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     // memory plan
     const size_t px = (size_t)g.nx * g.ny;
     const size_t t_bytes = (size_t)g.n_slices * px * 8;
-    const size_t s_bytes = (size_t)P->nbeams * nxs * nys * 8;
+    // FP32 mode keeps S for all beams; 16-bit mode keeps the pixel-major 16-bit S plus one FP32
+    // beam batch that the quantiser reads
+    const size_t sbeam = (size_t)nxs * nys * 8;
+    const size_t s16_bytes = half ? (size_t)nxs * nys * P->kp * 2 + (size_t)P->kp / 2 * sizeof(float) : 0;
     const size_t w_bytes = px * 8;
-    const size_t fixed = t_bytes + s_bytes + (1 << 20);
+    const size_t per_beam = w_bytes + (half ? sbeam : 0);
+    const size_t fixed = t_bytes + (half ? s16_bytes : (size_t)P->nbeams * sbeam) + (1 << 20);
     int batch = P->nbeams;
     if (hbm_budget_bytes) {
-        if (fixed + w_bytes > hbm_budget_bytes) {
+        if (fixed + per_beam > hbm_budget_bytes) {
             delete P;
-            return fail(PRISM_ERR_BUDGET, "plan needs " + std::to_string(fixed + w_bytes) + " bytes, budget " + std::to_string(hbm_budget_bytes));
+            return fail(PRISM_ERR_BUDGET, "plan needs " + std::to_string(fixed + per_beam) + " bytes, budget " + std::to_string(hbm_budget_bytes));
         }
-        batch = (int)std::min<size_t>(P->nbeams, (hbm_budget_bytes - fixed) / w_bytes);
+        batch = (int)std::min<size_t>(P->nbeams, (hbm_budget_bytes - fixed) / per_beam);
     }
     P->batch = batch;
+    const size_t s_bytes = (half ? (size_t)batch : (size_t)P->nbeams) * sbeam;
     P->tw64 = make_tw64();
     std::vector<float2> tww_f;
     {
@@ -510,6 +529,15 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     };
     if ((rc = A.alloc((void **)&P->t, t_bytes))) return bail(rc);
     if ((rc = A.alloc((void **)&P->S, s_bytes))) return bail(rc);
+    if (half) {
+        if ((rc = A.alloc(&P->S16, (size_t)nxs * nys * P->kp * 2))) return bail(rc);
+        if ((rc = A.alloc((void **)&P->scale, (size_t)P->kp / 2 * sizeof(float)))) return bail(rc);
+        // padded beams stay zero in S16 (their coefficients are zero too, and 0 * 0 must not be NaN)
+        CUDA_TRY(cudaMemsetAsync(P->S16, 0, (size_t)nxs * nys * P->kp * 2, P->stream));
+        CUDA_TRY(cudaMemsetAsync(P->scale, 0, (size_t)P->kp / 2 * sizeof(float), P->stream));
+    }
+    if ((rc = A.alloc((void **)&P->dev_err, sizeof(int)))) return bail(rc);
+    CUDA_TRY(cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->stream));
     if ((rc = A.alloc((void **)&P->wave, (size_t)batch * w_bytes))) return bail(rc);
     if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
     if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
@@ -549,6 +577,12 @@ extern "C" int prism_sync(prism_plan *P) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
     CUDA_TRY(cudaStreamSynchronize(P->stream));
     CUDA_TRY(cudaGetLastError());
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(cudaMemset(P->dev_err, 0, sizeof(int)));
+        return fail(PRISM_ERR_DEVICE, "a kernel's bounded wait ran out (device error word " + std::to_string(err) + ")");
+    }
     return PRISM_OK;
 }
 
@@ -613,9 +647,22 @@ extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
         }
         RowArgs ro = row_args(P);
         ro.n_rows = nb * (g.downsample == 2 ? g.ny / 2 : g.ny);
-        ro.beam0 = b0;
+        ro.beam0 = P->prec == PRISM_PRECISION_FP32 ? b0 : 0;  // 16-bit mode: S holds this batch only
         rc = plan_launch(P, PRISM_K_ROW_OUT, [&] { return launch_row(g.nx, ROW_OUT, ro, P->stream); });
         if (rc) return rc;
+        if (P->prec != PRISM_PRECISION_FP32) {
+            QuantArgs q;
+            q.S = P->S;
+            q.S16 = P->S16;
+            q.scale = P->scale;
+            q.beam0 = b0;
+            q.nb = nb;
+            q.npix = P->nxs * P->nys;
+            q.kp = P->kp;
+            q.bf16 = P->prec == PRISM_PRECISION_BF16;
+            rc = plan_launch(P, PRISM_K_QUANT, [&] { return launch_quantize(q, P->stream); });
+            if (rc) return rc;
+        }
     }
     P->built = true;
     return PRISM_OK;
@@ -702,8 +749,27 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     a.nbins = det ? det->nbins : 0;
     a.n_probes = (int)Pn;
     a.probe0 = 0;
+    a.S16 = P->S16;
+    a.beam_scale = P->scale;
+    a.kp = P->kp;
+    a.scan_px = sc->px;
+    a.scan_py = sc->py;
+    a.err = P->dev_err;
     a.tw = P->tw64;
     return PRISM_OK;
+}
+
+// FP32 mode: the CUDA-core scan kernels; 16-bit mode: the tensor-core kernel (persistent grid, its
+// window scratch grown on demand)
+static int scan_launch(prism_plan *P, ScanArgs &a) {
+    if (P->prec == PRISM_PRECISION_FP32) return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    const int bf = P->prec == PRISM_PRECISION_BF16;
+    const int grid = scan_tc_grid(P->nw, P->kp, bf, a.scan_px, a.scan_py);
+    if (grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
+    int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, grid));
+    if (rc) return rc;
+    a.win = P->win;
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, bf, grid, a, P->stream); });
 }
 
 extern "C" int prism_scan_run(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
@@ -715,7 +781,7 @@ extern "C" int prism_scan_run(prism_plan *P, const prism_probe *probe, const pri
     if (a.n_probes == 0) return PRISM_OK;
     if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
     a.out = out_dev;
-    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    return scan_launch(P, a);
 }
 
 extern "C" int prism_scan_run_host(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
@@ -729,7 +795,7 @@ extern "C" int prism_scan_run_host(prism_plan *P, const prism_probe *probe, cons
     const size_t bytes = (size_t)a.n_probes * det->nbins * sizeof(float);
     if ((rc = grow(P->arena, (void **)&P->out_stage, &P->out_cap, bytes))) return rc;
     a.out = P->out_stage;
-    rc = plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    rc = scan_launch(P, a);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpyAsync(out_host, P->out_stage, bytes, cudaMemcpyDeviceToHost, P->stream));
     return PRISM_OK;
@@ -744,7 +810,7 @@ extern "C" int prism_scan_run_cbed(prism_plan *P, const prism_probe *probe, cons
     if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
     a.out = nullptr;
     a.cbed = out_dev;
-    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    return scan_launch(P, a);
 }
 
 extern "C" int prism_scan_run_accumulate(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
@@ -759,7 +825,7 @@ extern "C" int prism_scan_run_accumulate(prism_plan *P, const prism_probe *probe
     a.out = out_dev;
     a.accumulate = 1;
     a.acc_w = weight;
-    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    return scan_launch(P, a);
 }
 
 // ------------------------------------------------------------------ multislice baseline
@@ -920,7 +986,8 @@ extern "C" int prism_plan_info(const prism_plan *P, prism_info *out) {
 
 extern "C" int prism_plan_smatrix_bytes(const prism_plan *P, size_t *out) {
     if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
-    *out = (size_t)P->nbeams * P->nxs * P->nys * 8;
+    *out = P->prec == PRISM_PRECISION_FP32 ? (size_t)P->nbeams * P->nxs * P->nys * 8
+                                            : (size_t)P->nxs * P->nys * P->kp * 2 + (size_t)P->kp / 2 * sizeof(float);
     return PRISM_OK;
 }
 
@@ -936,7 +1003,24 @@ extern "C" int prism_plan_beams(const prism_plan *P, int *m, int *n, int capacit
 
 extern "C" int prism_plan_smatrix(const prism_plan *P, const void **dev_ptr) {
     if (!P || !dev_ptr) return fail(PRISM_ERR_INVALID, "NULL argument");
+    if (P->prec != PRISM_PRECISION_FP32) return fail(PRISM_ERR_INVALID, "S is stored in 16 bits: use prism_plan_smatrix_copy");
     *dev_ptr = P->S;
+    return PRISM_OK;
+}
+
+extern "C" int prism_plan_smatrix_copy(prism_plan *P, float *out_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(out_dev, 8, "out_dev"))) return rc;
+    if (!P->built) return fail(PRISM_ERR_INVALID, "S-matrix not built");
+    const size_t npix = (size_t)P->nxs * P->nys;
+    if (P->prec == PRISM_PRECISION_FP32) {
+        CUDA_TRY(cudaMemcpyAsync(out_dev, P->S, (size_t)P->nbeams * npix * 8, cudaMemcpyDeviceToDevice, P->stream));
+        return PRISM_OK;
+    }
+    cudaError_t e = launch_dequantize(P->S16, P->scale, (float2 *)out_dev, P->nbeams, (int)npix, P->kp,
+                                      P->prec == PRISM_PRECISION_BF16, P->stream);
+    if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string("dequantize: ") + cudaGetErrorString(e));
     return PRISM_OK;
 }
 
@@ -956,7 +1040,7 @@ extern "C" int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cud
 }
 
 // ------------------------------------------------------------------ timing
-static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan"};
+static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan", "quantize"};
 
 extern "C" const char *prism_kernel_name(int kind) {
     if (kind < 0 || kind >= PRISM_K_COUNT) return "?";

@@ -12,6 +12,7 @@
 
 #include "fft.cuh"
 #include "params.h"
+#include "scan_common.cuh"
 
 namespace prism {
 
@@ -193,28 +194,10 @@ struct GroupCfg {
     static constexpr size_t SMEM_FIXED = (size_t)(BIG + EX + NW) * sizeof(float2) + 64 * sizeof(int);
 };
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Sum over one warp of per-lane FP32 partial sums, fixed xor-shuffle tree (every lane gets the
-// total).  Pairwise: relative error <= (terms per lane + 5) * 2^-24 for non-negative terms.
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <int NW>
 __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __grid_constant__ ScanArgs a) {
     using C = GroupCfg<NW>;
-    using FS = FftShape<NW>;
-    using Fwd = FwdFft<NW>;
-    constexpr int BLOCK = C::BLOCK, PIX = C::PIX, G = C::G, T = C::T, E = FS::E, PW = C::PW;
+    constexpr int BLOCK = C::BLOCK, PIX = C::PIX, G = C::G, PW = C::PW;
     extern __shared__ float2 smem[];
     float2 *big = smem;                    // staging tiles [STAGES][MAXTILE], later windows [G][NW][PW]
     float2 *ex = big + C::BIG;             // FFT exchange
@@ -226,54 +209,8 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
     if (p0 >= a.n_probes) return;
     const int gn = min(G, a.n_probes - p0);
     for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
-
-    // coefficients of the group's probes
-    for (int i = tid; i < G * a.n_beams; i += BLOCK) {
-        const int p = i / a.n_beams, b = i - p * a.n_beams;
-        float2 v = make_float2(0.f, 0.f);
-        if (p < gn) {
-            double c = a.qx[b] * (a.x0[p0 + p] - a.shift_x) + a.qy[b] * (a.y0[p0 + p] - a.shift_y);
-            c -= rint(c);
-            float s, co;
-            sincospif(-2.0f * (float)c, &s, &co);
-            v = cmul(__ldg(a.base + b), make_float2(co, s));
-        }
-        alpha[i] = v;
-    }
-    // window origins (FP64, Eq. RegionBounds) and the union tile relative to probe 0; the tile
-    // starts on an even column and has an even width so that pixel pairs are 16-byte aligned
-    if (tid == 0) {
-        int sx[G], sy[G];
-        for (int p = 0; p < gn; ++p) {
-            sx[p] = ((int)floor(a.x0[p0 + p] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
-            sy[p] = ((int)floor(a.y0[p0 + p] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
-        }
-        int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0, dx[G], dy[G];
-        for (int p = 0; p < gn; ++p) {
-            dx[p] = ((sx[p] - sx[0] + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2;
-            dy[p] = ((sy[p] - sy[0] + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2;
-            dxmin = min(dxmin, dx[p]);
-            dxmax = max(dxmax, dx[p]);
-            dymin = min(dymin, dy[p]);
-            dymax = max(dymax, dy[p]);
-        }
-        const int tx0 = (sx[0] + dxmin) & (a.nx_s - 1);
-        const int shift = tx0 & 1;                       // extra leading column to reach an even origin
-        const int tw = (dxmax - dxmin + NW + shift + 1) & ~1;
-        const int th = dymax - dymin + NW;
-        const bool fits = tw <= NW + C::D && th <= NW + C::D && tw * th <= C::MAXTILE;
-        meta[0] = fits ? 1 : gn;  // number of sub-groups
-        for (int p = 0; p < G; ++p) {
-            meta[8 + p] = sx[p < gn ? p : 0];
-            meta[16 + p] = sy[p < gn ? p : 0];
-            meta[24 + p] = p < gn ? dx[p] - dxmin + shift : 0;
-            meta[32 + p] = p < gn ? dy[p] - dymin : 0;
-        }
-        meta[1] = tw;
-        meta[2] = th;
-        meta[3] = tx0 - shift;
-        meta[4] = (sy[0] + dymin) & (a.ny_s - 1);
-    }
+    group_coefficients<G>(a, p0, gn, alpha, tid, BLOCK);
+    if (tid == 0) group_geometry<NW, G, C::D, C::MAXTILE>(a, p0, gn, meta);
     __syncthreads();
     const int nsub = meta[0];
     const size_t bstride = (size_t)a.ny_s * a.nx_s;
@@ -363,79 +300,7 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
             }
         }
         __syncthreads();
-        const int nwin = all ? gn : 1;
-
-        // window FFTs: rows of all windows, then columns
-        {
-            const int slot = tid / T, t = tid % T;
-            WarpExchange<FS::N1, FS::N2, T> exr{ex + slot * (FS::N1 * (FS::N2 + 1))};
-#pragma unroll 1
-            for (int r0 = 0; r0 < G * NW; r0 += C::RSLOTS) {
-                const int row = r0 + slot;
-                const bool ok = row < nwin * NW;
-                const int rr = ok ? row : row % NW;
-                float2 v[E];
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = win[rr * PW + Fwd::in_elem(r, t)];
-                Fwd::run(v, t, twf, a.tw, exr);
-                if (ok) {
-#pragma unroll
-                    for (int r = 0; r < E; ++r) win[rr * PW + Fwd::out_elem(r, t)] = v[r];
-                }
-            }
-        }
-        __syncthreads();
-        {
-            const int c = tid % C::CW, t = tid / C::CW;
-            ColExchange<FS::N1, FS::N2, C::CW> exc{ex, c};
-#pragma unroll 1
-            for (int c0 = 0; c0 < G * NW; c0 += C::CW) {
-                const int col = c0 + c;
-                const bool ok = col < nwin * NW;
-                const int cc = ok ? col : col % NW;
-                float2 *w = win + (cc / NW) * NW * PW;
-                const int x = cc % NW;
-                float2 v[E];
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = w[Fwd::in_elem(r, t) * PW + x];
-                Fwd::run(v, t, twf, a.tw, exc);
-                __syncthreads();
-                if (ok) {
-#pragma unroll
-                    for (int r = 0; r < E; ++r) w[Fwd::out_elem(r, t) * PW + x] = v[r];
-                }
-            }
-        }
-        __syncthreads();
-        constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
-        // full diffraction patterns, if requested
-        if (a.cbed) {
-            const float fnorm = (float)a.inv_norm;
-            for (int i = tid; i < nwin * NW * NW; i += BLOCK) {
-                const int p = i >> (2 * LNW), u = i & (NW * NW - 1);
-                const float2 z = win[(p * NW + (u >> LNW)) * PW + (u & (NW - 1))];
-                a.cbed[(size_t)(p0 + (all ? p : sg)) * NW * NW + u] = (z.x * z.x + z.y * z.y) * fnorm;
-            }
-        }
-        // |Psi|^2 and bins: one warp per (probe, bin); FP32 pairwise sums, FP64 scale
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int j = (a.out ? warp : nwin * a.nbins); j < nwin * a.nbins; j += BLOCK / 32) {
-            const int p = j / a.nbins, k = j - p * a.nbins;
-            const float2 *w = win + p * NW * PW;
-            float sum = 0.f;
-            const int e = __ldg(a.bin_off + k + 1);
-            for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) {
-                const int u = __ldg(a.bin_idx + i);
-                const float2 z = w[(u >> LNW) * PW + (u & (NW - 1))];
-                sum += z.x * z.x + z.y * z.y;
-            }
-            sum = warp_sum(sum);
-            if (lane == 0) {
-                const float val = (float)((double)sum * a.inv_norm);
-                float *o = a.out + (size_t)(p0 + (all ? p : sg)) * a.nbins + k;
-                *o = a.accumulate ? *o + a.acc_w * val : val;
-            }
-        }
+        window_epilogue<NW, BLOCK, G, PW>(a, win, ex, twf, all ? gn : 1, meta + 40 + (all ? 0 : sg), tid);
         __syncthreads();  // windows and staging buffers are reused by the next sub-group
     }
 }

@@ -1,9 +1,14 @@
 // kernels_tc.cu -- tensor-core (tcgen05) kernels: a layout self-test and the reduced-precision
 // PRISM beam contraction.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "fft.cuh"
 #include "params.h"
+#include "scan_common.cuh"
 #include "tc.cuh"
 
 namespace prism {
@@ -78,6 +83,438 @@ cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     k_tc_selftest<<<1, 128, smem, s>>>(out, status);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ 16-bit S-matrix
+// Storage reduction of the S-matrix (PRISM Algorithm section): after the build, each beam's
+// real-space exit wave is divided by a power-of-two scale (the smallest power of two above its
+// largest |Re| or |Im|, so the division is exact and the values lie in (-1, 1)) and rounded to
+// FP16 or BF16.  The layout is pixel-major: pixel j holds (Re, Im) of beams 0..B-1 at
+// S16[j*kp + 2b], beams B..kp/2-1 are zero.  That row is the K dimension of the tensor-core beam
+// sum.
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (BF) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    } else {
+        const __half2 v = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    }
+}
+template <bool BF>
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+    if constexpr (BF) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&w);
+        return __bfloat1622float2(v);
+    } else {
+        const __half2 v = *reinterpret_cast<const __half2 *>(&w);
+        return __half22float2(v);
+    }
+}
+
+// smallest power of two strictly above x >= 0 (1 for x == 0), from the exponent field
+__device__ __forceinline__ float pow2_above(float x) {
+    if (!(x > 0.f)) return 1.f;
+    unsigned e = __float_as_uint(x) >> 23;  // biased exponent (x is non-negative)
+    e = e < 253u ? e + 1u : 254u;
+    return __uint_as_float(e << 23);
+}
+
+// one CTA per beam: scale[beam0 + b] = pow2_above(max |Re|, |Im| over the beam)
+__global__ void __launch_bounds__(512) k_beam_scale(const QuantArgs a) {
+    __shared__ float red[16];
+    const int b = blockIdx.x;
+    const float2 *src = a.S + (size_t)b * a.npix;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < a.npix; i += 512) {
+        const float2 v = src[i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < 16 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) a.scale[a.beam0 + b] = pow2_above(m);
+    }
+}
+
+// 32 pixels x 32 beams per tile through shared memory: coalesced reads along pixels of one beam,
+// coalesced 4-byte (Re, Im) writes along the beams of one pixel
+template <bool BF>
+__global__ void __launch_bounds__(256) k_quantize(const QuantArgs a) {
+    __shared__ float2 tile[32][33];
+    const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int pix0 = blockIdx.x * 32;
+    for (int c0 = 0; c0 < a.nb; c0 += 32) {
+        for (int j = ty; j < 32; j += 8) {
+            const int b = c0 + j;
+            tile[j][lane] = b < a.nb && pix0 + lane < a.npix ? a.S[(size_t)b * a.npix + pix0 + lane] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int b = c0 + lane;
+        if (b < a.nb) {
+            const float inv = 1.0f / a.scale[a.beam0 + b];  // exact: a power of two
+            uint32_t *dst = reinterpret_cast<uint32_t *>(a.S16);
+            for (int p = ty; p < 32; p += 8) {
+                if (pix0 + p >= a.npix) break;
+                const float2 v = tile[lane][p];
+                dst[((size_t)(pix0 + p) * a.kp) / 2 + a.beam0 + b] = pack2<BF>(v.x * inv, v.y * inv);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <bool BF>
+__global__ void k_dequantize(const uint32_t *S16, const float *scale, float2 *out, int n_beams, int npix, int kp) {
+    const size_t n = (size_t)n_beams * npix;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / npix);
+        const size_t j = i - (size_t)b * npix;
+        const float2 v = unpack2<BF>(S16[(j * kp) / 2 + b]);
+        out[i] = make_float2(v.x * scale[b], v.y * scale[b]);
+    }
+}
+
+cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s) {
+    if (a.nb <= 0) return cudaSuccess;
+    k_beam_scale<<<a.nb, 512, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int blocks = (a.npix + 31) / 32;
+    if (a.bf16)
+        k_quantize<true><<<blocks, 256, 0, s>>>(a);
+    else
+        k_quantize<false><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp, int bf16,
+                              cudaStream_t s) {
+    const size_t n = (size_t)n_beams * npix;
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    if (bf16)
+        k_dequantize<true><<<blocks, 256, 0, s>>>((const uint32_t *)S16, scale, out, n_beams, npix, kp);
+    else
+        k_dequantize<false><<<blocks, 256, 0, s>>>((const uint32_t *)S16, scale, out, n_beams, npix, kp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ tensor-core PRISM scan
+// The beam sum of Eq. PRISMfinal for a group of GX x GY neighbouring probes of the raster is one
+// real GEMM on the union tile R of their windows:
+//     D[r][n] = sum_k A[r][k] Bc[n][k],   A[r][2b + c] = (Re, Im)_c S16_b(r)   (r in R, M side)
+//     Bc[2p][2b] = s_b Re a_bp,  Bc[2p][2b+1] = -s_b Im a_bp,  Bc[2p+1][2b] = s_b Im a_bp,
+//     Bc[2p+1][2b+1] = s_b Re a_bp      (a_bp the coefficient of beam b for probe p, s_b its scale)
+// so D[r][2p] + i D[r][2p+1] = psi_p(r).  The tile is streamed in M tiles of 128 pixels and K
+// chunks (a 3-stage cp.async ring), one thread issues tcgen05.mma (M = 128, N = 2 G, K = 16) into
+// one of two TMEM accumulators, all warps drain a finished accumulator (tcgen05.ld) and scatter
+// each probe's window pixels to a per-CTA global scratch.  When the group is done the windows come
+// back through shared memory for the window FFT, |.|^2 and the bins (the epilogue of the FP32
+// path).  A group whose union tile is larger than its windows together is run probe by probe.
+template <int NW>
+struct TcCfg {
+    using FS = FftShape<NW>;
+    static constexpr int GX = 8, GY = 2, G = GX * GY, N = 2 * G;
+    static constexpr int BLOCK = 256;
+    static constexpr int STAGES = 3;
+    static constexpr int KCMAX = 96;                        // K (16-bit values) per ring stage
+    static constexpr int STAGE_BYTES = 128 * KCMAX * 2;     // 128 pixels x KCMAX
+    static constexpr int RING = STAGES * STAGE_BYTES;
+    static constexpr int PW = NW + 8;
+    static constexpr int EW = NW >= 64 ? 2 : NW == 32 ? 8 : 16;  // windows per epilogue pass
+    static constexpr int T = FS::T;
+    static constexpr int RSLOTS = BLOCK / T, CW = BLOCK / T;
+    static constexpr int EXR = RSLOTS * FS::N1 * (FS::N2 + 1);
+    static constexpr int EXC = FS::N1 * (FS::N2 + 1) * CW;
+    static constexpr int EX = EXR > EXC ? EXR : EXC;
+    static constexpr size_t EPI = (size_t)(EW * NW * PW + EX) * sizeof(float2);
+    static constexpr int META = 256;                        // ints
+    static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16;
+    static constexpr uint32_t TMEM_COLS = 2 * N;            // two accumulators
+    __host__ __device__ static constexpr size_t region0(int kp) {
+        const size_t r = (size_t)RING + (size_t)kp * N * 2;
+        return ((r > EPI ? r : EPI) + 127) & ~(size_t)127;
+    }
+    __host__ __device__ static constexpr size_t smem(int kp) { return region0(kp) + MISC; }
+};
+// meta (ints): [0] union tile  [1] tile width  [2] tile height  [3] tile x0  [4] tile y0
+// [5] probes in the group; per slot p < G: [8+p] window x0  [40+p] window y0  [72+p] x offset in
+// the tile  [104+p] y offset in the tile  [136+p] probe index or -1; [168+e] slot of the e-th
+// probe, [200+e] its probe index
+
+constexpr uint32_t TC_POLL_LIMIT = 1u << 22;  // mbarrier polls before a wait gives up
+
+template <int NW, bool BF>
+__global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ ScanArgs a) {
+    using C = TcCfg<NW>;
+    constexpr int G = C::G, N = C::N, GX = C::GX, GY = C::GY, BLOCK = C::BLOCK, PW = C::PW, S = C::STAGES;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int kp = a.kp;
+    unsigned char *ring = sm;
+    unsigned char *bmat = sm + C::RING;
+    float2 *win = reinterpret_cast<float2 *>(sm);  // epilogue: windows, then exchange (aliases ring + bmat)
+    float2 *ex = win + C::EW * NW * PW;
+    float2 *twf = reinterpret_cast<float2 *>(sm + C::region0(kp));
+    int *meta = reinterpret_cast<int *>(twf + NW);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(meta + C::META);
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(mbar + S);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint16_t *S16 = reinterpret_cast<const uint16_t *>(a.S16);
+
+    for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) tc::mbar_init(&mbar[i], 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_base, C::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_base;
+    const uint32_t idesc = tc::idesc_f16_f32(128, N, BF);
+    const uint32_t bbase = tc::smem_u32(bmat);
+    const int ngx = (a.scan_px + GX - 1) / GX, ngy = (a.scan_py + GY - 1) / GY;
+    const int ngroups = ngx * ngy;
+    const int bp = kp / 2;  // beams incl. padding
+    uint32_t st = 0;        // pipeline steps issued by this CTA (same value in every thread)
+    bool dead = false;  // set uniformly (through __syncthreads_or) once any thread's wait ran out
+    int my_fail = 0;
+
+    auto fail = [&]() {
+        my_fail = 1;
+        if (a.err) atomicOr(a.err, 1);
+    };
+
+    for (int grp = blockIdx.x; grp < ngroups && !dead; grp += gridDim.x) {
+        const int gy = grp / ngx, gx = grp - gy * ngx;
+        // coefficient operand Bc, K-major core matrices: core (k/8, n/8) at ((k/8)(N/8) + n/8) * 128 B
+        for (int i = tid; i < G * bp; i += BLOCK) {
+            const int p = i / bp, b = i - p * bp;
+            const int row = gy * GY + p / GX, col = gx * GX + p % GX;
+            float ar = 0.f, ai = 0.f;
+            if (row < a.scan_py && col < a.scan_px && b < a.n_beams) {
+                const int pr = row * a.scan_px + col;
+                double c = a.qx[b] * (a.x0[pr] - a.shift_x) + a.qy[b] * (a.y0[pr] - a.shift_y);
+                c -= rint(c);
+                float sn, cs;
+                sincospif(-2.0f * (float)c, &sn, &cs);
+                const float2 v = cmul(__ldg(a.base + b), make_float2(cs, sn));
+                const float sc = __ldg(a.beam_scale + b);
+                ar = v.x * sc;
+                ai = v.y * sc;
+            }
+            const int k = 2 * b;
+            unsigned char *core = bmat + ((k >> 3) * (N / 8)) * 128 + (k & 7) * 2;
+            const int n0 = 2 * p, n1 = 2 * p + 1;
+            *reinterpret_cast<uint32_t *>(core + (n0 >> 3) * 128 + (n0 & 7) * 16) = pack2<BF>(ar, -ai);
+            *reinterpret_cast<uint32_t *>(core + (n1 >> 3) * 128 + (n1 & 7) * 16) = pack2<BF>(ai, ar);
+        }
+        // group geometry (warp 0, one lane per slot): window origins of Eq. RegionBounds, union tile
+        if (warp == 0) {
+            const int p = lane;
+            const int row = gy * GY + p / GX, col = gx * GX + p % GX;
+            const bool valid = p < G && row < a.scan_py && col < a.scan_px;
+            int sx = 0, sy = 0;
+            if (valid) {
+                const int pr = row * a.scan_px + col;
+                sx = ((int)floor(a.x0[pr] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
+                sy = ((int)floor(a.y0[pr] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
+            }
+            const int sx0 = __shfl_sync(0xffffffffu, sx, 0), sy0 = __shfl_sync(0xffffffffu, sy, 0);
+            const int dx = valid ? ((sx - sx0 + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2 : 0;
+            const int dy = valid ? ((sy - sy0 + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2 : 0;
+            const int dxmin = __reduce_min_sync(0xffffffffu, dx), dxmax = __reduce_max_sync(0xffffffffu, dx);
+            const int dymin = __reduce_min_sync(0xffffffffu, dy), dymax = __reduce_max_sync(0xffffffffu, dy);
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            const int nvalid = __popc(vm);
+            const int tw = dxmax - dxmin + NW, th = dymax - dymin + NW;
+            if (p < G) {
+                meta[8 + p] = sx;
+                meta[40 + p] = sy;
+                meta[72 + p] = dx - dxmin;
+                meta[104 + p] = dy - dymin;
+                meta[136 + p] = valid ? row * a.scan_px + col : -1;
+            }
+            if (valid) {
+                const int e = __popc(vm & ((1u << p) - 1u));
+                meta[168 + e] = p;
+                meta[200 + e] = row * a.scan_px + col;
+            }
+            if (lane == 0) {
+                meta[0] = (long long)tw * th <= (long long)nvalid * NW * NW;
+                meta[1] = tw;
+                meta[2] = th;
+                meta[3] = (sx0 + dxmin) & (a.nx_s - 1);
+                meta[4] = (sy0 + dymin) & (a.ny_s - 1);
+                meta[5] = nvalid;
+            }
+        }
+        tc::fence_proxy_async();  // Bc was written through the generic proxy; the MMAs read it
+        __syncthreads();
+        const bool uni = meta[0] != 0;
+        const int nkc = (kp + C::KCMAX - 1) / C::KCMAX;
+        const int kcs = ((kp + nkc - 1) / nkc + 15) & ~15;
+        for (int sg = 0; sg < (uni ? 1 : G) && !dead; ++sg) {
+            if (!uni && meta[136 + sg] < 0) continue;
+            const int tw = uni ? meta[1] : NW, th = uni ? meta[2] : NW;
+            const int tx0 = uni ? meta[3] : meta[8 + sg], ty0 = uni ? meta[4] : meta[40 + sg];
+            const int npx = tw * th, nmt = (npx + 127) / 128, nsteps = nmt * nkc;
+            const uint32_t st0 = st;
+            // A chunk of local step ls: thread -> pixel m = 16 warp + lane/2 of the M tile, K cores
+            // kc = lane%2, lane%2 + 2, ...  (a lane pair reads one 32-byte sector of a pixel; a warp
+            // writes 2 x 256 contiguous shared-memory bytes)
+            auto load = [&](int ls) {
+                if (ls < nsteps) {
+                    const int mt = ls / nkc, c = ls - mt * nkc;
+                    const int k0 = c * kcs, kn = min(kcs, kp - k0);
+                    const int m = warp * 16 + (lane >> 1);
+                    const int idx = mt * 128 + m;
+                    if (idx < npx) {
+                        const int ty = idx / tw, tx = idx - ty * tw;
+                        const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
+                        const uint16_t *src = S16 + gp * kp + k0;
+                        unsigned char *dst = ring + ((st0 + ls) % S) * C::STAGE_BYTES + (m >> 3) * 128 + (m & 7) * 16;
+                        for (int kc = lane & 1; kc < kn / 8; kc += 2) cp_async16(dst + kc * 2048, src + kc * 8);
+                    }
+                }
+                cp_async_commit();
+            };
+            // accumulator of M tile mt -> window scratch of every probe whose window holds the pixel
+            auto drain = [&](int mt) {
+                tc::fence_after_sync();
+                const int q = warp & 3, h = warp >> 2;
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((mt & 1) * N + h * 16), v);
+                const int idx = mt * 128 + 32 * q + lane;
+                if (idx < npx) {
+                    const int ty = idx / tw, tx = idx - ty * tw;
+#pragma unroll
+                    for (int pp = 0; pp < 8; ++pp) {
+                        const int p = 8 * h + pp;
+                        const bool act = uni ? meta[136 + p] >= 0 : p == sg;
+                        const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
+                        if (act && (unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
+                            a.win[((size_t)blockIdx.x * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
+                    }
+                }
+                tc::fence_before_sync();
+            };
+            load(0);
+            load(1);
+            for (int ls = 0; ls < nsteps; ++ls) {
+                const uint32_t s = st0 + ls;
+                cp_async_wait<1>();
+                tc::fence_proxy_async();
+                if (__syncthreads_or(my_fail)) {
+                    dead = true;
+                    break;
+                }
+                const int mt = ls / nkc, c = ls - mt * nkc;
+                if (tid == 0) {
+                    tc::fence_after_sync();
+                    const int k0 = c * kcs, kn = min(kcs, kp - k0);
+                    const uint32_t abase = tc::smem_u32(ring + (s % S) * C::STAGE_BYTES);
+                    for (int j = 0; j < kn / 16; ++j) {
+                        const uint64_t ad = tc::smem_desc(abase + j * 4096, 2048, 128);
+                        const uint64_t bd = tc::smem_desc(bbase + (uint32_t)((k0 / 16 + j) * 2 * (N / 8)) * 128, (N / 8) * 128, 128);
+                        tc::mma_f16(tmem + (uint32_t)((mt & 1) * N), ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(&mbar[s % S]);
+                }
+                // ring slot (s + 2) % S was read by step s - 1: wait for its MMAs before refilling it
+                if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_POLL_LIMIT)) fail();
+                load(ls + 2);
+                if (c == 0 && mt >= 1) drain(mt - 1);
+            }
+            st = st0 + nsteps;
+            if (dead) break;
+            if (!tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_POLL_LIMIT)) fail();
+            drain(nmt - 1);
+            if (__syncthreads_or(my_fail)) dead = true;
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // window scratch written by this CTA is visible to all its threads
+        if (dead) break;
+        // epilogue: EW windows at a time through shared memory
+        const int nvalid = meta[5];
+        for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
+            const int ne = min(C::EW, nvalid - e0);
+            for (int i = tid; i < ne * NW * NW; i += BLOCK) {
+                const int e = i / (NW * NW), u = i - e * (NW * NW);
+                const int slot = meta[168 + e0 + e];
+                win[(e * NW + u / NW) * PW + (u & (NW - 1))] = __ldcg(a.win + ((size_t)blockIdx.x * G + slot) * (NW * NW) + u);
+            }
+            __syncthreads();
+            window_epilogue<NW, BLOCK, C::EW, PW>(a, win, ex, twf, ne, meta + 200 + e0, tid);
+            __syncthreads();
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    if (dead && tid == 0 && st > 0) tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_POLL_LIMIT);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+bool scan_tc_supported(int nw) { return nw == 16 || nw == 32 || nw == 64; }
+
+template <int NW, bool BF>
+static int tc_grid(int kp, int scan_px, int scan_py) {
+    using C = TcCfg<NW>;
+    const size_t smem = C::smem(kp);
+    if (smem > 227 * 1024) return 0;
+    if (cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan_tc<NW, BF>, C::BLOCK, smem) != cudaSuccess || per_sm < 1)
+        return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
+    return (int)std::max<long long>(1, std::min<long long>(groups, (long long)per_sm * sms));
+}
+
+int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py) {
+    switch (nw) {
+        case 16: return bf16 ? tc_grid<16, true>(kp, scan_px, scan_py) : tc_grid<16, false>(kp, scan_px, scan_py);
+        case 32: return bf16 ? tc_grid<32, true>(kp, scan_px, scan_py) : tc_grid<32, false>(kp, scan_px, scan_py);
+        case 64: return bf16 ? tc_grid<64, true>(kp, scan_px, scan_py) : tc_grid<64, false>(kp, scan_px, scan_py);
+        default: return 0;
+    }
+}
+
+size_t scan_tc_win_bytes(int nw, int grid) { return (size_t)grid * TcCfg<16>::G * nw * nw * sizeof(float2); }
+
+template <int NW, bool BF>
+static cudaError_t tc_launch(int grid, const ScanArgs &a, cudaStream_t s) {
+    using C = TcCfg<NW>;
+    const size_t smem = C::smem(a.kp);
+    cudaError_t e = cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_scan_tc<NW, BF><<<grid, C::BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tc(int nw, int bf16, int grid, const ScanArgs &a, cudaStream_t s) {
+    if (grid <= 0 || a.kp % 16 || a.kp < 2 * a.n_beams || !a.S16 || !a.beam_scale || !a.win) return cudaErrorInvalidValue;
+    switch (nw) {
+        case 16: return bf16 ? tc_launch<16, true>(grid, a, s) : tc_launch<16, false>(grid, a, s);
+        case 32: return bf16 ? tc_launch<32, true>(grid, a, s) : tc_launch<32, false>(grid, a, s);
+        case 64: return bf16 ? tc_launch<64, true>(grid, a, s) : tc_launch<64, false>(grid, a, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace prism

@@ -74,7 +74,23 @@ struct ScanArgs {
     int nbins;
     int n_probes;
     int probe0;
+    // 16-bit mode (tensor-core beam sum)
+    const void *S16;           // [ny_s * nx_s][kp] 16-bit (re, im) of each beam, zero-padded beams
+    const float *beam_scale;   // [B] power of two: S_b = S16_b * beam_scale[b]
+    float2 *win;               // window scratch [grid][probes per group][nw][nw]
+    int *err;                  // device error word (a bounded wait that ran out sets bit 0)
+    int kp;                    // K = 2 * roundup(B, 8)
+    int scan_px, scan_py;      // probe raster, probe index = row * scan_px + col
     Tw64 tw;
+};
+
+// FP32 S of one beam batch -> per-beam scale and pixel-major 16-bit S
+struct QuantArgs {
+    const float2 *S;           // [nb][npix]
+    void *S16;                 // [npix][kp]
+    float *scale;              // [B]
+    int beam0, nb, npix, kp;
+    int bf16;                  // 0: FP16, 1: BF16
 };
 
 struct ShiftArgs {
@@ -102,6 +118,16 @@ cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
 cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);
+// 16-bit mode (kernels_tc.cu)
+cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s);
+cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp,
+                              int bf16, cudaStream_t s);
+cudaError_t launch_scan_tc(int nw, int bf16, int grid, const ScanArgs &a, cudaStream_t s);
+bool scan_tc_supported(int nw);
+// persistent grid of the tensor-core scan (resident CTAs, at most the probe groups), 0 if it does
+// not fit; window scratch bytes for that grid
+int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py);
+size_t scan_tc_win_bytes(int nw, int grid);
 // smallest scan-window / FFT sizes the kernels are instantiated for
 bool row_supported(int n);
 bool col_supported(int n);

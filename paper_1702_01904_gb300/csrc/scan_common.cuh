@@ -1,0 +1,173 @@
+// scan_common.cuh -- pieces shared by the grouped PRISM scan kernels (FP32 CUDA-core contraction
+// and FP16 tensor-core contraction): async copies, probe-group geometry, coefficients and the
+// per-window epilogue (window FFT, full diffraction pattern, annular bins).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "params.h"
+
+namespace prism {
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+// 16-byte copy through L1 (sectors shared by neighbouring copies are fetched once)
+__device__ __forceinline__ void cp_async16_ca(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Sum over one warp of per-lane FP32 partial sums, fixed xor-shuffle tree (every lane gets the
+// total).  Pairwise: relative error <= (terms per lane + 5) * 2^-24 for non-negative terms.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Geometry of a group of up to G consecutive probes (thread 0 only).  Window origins follow
+// Eq. RegionBounds in FP64; the union tile of the group's windows, relative to probe 0, starts on
+// an even column with an even width (16-byte aligned pixel pairs).  meta layout:
+//   [0] sub-groups (1: whole group on one tile, else one per probe)  [1] tile width  [2] tile height
+//   [3] tile x origin  [4] tile y origin  [8+p] window x origin  [16+p] window y origin
+//   [24+p] window x offset in the tile  [32+p] window y offset in the tile  [40+p] output row (p0 + p)
+template <int NW, int G, int D, int MAXTILE>
+__device__ void group_geometry(const ScanArgs &a, int p0, int gn, int *meta) {
+    int sx[G], sy[G];
+    for (int p = 0; p < gn; ++p) {
+        sx[p] = ((int)floor(a.x0[p0 + p] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
+        sy[p] = ((int)floor(a.y0[p0 + p] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
+    }
+    int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0, dx[G], dy[G];
+    for (int p = 0; p < gn; ++p) {
+        dx[p] = ((sx[p] - sx[0] + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2;
+        dy[p] = ((sy[p] - sy[0] + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2;
+        dxmin = min(dxmin, dx[p]);
+        dxmax = max(dxmax, dx[p]);
+        dymin = min(dymin, dy[p]);
+        dymax = max(dymax, dy[p]);
+    }
+    const int tx0 = (sx[0] + dxmin) & (a.nx_s - 1);
+    const int shift = tx0 & 1;  // extra leading column to reach an even origin
+    const int tw = (dxmax - dxmin + NW + shift + 1) & ~1;
+    const int th = dymax - dymin + NW;
+    const bool fits = tw <= NW + D && th <= NW + D && tw * th <= MAXTILE;
+    meta[0] = fits ? 1 : gn;
+    for (int p = 0; p < G; ++p) {
+        meta[8 + p] = sx[p < gn ? p : 0];
+        meta[16 + p] = sy[p < gn ? p : 0];
+        meta[24 + p] = p < gn ? dx[p] - dxmin + shift : 0;
+        meta[32 + p] = p < gn ? dy[p] - dymin : 0;
+        meta[40 + p] = p0 + p;
+    }
+    meta[1] = tw;
+    meta[2] = th;
+    meta[3] = tx0 - shift;
+    meta[4] = (sy[0] + dymin) & (a.ny_s - 1);
+}
+
+// alpha[p][b] = A(q_b - q_t) e^{-i chi} e^{-2 pi i q_b.(r0_p - h tan theta)} for the group's probes
+// (phase in FP64, reduced before the FP32 sincos); zero for probes past the end.
+template <int G>
+__device__ void group_coefficients(const ScanArgs &a, int p0, int gn, float2 *alpha, int tid, int nthreads) {
+    for (int i = tid; i < G * a.n_beams; i += nthreads) {
+        const int p = i / a.n_beams, b = i - p * a.n_beams;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < gn) {
+            double c = a.qx[b] * (a.x0[p0 + p] - a.shift_x) + a.qy[b] * (a.y0[p0 + p] - a.shift_y);
+            c -= rint(c);
+            float s, co;
+            sincospif(-2.0f * (float)c, &s, &co);
+            v = cmul(__ldg(a.base + b), make_float2(co, s));
+        }
+        alpha[i] = v;
+    }
+}
+
+// Window epilogue for nwin windows win[p][NW][PW] (psi in real space on entry): 2-D FFT of every
+// window (rows then columns, two-level FFTs), then the full diffraction pattern (if a.cbed) and
+// the annular bins (if a.out): one warp per (probe, bin), FP32 pairwise sums, FP64 scale.
+// Window p is written to output row oidx[p] (shared memory).  G bounds nwin.
+template <int NW, int BLOCK, int G, int PW>
+__device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, const float2 *twf, int nwin,
+                                const int *oidx, int tid) {
+    using FS = FftShape<NW>;
+    using Fwd = FwdFft<NW>;
+    constexpr int T = FS::T, E = FS::E;
+    constexpr int RSLOTS = BLOCK / T, CW = BLOCK / T;
+    {
+        const int slot = tid / T, t = tid % T;
+        WarpExchange<FS::N1, FS::N2, T> exr{ex + slot * (FS::N1 * (FS::N2 + 1))};
+#pragma unroll 1
+        for (int r0 = 0; r0 < G * NW; r0 += RSLOTS) {
+            const int row = r0 + slot;
+            const bool ok = row < nwin * NW;
+            const int rr = ok ? row : row % NW;
+            float2 v[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = win[rr * PW + Fwd::in_elem(r, t)];
+            Fwd::run(v, t, twf, a.tw, exr);
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) win[rr * PW + Fwd::out_elem(r, t)] = v[r];
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const int c = tid % CW, t = tid / CW;
+        ColExchange<FS::N1, FS::N2, CW> exc{ex, c};
+#pragma unroll 1
+        for (int c0 = 0; c0 < G * NW; c0 += CW) {
+            const int col = c0 + c;
+            const bool ok = col < nwin * NW;
+            const int cc = ok ? col : col % NW;
+            float2 *w = win + (cc / NW) * NW * PW;
+            const int x = cc % NW;
+            float2 v[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = w[Fwd::in_elem(r, t) * PW + x];
+            Fwd::run(v, t, twf, a.tw, exc);
+            __syncthreads();
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) w[Fwd::out_elem(r, t) * PW + x] = v[r];
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
+    if (a.cbed) {
+        const float fnorm = (float)a.inv_norm;
+        for (int i = tid; i < nwin * NW * NW; i += BLOCK) {
+            const int p = i >> (2 * LNW), u = i & (NW * NW - 1);
+            const float2 z = win[(p * NW + (u >> LNW)) * PW + (u & (NW - 1))];
+            a.cbed[(size_t)oidx[p] * NW * NW + u] = (z.x * z.x + z.y * z.y) * fnorm;
+        }
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int j = (a.out ? warp : nwin * a.nbins); j < nwin * a.nbins; j += BLOCK / 32) {
+        const int p = j / a.nbins, k = j - p * a.nbins;
+        const float2 *w = win + p * NW * PW;
+        float sum = 0.f;
+        const int e = __ldg(a.bin_off + k + 1);
+        for (int i = __ldg(a.bin_off + k) + lane; i < e; i += 32) {
+            const int u = __ldg(a.bin_idx + i);
+            const float2 z = w[(u >> LNW) * PW + (u & (NW - 1))];
+            sum += z.x * z.x + z.y * z.y;
+        }
+        sum = warp_sum(sum);
+        if (lane == 0) {
+            const float val = (float)((double)sum * a.inv_norm);
+            float *o = a.out + (size_t)oidx[p] * a.nbins + k;
+            *o = a.accumulate ? *o + a.acc_w * val : val;
+        }
+    }
+}
+
+}  // namespace prism

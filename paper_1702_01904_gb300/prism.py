@@ -23,8 +23,12 @@ PRISM_ERR_CUDA = -3
 PRISM_ERR_DEVICE = -4
 PRISM_ERR_UNSUPPORTED = -5
 
-PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN = range(6)
-PRISM_K_COUNT = 6
+PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN, PRISM_K_QUANT = range(7)
+PRISM_K_COUNT = 7
+
+PRISM_PRECISION_FP32 = 0
+PRISM_PRECISION_FP16 = 1
+PRISM_PRECISION_BF16 = 2
 
 # every entry point declared in include/prism.h
 EXPORTED = [
@@ -32,7 +36,7 @@ EXPORTED = [
     "prism_build_smatrix", "prism_build_smatrix_host", "prism_scan_run", "prism_scan_run_host",
     "prism_scan_run_cbed", "prism_scan_run_accumulate",
     "multislice_scan_run", "multislice_scan_run_noalloc", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
-    "prism_plan_smatrix", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
+    "prism_plan_smatrix", "prism_plan_smatrix_copy", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
@@ -50,7 +54,8 @@ class PrismGrid(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("n_slices", c_int),
                 ("cell_x", c_double), ("cell_y", c_double), ("dz", c_double),
                 ("slice_dz", POINTER(c_double)), ("kv", c_double), ("f", c_int),
-                ("downsample", c_int), ("aa_frac", c_double), ("alpha_max_mrad", c_double)]
+                ("downsample", c_int), ("aa_frac", c_double), ("alpha_max_mrad", c_double),
+                ("precision", c_int)]
 
 
 class PrismProbe(ctypes.Structure):
@@ -118,6 +123,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_smatrix_bytes": (c_int, [P, POINTER(c_size_t)]),
         "prism_plan_beams": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int]),
         "prism_plan_smatrix": (c_int, [P, POINTER(P)]),
+        "prism_plan_smatrix_copy": (c_int, [P, P]),
         "prism_plan_transmission": (c_int, [P, POINTER(P)]),
         "prism_wavelength": (c_double, [c_double]),
         "prism_interaction_constant": (c_double, [c_double]),
@@ -167,8 +173,9 @@ def _stream(s):
 
 # ------------------------------------------------------------------ struct helpers
 def make_grid(nx, ny, n_slices, cell_x, cell_y, dz, kv, f=1, downsample=2, aa_frac=0.5,
-              alpha_max_mrad=20.0, slice_dz=None):
-    g = PrismGrid(nx, ny, n_slices, cell_x, cell_y, dz, None, kv, f, downsample, aa_frac, alpha_max_mrad)
+              alpha_max_mrad=20.0, slice_dz=None, precision=PRISM_PRECISION_FP32):
+    g = PrismGrid(nx, ny, n_slices, cell_x, cell_y, dz, None, kv, f, downsample, aa_frac, alpha_max_mrad,
+                  precision)
     if slice_dz is not None:
         arr = np.ascontiguousarray(slice_dz, dtype=np.float64)
         g._keep = arr
@@ -176,9 +183,9 @@ def make_grid(nx, ny, n_slices, cell_x, cell_y, dz, kv, f=1, downsample=2, aa_fr
     return g
 
 
-def grid_from_workload(w):
+def grid_from_workload(w, precision=PRISM_PRECISION_FP32):
     return make_grid(w.nx, w.ny, w.n_slices, w.cell_x, w.cell_y, w.dz, w.kv, w.f, w.downsample,
-                     w.aa_frac, w.alpha_mrad)
+                     w.aa_frac, w.alpha_mrad, precision=precision)
 
 
 def make_probe(alpha_mrad, c1=0.0, c3=0.0, tilt_x=0.0, tilt_y=0.0):
@@ -286,6 +293,10 @@ def prism_plan_smatrix(plan):
     p = c_void_p()
     _check(load().prism_plan_smatrix(plan, byref(p)))
     return p.value
+
+
+def prism_plan_smatrix_copy(plan, out_dev):
+    _check(load().prism_plan_smatrix_copy(plan, _ptr(out_dev)))
 
 
 def prism_plan_transmission(plan):

@@ -67,22 +67,28 @@ class PrismSimulation:
         P.prism_scan_run_host(self.plan, probe, P.make_scan(px, py, x0, y0), det, out_host)
         return out_host
 
-    def scan_cbed(self, probe, x0, y0, out: torch.Tensor | None = None):
+    def scan_cbed(self, probe, x0, y0, out: torch.Tensor | None = None, px=None, py=None):
         """Full window diffraction patterns [P][nw][nw] (FFT order), units of incident intensity."""
         x0 = np.ascontiguousarray(x0, np.float64)
         y0 = np.ascontiguousarray(y0, np.float64)
         n = len(x0)
+        px = n if px is None else px
+        py = 1 if py is None else py
+        assert px * py == n
         nw = self.info.nw_x
         if out is None:
             out = torch.empty((n, self.info.nw_y, nw), dtype=torch.float32, device="cuda")
-        P.prism_scan_run_cbed(self.plan, probe, P.make_scan(n, 1, x0, y0), out)
+        P.prism_scan_run_cbed(self.plan, probe, P.make_scan(px, py, x0, y0), out)
         return out
 
-    def scan_accumulate(self, probe, x0, y0, det, weight, out: torch.Tensor):
+    def scan_accumulate(self, probe, x0, y0, det, weight, out: torch.Tensor, px=None, py=None):
         """out += weight * (annular bins of this S-matrix), e.g. frozen-phonon averaging."""
         x0 = np.ascontiguousarray(x0, np.float64)
         y0 = np.ascontiguousarray(y0, np.float64)
-        P.prism_scan_run_accumulate(self.plan, probe, P.make_scan(len(x0), 1, x0, y0), det, weight, out)
+        px = len(x0) if px is None else px
+        py = 1 if py is None else py
+        assert px * py == len(x0)
+        P.prism_scan_run_accumulate(self.plan, probe, P.make_scan(px, py, x0, y0), det, weight, out)
         return out
 
     def sync(self):
@@ -93,12 +99,14 @@ class PrismSimulation:
         return P.prism_plan_beams(self.plan)
 
     def smatrix(self) -> torch.Tensor:
-        """Copy of the S-matrix as complex64 [B][ny_s][nx_s] (waits for the plan's stream)."""
-        self.sync()
+        """Copy of the S-matrix as complex64 [B][ny_s][nx_s] (in 16-bit mode the stored values times
+        their beam scales); waits for the plan's stream."""
         i = self.info
-        v = torch.as_tensor(_CudaView(P.prism_plan_smatrix(self.plan), (i.n_beams, i.ny_s, i.nx_s, 2), "<f4"),
-                            device="cuda")
-        return torch.view_as_complex(v.clone())
+        out = torch.empty((i.n_beams, i.ny_s, i.nx_s, 2), dtype=torch.float32, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        P.prism_plan_smatrix_copy(self.plan, out)
+        self.sync()
+        return torch.view_as_complex(out)
 
     def transmission(self) -> torch.Tensor:
         """Copy of the transmission functions complex64 [H][ny][nx] (waits for the plan's stream)."""

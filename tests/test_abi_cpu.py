@@ -63,7 +63,7 @@ int main(void) {
   printf("prism_detector %zu\\n", sizeof(prism_detector));
   printf("prism_info %zu\\n", sizeof(prism_info));
   F(prism_grid, cell_x) F(prism_grid, slice_dz) F(prism_grid, kv) F(prism_grid, f) F(prism_grid, aa_frac)
-  F(prism_grid, alpha_max_mrad) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
+  F(prism_grid, alpha_max_mrad) F(prism_grid, precision) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
   F(prism_info, wavelength) F(prism_info, device_bytes)
   return 0;
 }
@@ -86,3 +86,21 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(P, "_lib", None)
     with pytest.raises(RuntimeError):
         P.load(str(tmp_path / "nope.so"))
+
+
+def test_plan_arguments_rejected_before_any_device_call():
+    """Argument checks of prism_plan_create run on the host before the first CUDA call."""
+    def status(**over):
+        g = P.make_grid(64, 64, 1, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0)
+        for k, v in over.items():
+            setattr(g, k, v)
+        with pytest.raises(P.PrismError) as e:
+            P.prism_plan_create(g)
+        return e.value.status
+    assert status(precision=3) == P.PRISM_ERR_INVALID
+    assert status(precision=-1) == P.PRISM_ERR_INVALID
+    # 16-bit S needs a 16, 32 or 64 pixel window: 64 px / 2 / f=4 is 8
+    assert status(precision=P.PRISM_PRECISION_FP16, f=4) == P.PRISM_ERR_UNSUPPORTED
+    assert status(precision=P.PRISM_PRECISION_BF16, f=4) == P.PRISM_ERR_UNSUPPORTED
+    assert status(nx=100) == P.PRISM_ERR_UNSUPPORTED
+    assert status(f=0) == P.PRISM_ERR_INVALID
