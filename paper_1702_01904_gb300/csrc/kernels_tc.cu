@@ -13,6 +13,9 @@
 
 namespace prism {
 
+// an mbarrier wait gives up (and the kernel reports through its error word) after about 1 s
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;
+
 // ------------------------------------------------------------------ self-test
 // One MMA D[128][16] = A[128][16] B[16][16]^T with small-integer FP16 operands (exact in FP32),
 // operands in the K-major core-matrix layout of tc.cuh.  The operand buffer is oversized so that
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(float *out, int *status) {
         const uint64_t bd = tc::smem_desc(tc::smem_u32(B), 2 * 128, 128);
         tc::mma_f16(taddr, ad, bd, tc::idesc_f16_f32(128, 16), 0);
         tc::mma_commit(mbar);
-        *flag = tc::mbar_wait_bounded(mbar, 0, 1u << 22) ? 1 : -1;
+        *flag = tc::mbar_wait_bounded(mbar, 0, TC_WAIT_CYCLES) ? 1 : -1;
     }
     __syncthreads();
     tc::fence_after_sync();
@@ -222,10 +225,10 @@ cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, 
 template <int NW>
 struct TcCfg {
     using FS = FftShape<NW>;
-    static constexpr int GX = 8, GY = 2, G = GX * GY, N = 2 * G;
+    static constexpr int GX = 8, GY = 4, G = GX * GY, N = 2 * G;
     static constexpr int BLOCK = 256;
     static constexpr int STAGES = 3;
-    static constexpr int KCMAX = 96;                        // K (16-bit values) per ring stage
+    static constexpr int KCMAX = 64;                        // K (16-bit values) per ring stage
     static constexpr int STAGE_BYTES = 128 * KCMAX * 2;     // 128 pixels x KCMAX
     static constexpr int RING = STAGES * STAGE_BYTES;
     static constexpr int PW = NW + 8;
@@ -250,10 +253,9 @@ struct TcCfg {
 // the tile  [104+p] y offset in the tile  [136+p] probe index or -1; [168+e] slot of the e-th
 // probe, [200+e] its probe index
 
-constexpr uint32_t TC_POLL_LIMIT = 1u << 22;  // mbarrier polls before a wait gives up
 
 template <int NW, bool BF>
-__global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ ScanArgs a) {
+__global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
     using C = TcCfg<NW>;
     constexpr int G = C::G, N = C::N, GX = C::GX, GY = C::GY, BLOCK = C::BLOCK, PW = C::PW, S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -393,19 +395,22 @@ __global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ Scan
             // accumulator of M tile mt -> window scratch of every probe whose window holds the pixel
             auto drain = [&](int mt) {
                 tc::fence_after_sync();
-                const int q = warp & 3, h = warp >> 2;
-                float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((mt & 1) * N + h * 16), v);
+                const int q = warp & 3, h = warp >> 2;  // lane quarter, half of the N columns
                 const int idx = mt * 128 + 32 * q + lane;
-                if (idx < npx) {
-                    const int ty = idx / tw, tx = idx - ty * tw;
+                const int ty = idx / tw, tx = idx - ty * tw;
 #pragma unroll
-                    for (int pp = 0; pp < 8; ++pp) {
-                        const int p = 8 * h + pp;
-                        const bool act = uni ? meta[136 + p] >= 0 : p == sg;
-                        const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
-                        if (act && (unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
-                            a.win[((size_t)blockIdx.x * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
+                for (int c16 = 0; c16 < N / 32; ++c16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((mt & 1) * N + h * (N / 2) + c16 * 16), v);
+                    if (idx < npx) {
+#pragma unroll
+                        for (int pp = 0; pp < 8; ++pp) {
+                            const int p = h * (G / 2) + c16 * 8 + pp;
+                            const bool act = uni ? meta[136 + p] >= 0 : p == sg;
+                            const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
+                            if (act && (unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
+                                a.win[((size_t)blockIdx.x * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
+                        }
                     }
                 }
                 tc::fence_before_sync();
@@ -433,13 +438,13 @@ __global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ Scan
                     tc::mma_commit(&mbar[s % S]);
                 }
                 // ring slot (s + 2) % S was read by step s - 1: wait for its MMAs before refilling it
-                if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_POLL_LIMIT)) fail();
+                if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
                 load(ls + 2);
                 if (c == 0 && mt >= 1) drain(mt - 1);
             }
             st = st0 + nsteps;
             if (dead) break;
-            if (!tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_POLL_LIMIT)) fail();
+            if (!tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
             drain(nmt - 1);
             if (__syncthreads_or(my_fail)) dead = true;
         }
@@ -450,10 +455,28 @@ __global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ Scan
         const int nvalid = meta[5];
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
             const int ne = min(C::EW, nvalid - e0);
-            for (int i = tid; i < ne * NW * NW; i += BLOCK) {
-                const int e = i / (NW * NW), u = i - e * (NW * NW);
-                const int slot = meta[168 + e0 + e];
-                win[(e * NW + u / NW) * PW + (u & (NW - 1))] = __ldcg(a.win + ((size_t)blockIdx.x * G + slot) * (NW * NW) + u);
+            // pixel pairs, VEC independent 16-byte loads in flight per thread
+            constexpr int VEC = 8;
+            for (int i0 = 0; i0 < ne * NW * NW / 2; i0 += BLOCK * VEC) {
+                float4 v[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const int i = i0 + tid + k * BLOCK;
+                    if (i < ne * NW * NW / 2) {
+                        const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
+                        v[k] = __ldcg(reinterpret_cast<const float4 *>(a.win + ((size_t)blockIdx.x * G + meta[168 + e0 + e]) * (NW * NW) + u));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const int i = i0 + tid + k * BLOCK;
+                    if (i < ne * NW * NW / 2) {
+                        const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
+                        float2 *d = win + (e * NW + u / NW) * PW + (u & (NW - 1));
+                        d[0] = make_float2(v[k].x, v[k].y);
+                        d[1] = make_float2(v[k].z, v[k].w);
+                    }
+                }
             }
             __syncthreads();
             window_epilogue<NW, BLOCK, C::EW, PW>(a, win, ex, twf, ne, meta + 200 + e0, tid);
@@ -462,7 +485,7 @@ __global__ void __launch_bounds__(256, 2) k_scan_tc(const __grid_constant__ Scan
     }
     cp_async_wait<0>();
     __syncthreads();
-    if (dead && tid == 0 && st > 0) tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_POLL_LIMIT);
+    if (dead && tid == 0 && st > 0) tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_WAIT_CYCLES);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -477,11 +500,25 @@ static int tc_grid(int kp, int scan_px, int scan_py) {
     const size_t smem = C::smem(kp);
     if (smem > 227 * 1024) return 0;
     if (cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan_tc<NW, BF>, C::BLOCK, smem) != cudaSuccess || per_sm < 1)
+    if (cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    // Resident CTAs per SM from the kernel's own limits.  The runtime's occupancy query reports one
+    // CTA per SM for every kernel that uses tcgen05, but CTAs whose registers, shared memory and
+    // TMEM columns fit do run side by side (each allocates TMEM_COLS of the SM's 512 columns; an
+    // allocation that does not fit waits for another CTA to free its columns).
+    cudaFuncAttributes fa;
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, k_scan_tc<NW, BF>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
         return 0;
+    const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * C::BLOCK);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+    const int by_tmem = 512 / (int)C::TMEM_COLS;
+    const int per_sm = std::min(std::min(by_regs, by_smem), std::min(by_tmem, 2048 / C::BLOCK));
+    if (per_sm < 1) return 0;
     const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
     return (int)std::max<long long>(1, std::min<long long>(groups, (long long)per_sm * sms));
 }
@@ -496,12 +533,15 @@ int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py) {
 }
 
 size_t scan_tc_win_bytes(int nw, int grid) { return (size_t)grid * TcCfg<16>::G * nw * nw * sizeof(float2); }
+static_assert(TcCfg<16>::G == TcCfg<32>::G && TcCfg<16>::G == TcCfg<64>::G, "one group size for every window");
 
 template <int NW, bool BF>
 static cudaError_t tc_launch(int grid, const ScanArgs &a, cudaStream_t s) {
     using C = TcCfg<NW>;
     const size_t smem = C::smem(a.kp);
     cudaError_t e = cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     k_scan_tc<NW, BF><<<grid, C::BLOCK, smem, s>>>(a);
     return cudaGetLastError();

@@ -121,13 +121,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false if the phase did not complete within `limit` polls
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (mbar_try_wait(mbar, parity)) return true;
-        __nanosleep(64);
-    }
-    return false;
+// bounded wait: false if the phase did not complete within `limit_cycles` SM clock cycles
+// (try_wait itself suspends the thread for a short hardware-defined time between checks)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit_cycles) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity))
+        if (clock64() - t0 > limit_cycles) return false;
+    return true;
 }
 
 }  // namespace tc
