@@ -237,24 +237,31 @@ def serving_run(w, V_host, n_requests=40, rate=20.0, seed=5):
                    "a-C cell at 0.2-0.5 A steps (up to 62500 probes) from one resident S-matrix"}
 
 
-def ncu_case():
+def ncu_case(precision="fp32"):
     import torch
 
     from paper_1702_01904_gb300 import prism as PR
     from paper_1702_01904_gb300 import specimens
     from paper_1702_01904_gb300.runtime import PrismSimulation
 
-    w = specimens.workload_amorphous_carbon(n_slices=4, alpha_mrad=9.0)
+    # FP32: 25 beams (alpha_max 9 mrad), the first 10 scan rows (2000 probes).  16-bit: the full
+    # 129-beam set, so that the tensor-core scan sees the real K, and the first 52 rows (10400
+    # probes, 325 groups of 8 x 4: every resident CTA busy).  Both: 4 slices.
+    half = precision != "fp32"
+    w = specimens.workload_amorphous_carbon(n_slices=4, alpha_mrad=20.0 if half else 9.0)
     V = torch.from_numpy(w.potential()).cuda()
     x0, y0 = w.scan_positions()
-    sim = PrismSimulation(PR.grid_from_workload(w))
+    code = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16}[precision]
+    sim = PrismSimulation(PR.grid_from_workload(w, precision=code))
     det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
     probe = PR.make_probe(w.alpha_mrad)
-    for _ in range(2):  # launches per pass: transmission, 4 x (row, col), row_out, scan
+    rows = 52 if half else 10
+    n = 200 * rows
+    for _ in range(2):  # launches per pass: transmission, 4 x (row, col), row_out, [quantize], scan
         sim.build(V)
-        sim.scan(probe, x0[:2000], y0[:2000], det)
+        sim.scan(probe, x0[:n], y0[:n], det, px=200, py=rows)
     sim.sync()
-    print(json.dumps({"ncu_case": "ok", "beams": sim.info.n_beams, "launches": sim.launches()}))
+    print(json.dumps({"ncu_case": "ok", "precision": precision, "beams": sim.info.n_beams, "launches": sim.launches()}))
     sim.close()
     return 0
 
@@ -269,12 +276,16 @@ def main():
     ap.add_argument("--ms-probes", type=int, default=1024, help="probes timed for the multislice baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
+                    help="S-matrix storage / beam-sum arithmetic of the headline line")
+    ap.add_argument("--no-precision-leg", action="store_true",
+                    help="skip timing the other precisions beside the headline one")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the profiling case twice and exit: the same 1024^2 a-C grid, 4 slices, "
                          "alpha_max 9 mrad (25 beams, 200 MB wave stack), 2000 probes")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case()
+        return ncu_case(args.precision)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -331,7 +342,9 @@ def main():
     V = V_host.cuda()
     x0, y0 = w.scan_positions()
     P = len(x0)
-    grid = PR.grid_from_workload(w)
+    PREC = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16}
+    grid = PR.grid_from_workload(w, precision=PREC[args.precision])
+    grid32 = PR.grid_from_workload(w)
     det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
     probe = PR.make_probe(w.alpha_mrad)
     stream = torch.cuda.Stream()
@@ -409,15 +422,58 @@ def main():
         nms = min(args.ms_probes, P)
         sel = np.linspace(0, P - 1, nms).astype(np.int64)
         ms_out = torch.empty((nms, DET["nbins"]), dtype=torch.float32, device="cuda")
-        multislice(grid, V, probe, x0[sel][:8], y0[sel][:8], det, stream=stream, out=ms_out[:8])
+        multislice(grid32, V, probe, x0[sel][:8], y0[sel][:8], det, stream=stream, out=ms_out[:8])
         stream.synchronize()
         m0 = torch.cuda.Event(enable_timing=True)
         m1 = torch.cuda.Event(enable_timing=True)
         m0.record(stream)
-        multislice(grid, V, probe, x0[sel], y0[sel], det, stream=stream, out=ms_out, scratch_bytes=2 << 30)
+        multislice(grid32, V, probe, x0[sel], y0[sel], det, stream=stream, out=ms_out, scratch_bytes=2 << 30)
         m1.record(stream)
         stream.synchronize()
         ms_ms = m0.elapsed_time(m1)
+
+        # the other precisions on the same workload: step time, scan time, and the deviation of
+        # every detector image from this run's headline output
+        prec_leg = {}
+        if rank == 0 and not args.no_precision_leg:
+            ref_out = out.cpu().numpy().astype(np.float64)
+            for name in ("fp32", "fp16", "bf16"):
+                if name == args.precision:
+                    continue
+                s2 = PrismSimulation(PR.grid_from_workload(w, precision=PREC[name]), 0, stream)
+                o2 = torch.empty_like(out)
+
+                def step2():
+                    s2.build(V)
+                    s2.scan(probe, x0, y0, det, out=o2, px=w.scan_px, py=w.scan_py)
+
+                for _ in range(2):
+                    step2()
+                stream.synchronize()
+                s2.reset_stats()
+                s2.set_profiling(True)
+                q0 = torch.cuda.Event(enable_timing=True)
+                q1 = torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                for _ in range(args.steps):
+                    step2()
+                q1.record(stream)
+                stream.synchronize()
+                st2 = s2.kernel_stats()
+                t2 = q0.elapsed_time(q1) / args.steps
+                o2n = o2.cpu().numpy().astype(np.float64)
+                mean = ref_out.mean(0)
+                dev = {}
+                for floor in (1e-3, 1e-5):
+                    sel2 = mean >= floor
+                    e = np.linalg.norm(o2n[:, sel2] - ref_out[:, sel2], axis=0) / np.linalg.norm(ref_out[:, sel2], axis=0)
+                    dev[f"images_mean_ge_{floor:g}"] = {"max_rel_l2": float(e.max()), "median_rel_l2": float(np.median(e)),
+                                                        "images": int(sel2.sum())}
+                scan2 = st2["scan"][1] / max(st2["scan"][0], 1)
+                prec_leg[name] = {"value": P / (t2 / 1000.0), "unit": UNIT, "ms_per_step": t2, "scan_ms": scan2,
+                                  "build_ms": t2 - scan2, "smatrix_bytes": PR.prism_plan_smatrix_bytes(s2.plan),
+                                  "deviation_from_headline": dev}
+                s2.close()
         sim.close()
 
     value = world * P * args.steps / (total_ms / 1000.0)
@@ -440,6 +496,8 @@ def main():
         "row_plane": Bn * px * 8 + px * 8,
         "row_out": Bn * (px // 2) * 8 + Bn * (px // 4) * 8,
         "transmission": w.n_slices * px * (4 + 8),
+        # 16-bit mode: FP32 S of the batch read twice (scale, convert), 16-bit pixel-major S written
+        "quantize": 2 * Bn * (px // 4) * 8 + (px // 4) * 2 * ((Bn + 7) // 8 * 8) * 2,
     }
     rows = {}
     for name, (n_l, t_ms) in stats.items():
@@ -453,6 +511,15 @@ def main():
             gbs = alg[name] / (r["mean_ms"] / 1000.0) / 1e9
             roof_all[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                               "frac": gbs / hbm_peak, "bytes_per_launch": alg[name], **r}
+        elif name == "scan" and args.precision != "fp32":
+            # beam sum on the tensor cores: 8 real flops per complex MAC, against the measured dense
+            # 16-bit rate (sustained: the scan runs inside a seconds-long loop of steps)
+            nw = w.nx // w.downsample // w.f
+            flops = P * 8.0 * Bn * nw * nw
+            peak_tf = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
+            tf = flops / (r["mean_ms"] / 1000.0) / 1e12
+            roof_all[name] = {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                              "frac": tf / peak_tf, "flops_per_launch": flops, **r}
         elif name == "scan":
             # ALU-bound: 8 flops per complex MAC of the beam sum (a7) + window FFTs
             nw = w.nx // w.downsample // w.f
@@ -466,7 +533,7 @@ def main():
     rd = roof_all[dom]
     roofline = {"bound": rd["bound"], "achieved": rd["achieved"], "peak": rd["peak"], "unit": rd["unit"],
                 "frac": rd["frac"], "traffic": ncu_traffic(dom), "kernel": dom,
-                "peak_source": f"{peak_note} ({'MEASURED_PEAKS.json hbm_gbs' if rd['unit'] == 'GB/s' else '152 SMs x 128 FP32 lanes x 2 x median SM clock'})"}
+                "peak_source": f"{peak_note} ({'MEASURED_PEAKS.json hbm_gbs' if rd['unit'] == 'GB/s' else ('MEASURED_PEAKS.json bf16 sustained' if rd['bound'] == 'tensor' else '152 SMs x 128 FP32 lanes x 2 x median SM clock')})"}
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -484,7 +551,7 @@ def main():
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16 S / f32 accumulate", "bf16": "bf16 S / f32 accumulate"}[args.precision],
             "data": "synthetic (seeded amorphous-carbon phantom; the paper's Pt/a-C coordinates are not available)",
             "config": {**workload_config(w, Bn), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": world * P * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
@@ -494,6 +561,10 @@ def main():
             "roofline": roofline,
             "roofline_all": roof_all,
             "cpu_baseline": cpu,
+            "precision": {"headline": args.precision, "others": prec_leg,
+                          "note": "16-bit modes store S in FP16/BF16 with per-beam power-of-two scales and run the beam "
+                                  "sum on tcgen05 tensor cores (FP32 accumulation); their error against the FP64 oracle "
+                                  "per detector image is gated in tests/test_gpu_precision.py"},
             "multislice": {"probes_per_s": ms_probes_s, "probes_timed": nms, "ms": ms_ms,
                            "speedup_prism_vs_multislice": value / world / ms_probes_s},
             "beams_slices_per_s": Bn * w.n_slices / (build_ms / 1000.0),
