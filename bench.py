@@ -237,6 +237,63 @@ def serving_run(w, V_host, n_requests=40, rate=20.0, seed=5):
                    "a-C cell at 0.2-0.5 A steps (up to 62500 probes) from one resident S-matrix"}
 
 
+def batch_leg(n_cells=64, runs=2, n_branches=4):
+    """The batched workload: n_cells seeded uneven cells (seeds 100...), FP32, one captured CUDA
+    graph per run (prism_batch_*).  Potentials are generated by a spawn process pool."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_1702_01904_gb300 import prism as PR
+    from paper_1702_01904_gb300 import specimens
+    from paper_1702_01904_gb300.runtime import Batch
+
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        made = pool.map(specimens.batch_cell_potential, range(100, 100 + n_cells))
+    gen_s = time.perf_counter() - t0
+    det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
+    stream = torch.cuda.Stream()
+    cells, beams_slices, probes, mix, build_bytes = [], 0, 0, {}, 0
+    for w, V in made:
+        x0, y0 = w.scan_positions()
+        cells.append(dict(grid=PR.grid_from_workload(w), V=torch.from_numpy(V).cuda(), probe=PR.make_probe(w.alpha_mrad),
+                          x0=x0, y0=y0, px=w.scan_px, py=w.scan_py, det=det))
+        lam = PR.prism_wavelength(w.kv)
+        r = w.alpha_mrad * 1e-3 / (lam * w.f / w.cell_x)
+        k = np.arange(-int(r) - 1, int(r) + 2)
+        nb = int(np.count_nonzero(k[:, None] ** 2 + k[None, :] ** 2 <= r * r * (1 + 1e-12)))
+        beams_slices += nb * w.n_slices
+        # build passes stream the wave stack twice per slice (32 B per beam-pixel) plus t_p
+        build_bytes += nb * w.n_slices * w.nx * w.ny * 32 + w.n_slices * w.nx * w.ny * 8
+        probes += w.scan_px * w.scan_py
+        key = f"{w.nx}px_f{w.f}"
+        mix[key] = mix.get(key, 0) + 1
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b = Batch(cells, n_branches=n_branches, stream=stream)
+        b.run()
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(runs):
+            b.run()
+        e1.record(stream)
+        b.sync()
+        ms = e0.elapsed_time(e1) / runs
+        info = b.info
+        b.close()
+    return {"cells": n_cells, "seeds": f"100..{99 + n_cells}", "size_mix": mix, "runs_timed": runs,
+            "ms_per_run": ms, "cells_per_s": n_cells / (ms / 1000.0), "probes_per_s": probes / (ms / 1000.0),
+            "beams_slices_per_s": beams_slices / (ms / 1000.0), "graph_nodes": info.graph_nodes,
+            "build_pass_bytes_per_run": build_bytes,
+            "build_pass_gbs_over_whole_run": build_bytes / (ms / 1000.0) / 1e9,
+            "kernel_launches_per_run": info.kernel_launches, "branches": info.n_branches,
+            "device_gb": info.device_bytes / 1e9, "potential_generation_s": gen_s,
+            "what": "every cell's transmission + S-matrix build + 16x16-probe scan, FP32, one cudaGraphLaunch per run"}
+
+
 def ncu_case(precision="fp32"):
     import torch
 
@@ -278,6 +335,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
                     help="S-matrix storage / beam-sum arithmetic of the headline line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-cells leg")
+    ap.add_argument("--batch-cells", type=int, default=64)
     ap.add_argument("--no-precision-leg", action="store_true",
                     help="skip timing the other precisions beside the headline one")
     ap.add_argument("--ncu-case", action="store_true",
@@ -539,6 +598,10 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = serving_run(w, V_host)
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_leg(args.batch_cells)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, V_host.numpy(), budget_s=20.0)
@@ -572,6 +635,7 @@ def main():
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                            "what": "one whole step (S-matrix build + 40000-probe scan), device time"},
             "serving": serving,
+            "batch": batch,
             "clocks": clk,
         }
         print(json.dumps(res), flush=True)

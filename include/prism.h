@@ -274,6 +274,49 @@ int prism_server_stats(prism_server *server, prism_server_info *out);
 /* Finish the queued and running requests, release every S-matrix and stop the worker. */
 void prism_server_destroy(prism_server *server);
 
+/* ---- batches of uneven cells: one captured CUDA graph ------------------------------
+ *
+ * Many independent simulations of different sizes, slice counts, f and precision (the paper's
+ * cost model, Calculation Time section, makes small cells launch-bound and large ones
+ * bandwidth-bound) run as one CUDA graph: each cell gets its own plan, all scan inputs are uploaded
+ * at creation, and every cell's transmission, build, quantisation and scan launches are captured
+ * once.  Cells are spread over n_branches parallel graph branches, longest estimated work first
+ * (beams x slices x pixels for the build plus probes x beams x window pixels for the scan), so
+ * small cells run beside large ones.  prism_batch_run is one cudaGraphLaunch.  The paper has no
+ * counterpart; this is the batched form of its algorithm. */
+typedef struct prism_cell {
+    prism_grid grid;          /* the cell (any precision); grid.slice_dz is copied at creation    */
+    const float *V_dev;       /* [n_slices][ny][nx] potential, caller-owned device memory, read at
+                                 every run (its contents may change between runs, not its address) */
+    prism_probe probe;
+    prism_scan scan;          /* positions are copied at creation; px * py may be 0                */
+    prism_detector det;
+    float *out_dev;           /* [py*px][nbins] caller-owned device output, written at every run    */
+} prism_cell;
+
+typedef struct prism_batch_info {
+    int n_cells;
+    int n_branches;
+    size_t graph_nodes;       /* kernel and event nodes of the captured graph                     */
+    long kernel_launches;     /* kernels one run launches                                           */
+    size_t device_bytes;      /* device memory held by the batch's plans                          */
+} prism_batch_info;
+
+typedef struct prism_batch prism_batch;
+
+/* Validate every cell, create its plan (INVALID/UNSUPPORTED as prism_plan_create, with the cell
+ * index in the message), upload its scan inputs and capture the graph.  n_branches in [1, 16]
+ * (0 = min(n_cells, 4)).  hbm_budget_bytes bounds the sum of the plans' device memory (0 = no
+ * limit; BUDGET if exceeded).  The graph is launched into cuda_stream (NULL = legacy default). */
+int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches,
+                       void *cuda_stream, prism_batch **out);
+/* Enqueue one run of the whole batch (asynchronous on the batch's stream). */
+int prism_batch_run(prism_batch *batch);
+/* Wait for the batch's stream; DEVICE if a kernel of any cell raised its error word. */
+int prism_batch_sync(prism_batch *batch);
+int prism_batch_info_get(const prism_batch *batch, prism_batch_info *out);
+void prism_batch_destroy(prism_batch *batch);
+
 /* ---- introspection (tests, tools) ----------------------------------------------- */
 
 int prism_plan_info(const prism_plan *plan, prism_info *out);

@@ -618,10 +618,19 @@ static ColArgs col_args(const GridTables &T, float2 *wave, const float2 *prop_x,
     return a;
 }
 
+static int build_launches(prism_plan *P, const float *V_dev);
+
 extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
     int rc;
     if ((rc = check_dev_ptr(V_dev, 16, "V_dev"))) return rc;
+    return build_launches(P, V_dev);
+}
+
+// transmission, every slice's row and column passes, ROW_OUT (and the 16-bit quantiser) of every
+// beam batch: kernel launches only (also captured into batch graphs)
+static int build_launches(prism_plan *P, const float *V_dev) {
+    int rc;
     const prism_grid &g = P->g;
     const size_t px = (size_t)g.nx * g.ny;
     // transmission functions t_p = exp(i sigma V_p) for all slices
@@ -680,13 +689,13 @@ extern "C" int prism_build_smatrix_host(prism_plan *P, const float *V_host) {
 
 // ------------------------------------------------------------------ scan
 static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_scan *sc, const prism_detector *det,
-                        ScanArgs &a) {
+                        ScanArgs &a, bool need_built = true) {
     int rc;
     if ((rc = check_probe(probe))) return rc;
     if (det && (rc = check_det(det))) return rc;
     const double pxs = P->g.cell_x / P->nxs, pys = P->g.cell_y / P->nys;
     if ((rc = check_scan(sc, pxs * (double)(1 << 28), pys * (double)(1 << 28)))) return rc;
-    if (!P->built) return fail(PRISM_ERR_INVALID, "S-matrix not built");
+    if (need_built && !P->built) return fail(PRISM_ERR_INVALID, "S-matrix not built");
     const int B = P->nbeams;
     const double lam = P->T.lam;
     const Tilt tl = tilt_terms(probe, lam, P->T.dz);
@@ -761,15 +770,28 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
 
 // FP32 mode: the CUDA-core scan kernels; 16-bit mode: the tensor-core kernel (persistent grid, its
 // window scratch grown on demand)
-static int scan_launch(prism_plan *P, ScanArgs &a) {
-    if (P->prec == PRISM_PRECISION_FP32) return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
-    const int bf = P->prec == PRISM_PRECISION_BF16;
-    const int grid = scan_tc_grid(P->nw, P->kp, bf, a.scan_px, a.scan_py);
-    if (grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
-    int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, grid));
+static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
+    *grid = 0;
+    if (P->prec == PRISM_PRECISION_FP32) return PRISM_OK;
+    *grid = scan_tc_grid(P->nw, P->kp, P->prec == PRISM_PRECISION_BF16, a.scan_px, a.scan_py);
+    if (*grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
+    int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid));
     if (rc) return rc;
     a.win = P->win;
+    return PRISM_OK;
+}
+
+static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
+    if (P->prec == PRISM_PRECISION_FP32) return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    const int bf = P->prec == PRISM_PRECISION_BF16;
     return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, bf, grid, a, P->stream); });
+}
+
+static int scan_launch(prism_plan *P, ScanArgs &a) {
+    int grid = 0;
+    int rc = scan_setup(P, a, &grid);
+    if (rc) return rc;
+    return scan_go(P, a, grid);
 }
 
 extern "C" int prism_scan_run(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
@@ -1150,3 +1172,174 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
 }
 
 }  // namespace prism
+
+// ------------------------------------------------------------------ batches of cells (one CUDA graph)
+struct prism_batch {
+    std::vector<prism_plan *> plans;
+    std::vector<ScanArgs> scans;
+    std::vector<int> scan_grid;
+    std::vector<const float *> V;
+    std::vector<int> branch_of;
+    std::vector<cudaStream_t> branches;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t origin = nullptr;  // capture origin (the caller's stream may be the legacy stream)
+    cudaStream_t stream = nullptr;  // the caller's stream: every run is launched into it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    long launches = 0;
+};
+
+static void batch_release(prism_batch *B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->stream);  // graph runs are ordered on the caller's stream (NULL: legacy)
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    for (prism_plan *P : B->plans) prism_plan_destroy(P);
+    for (cudaEvent_t e : B->joins) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
+    for (cudaStream_t st : B->branches) cudaStreamDestroy(st);
+    if (B->origin) cudaStreamDestroy(B->origin);
+    delete B;
+}
+
+extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches,
+                                  void *cuda_stream, prism_batch **out) {
+    if (!out) return fail(PRISM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cells || n_cells < 1) return fail(PRISM_ERR_INVALID, "need at least one cell");
+    if (n_branches < 0 || n_branches > 16) return fail(PRISM_ERR_INVALID, "n_branches must be in [0, 16]");
+    const int nb = n_branches ? std::min(n_branches, n_cells) : std::min(n_cells, 4);
+    int rc;
+    for (int i = 0; i < n_cells; ++i) {
+        const prism_cell &c = cells[i];
+        if ((rc = check_dev_ptr(c.V_dev, 16, "cell V_dev")) || (rc = check_probe(&c.probe)) || (rc = check_det(&c.det)))
+            return fail(rc, "cell " + std::to_string(i) + ": " + g_err);
+        if ((long long)c.scan.px * c.scan.py > 0 && (rc = check_dev_ptr(c.out_dev, 4, "cell out_dev")))
+            return fail(rc, "cell " + std::to_string(i) + ": " + g_err);
+    }
+    prism_batch *B = new prism_batch();
+    B->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](int code) {
+        const std::string msg = g_err;
+        batch_release(B);
+        g_err = msg;
+        return code;
+    };
+    auto cuda_bail = [&](cudaError_t e, const char *what) {
+        fail(PRISM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        return bail(PRISM_ERR_CUDA);
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking)) != cudaSuccess) return cuda_bail(e, "stream");
+    // plans on the origin stream first (their allocations and uploads), branches assigned after
+    std::vector<double> cost(n_cells);
+    size_t bytes = 0;
+    for (int i = 0; i < n_cells; ++i) {
+        const prism_cell &c = cells[i];
+        prism_plan *P = nullptr;
+        if ((rc = prism_plan_create(&c.grid, 0, B->origin, &P))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
+        B->plans.push_back(P);
+        ScanArgs a;
+        if ((rc = scan_prepare(P, &c.probe, &c.scan, &c.det, a, false))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
+        a.out = c.out_dev;
+        int grid = 0;
+        if (a.n_probes > 0 && (rc = scan_setup(P, a, &grid))) return bail(rc);
+        B->scans.push_back(a);
+        B->scan_grid.push_back(grid);
+        B->V.push_back(c.V_dev);
+        bytes += P->arena.bytes;
+        const double px = (double)c.grid.nx * c.grid.ny;
+        cost[i] = (double)P->nbeams * c.grid.n_slices * px * 32.0 +
+                  (double)a.n_probes * P->nbeams * P->nw * P->nw * (P->prec == PRISM_PRECISION_FP32 ? 8.0 : 1.0);
+    }
+    if (hbm_budget_bytes && bytes > hbm_budget_bytes)
+        return fail(PRISM_ERR_BUDGET, "batch needs " + std::to_string(bytes) + " bytes, budget " + std::to_string(hbm_budget_bytes)), bail(PRISM_ERR_BUDGET);
+    if ((e = cudaStreamSynchronize(B->origin)) != cudaSuccess) return cuda_bail(e, "batch setup");
+    // longest estimated work first onto the least-loaded branch
+    std::vector<int> order(n_cells);
+    for (int i = 0; i < n_cells; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<double> load(nb, 0.0);
+    B->branch_of.assign(n_cells, 0);
+    for (int i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        B->branch_of[i] = k;
+        load[k] += cost[i];
+    }
+    for (int k = 0; k < nb; ++k) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return cuda_bail(e, "stream");
+        B->branches.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_bail(e, "event");
+        B->joins.push_back(ev);
+    }
+    if ((e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming)) != cudaSuccess) return cuda_bail(e, "event");
+    for (int i = 0; i < n_cells; ++i) {
+        B->plans[i]->stream = B->branches[B->branch_of[i]];
+        B->plans[i]->arena.stream = B->plans[i]->stream;
+    }
+    // capture: fork every branch from the origin, each branch runs its cells in order, join
+    long before = 0;
+    for (prism_plan *P : B->plans) before += P->launches;
+    if ((e = cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_bail(e, "begin capture");
+    int crc = PRISM_OK;
+    cudaError_t ce = cudaEventRecord(B->fork, B->origin);
+    for (int k = 0; k < nb && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(B->branches[k], B->fork, 0);
+    for (int i = 0; i < n_cells && ce == cudaSuccess && !crc; ++i) {
+        prism_plan *P = B->plans[i];
+        crc = build_launches(P, B->V[i]);
+        if (!crc && B->scans[i].n_probes > 0) crc = scan_go(P, B->scans[i], B->scan_grid[i]);
+    }
+    for (int k = 0; k < nb && ce == cudaSuccess && !crc; ++k) {
+        ce = cudaEventRecord(B->joins[k], B->branches[k]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(B->origin, B->joins[k], 0);
+    }
+    cudaError_t ee = cudaStreamEndCapture(B->origin, &B->graph);
+    if (crc) return bail(crc);
+    if (ce != cudaSuccess) return cuda_bail(ce, "capture");
+    if (ee != cudaSuccess) return cuda_bail(ee, "end capture");
+    if ((e = cudaGraphInstantiate(&B->exec, B->graph, 0)) != cudaSuccess) return cuda_bail(e, "graph instantiate");
+    if ((e = cudaGraphGetNodes(B->graph, nullptr, &B->nodes)) != cudaSuccess) return cuda_bail(e, "graph nodes");
+    long after = 0;
+    for (prism_plan *P : B->plans) after += P->launches;
+    B->launches = after - before;
+    *out = B;
+    return PRISM_OK;
+}
+
+extern "C" int prism_batch_run(prism_batch *B) {
+    if (!B) return fail(PRISM_ERR_INVALID, "batch is NULL");
+    CUDA_TRY(cudaGraphLaunch(B->exec, B->stream));
+    return PRISM_OK;
+}
+
+extern "C" int prism_batch_sync(prism_batch *B) {
+    if (!B) return fail(PRISM_ERR_INVALID, "batch is NULL");
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    for (size_t i = 0; i < B->plans.size(); ++i) {
+        int err = 0;
+        CUDA_TRY(cudaMemcpy(&err, B->plans[i]->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            CUDA_TRY(cudaMemset(B->plans[i]->dev_err, 0, sizeof(int)));
+            return fail(PRISM_ERR_DEVICE, "cell " + std::to_string(i) + ": a kernel's bounded wait ran out");
+        }
+    }
+    return PRISM_OK;
+}
+
+extern "C" int prism_batch_info_get(const prism_batch *B, prism_batch_info *out) {
+    if (!B || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    out->n_cells = (int)B->plans.size();
+    out->n_branches = (int)B->branches.size();
+    out->graph_nodes = B->nodes;
+    out->kernel_launches = B->launches;
+    size_t bytes = 0;
+    for (prism_plan *P : B->plans) bytes += P->arena.bytes;
+    out->device_bytes = bytes;
+    return PRISM_OK;
+}
+
+extern "C" void prism_batch_destroy(prism_batch *B) { batch_release(B); }

@@ -41,6 +41,7 @@ EXPORTED = [
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
     "prism_selftest_tcgen05",
+    "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
 ]
 
 
@@ -94,6 +95,16 @@ class PrismServerInfo(ctypes.Structure):
 _lib = None
 
 
+class PrismCell(ctypes.Structure):
+    _fields_ = [("grid", PrismGrid), ("V_dev", c_void_p), ("probe", PrismProbe), ("scan", PrismScan),
+                ("det", PrismDetector), ("out_dev", c_void_p)]
+
+
+class PrismBatchInfo(ctypes.Structure):
+    _fields_ = [("n_cells", c_int), ("n_branches", c_int), ("graph_nodes", c_size_t),
+                ("kernel_launches", c_long), ("device_bytes", c_size_t)]
+
+
 def load(path: str = LIB_PATH):
     """Load libprism.so (built by ``paper_1702_01904_gb300.build``); raises if it is missing."""
     global _lib
@@ -124,6 +135,11 @@ def load(path: str = LIB_PATH):
         "prism_plan_beams": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int]),
         "prism_plan_smatrix": (c_int, [P, POINTER(P)]),
         "prism_plan_smatrix_copy": (c_int, [P, P]),
+        "prism_batch_create": (c_int, [POINTER(PrismCell), c_int, c_size_t, c_int, P, POINTER(P)]),
+        "prism_batch_run": (c_int, [P]),
+        "prism_batch_sync": (c_int, [P]),
+        "prism_batch_info_get": (c_int, [P, POINTER(PrismBatchInfo)]),
+        "prism_batch_destroy": (None, [P]),
         "prism_plan_transmission": (c_int, [P, POINTER(P)]),
         "prism_wavelength": (c_double, [c_double]),
         "prism_interaction_constant": (c_double, [c_double]),
@@ -367,3 +383,35 @@ def prism_server_destroy(server):
 
 def prism_selftest_tcgen05(out_dev, status_dev, cuda_stream=None):
     return _check(load().prism_selftest_tcgen05(_ptr(out_dev), _ptr(status_dev), _stream(cuda_stream)))
+
+
+# ------------------------------------------------------------------ batches of cells
+def make_cell(grid, V_dev, probe, scan, det, out_dev):
+    c = PrismCell(grid, _ptr(V_dev), probe, scan, det, _ptr(out_dev))
+    c._keep = (grid, scan)
+    return c
+
+
+def prism_batch_create(cells, hbm_budget_bytes=0, n_branches=0, cuda_stream=None):
+    arr = (PrismCell * len(cells))(*cells)
+    b = c_void_p()
+    _check(load().prism_batch_create(arr, len(cells), hbm_budget_bytes, n_branches, _stream(cuda_stream), byref(b)))
+    return b
+
+
+def prism_batch_run(batch):
+    _check(load().prism_batch_run(batch))
+
+
+def prism_batch_sync(batch):
+    _check(load().prism_batch_sync(batch))
+
+
+def prism_batch_info_get(batch):
+    i = PrismBatchInfo()
+    _check(load().prism_batch_info_get(batch, byref(i)))
+    return i
+
+
+def prism_batch_destroy(batch):
+    load().prism_batch_destroy(batch)

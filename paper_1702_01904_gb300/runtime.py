@@ -155,6 +155,59 @@ def multislice(grid, V: torch.Tensor, probe, x0, y0, det, stream=None, scratch_b
     return out
 
 
+class Batch:
+    """Many independent cells (any size, slices, f, precision) as one captured CUDA graph.
+
+    ``cells`` is a list of dicts with keys grid (PrismGrid), V (CUDA float32 tensor
+    [n_slices][ny][nx]), probe, x0, y0, det and optionally px, py.  The potentials are read and the
+    outputs (``self.outs[i]``, [px*py][nbins]) written at every ``run``; V's contents may change
+    between runs."""
+
+    def __init__(self, cells, hbm_budget_bytes: int = 0, n_branches: int = 0, stream=None):
+        _require_cuda()
+        P.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._keep = []
+        self.outs = []
+        cs = []
+        for c in cells:
+            V = c["V"]
+            assert V.is_cuda and V.dtype == torch.float32 and V.is_contiguous()
+            g = c["grid"]
+            assert tuple(V.shape) == (g.n_slices, g.ny, g.nx)
+            x0 = np.ascontiguousarray(c["x0"], np.float64)
+            y0 = np.ascontiguousarray(c["y0"], np.float64)
+            px = c.get("px") or len(x0)
+            py = c.get("py") or 1
+            assert px * py == len(x0)
+            det = c["det"]
+            out = torch.empty((px * py, det.nbins), dtype=torch.float32, device="cuda")
+            sc = P.make_scan(px, py, x0, y0)
+            cs.append(P.make_cell(g, V, c["probe"], sc, det, out))
+            self._keep.append((V, sc, g))
+            self.outs.append(out)
+        torch.cuda.current_stream().synchronize()
+        self.batch = P.prism_batch_create(cs, hbm_budget_bytes, n_branches, self.stream)
+        self.info = P.prism_batch_info_get(self.batch)
+
+    def run(self):
+        P.prism_batch_run(self.batch)
+
+    def sync(self):
+        P.prism_batch_sync(self.batch)
+
+    def close(self):
+        if getattr(self, "batch", None) is not None:
+            P.prism_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching request engine (libprism's prism_server_*): submit simulation requests
     from any thread; results arrive in host arrays.  S-matrices with a non-zero key stay resident

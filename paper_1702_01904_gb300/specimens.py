@@ -246,6 +246,30 @@ def workload_nanoparticle(f=4, **over) -> Workload:
     return w
 
 
+def workload_batch_cell(seed: int) -> Workload:
+    """One cell of the batched workload of uneven cells.  PCG64(seed) draws the grid N from
+    {256, 512, 1024} (0.0625 A pixels, so the cell is N/16 A square), the slice count H from
+    [10, 60] (2 A slices), f from {4, 8}; atoms by random sequential addition at 0.1 atoms/A^3 with
+    1.4 A minimum spacing, each atom's Z drawn from {6, 14, 29, 79}.  Scan: 16 x 16 probes at
+    0.25 A.  300 kV, 20 mrad."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = (256, 512, 1024)[int(rng.integers(0, 3))]
+    h = int(rng.integers(10, 61))
+    f = (4, 8)[int(rng.integers(0, 2))]
+    cell = n * 0.0625
+    n_atoms = int(round(0.1 * cell * cell * 2.0 * h))
+    spec = random_packing((cell, cell, 2.0 * h), n_atoms, 1.4, seed=seed, z_choices=(6, 14, 29, 79))
+    return Workload(name=f"batch-cell-{seed}-{n}px-{h}sl-f{f}", nx=n, ny=n, cell_x=cell, cell_y=cell,
+                    n_slices=h, dz=2.0, kv=300.0, f=f, alpha_mrad=20.0,
+                    scan_px=16, scan_py=16, scan_step=0.25, specimen=spec)
+
+
+def batch_cell_potential(seed: int):
+    """(workload, potential) of one batched cell; a top-level function so that process pools can map it."""
+    w = workload_batch_cell(seed)
+    return w, w.potential()
+
+
 def potential_stats(v: np.ndarray) -> dict:
     return {"min": float(v.min()), "max": float(v.max()), "mean": float(v.mean())}
 

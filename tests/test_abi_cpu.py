@@ -65,6 +65,10 @@ int main(void) {
   F(prism_grid, cell_x) F(prism_grid, slice_dz) F(prism_grid, kv) F(prism_grid, f) F(prism_grid, aa_frac)
   F(prism_grid, alpha_max_mrad) F(prism_grid, precision) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
   F(prism_info, wavelength) F(prism_info, device_bytes)
+  printf("prism_cell %zu\\n", sizeof(prism_cell));
+  printf("prism_batch_info %zu\\n", sizeof(prism_batch_info));
+  F(prism_cell, V_dev) F(prism_cell, probe) F(prism_cell, scan) F(prism_cell, det) F(prism_cell, out_dev)
+  F(prism_batch_info, graph_nodes) F(prism_batch_info, kernel_launches) F(prism_batch_info, device_bytes)
   return 0;
 }
 """)
@@ -73,7 +77,8 @@ int main(void) {
     out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                                 check=True).stdout.split("\n") if line)
     cls = {"prism_grid": P.PrismGrid, "prism_probe": P.PrismProbe, "prism_scan": P.PrismScan,
-           "prism_detector": P.PrismDetector, "prism_info": P.PrismInfo}
+           "prism_detector": P.PrismDetector, "prism_info": P.PrismInfo, "prism_cell": P.PrismCell,
+           "prism_batch_info": P.PrismBatchInfo}
     for k, v in out.items():
         if "." in k:
             s, m = k.split(".")
