@@ -237,7 +237,7 @@ def serving_run(w, V_host, n_requests=40, rate=20.0, seed=5):
                    "a-C cell at 0.2-0.5 A steps (up to 62500 probes) from one resident S-matrix"}
 
 
-def batch_leg(n_cells=64, runs=2, n_branches=4):
+def batch_leg(n_cells=64, runs=2, n_branches=4, autotune=True):
     """The batched workload: n_cells seeded uneven cells (seeds 100...), FP32, one captured CUDA
     graph per run (prism_batch_*).  Potentials are generated by a spawn process pool."""
     import multiprocessing as mp
@@ -271,7 +271,9 @@ def batch_leg(n_cells=64, runs=2, n_branches=4):
         mix[key] = mix.get(key, 0) + 1
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        b = Batch(cells, n_branches=n_branches, stream=stream)
+        t1 = time.perf_counter()
+        b = Batch(cells, n_branches=n_branches, stream=stream, autotune=autotune)
+        create_s = time.perf_counter() - t1
         b.run()
         b.sync()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -291,6 +293,7 @@ def batch_leg(n_cells=64, runs=2, n_branches=4):
             "build_pass_gbs_over_whole_run": build_bytes / (ms / 1000.0) / 1e9,
             "kernel_launches_per_run": info.kernel_launches, "branches": info.n_branches,
             "device_gb": info.device_bytes / 1e9, "potential_generation_s": gen_s,
+            "create_s": create_s, "autotuned": autotune,
             "what": "every cell's transmission + S-matrix build + 16x16-probe scan, FP32, one cudaGraphLaunch per run"}
 
 
@@ -336,6 +339,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
                     help="S-matrix storage / beam-sum arithmetic of the headline line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-cells leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes of the passes")
     ap.add_argument("--batch-cells", type=int, default=64)
     ap.add_argument("--no-precision-leg", action="store_true",
                     help="skip timing the other precisions beside the headline one")
@@ -411,6 +415,7 @@ def main():
     with torch.cuda.stream(stream):
         sim = PrismSimulation(grid, 0, stream)
         Bn = sim.info.n_beams
+        tune = None if args.no_autotune else sim.autotune()
         out = torch.empty((P, DET["nbins"]), dtype=torch.float32, device="cuda")
 
         def step():
@@ -600,7 +605,7 @@ def main():
 
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = batch_leg(args.batch_cells)
+        batch = batch_leg(args.batch_cells, autotune=not args.no_autotune)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -636,6 +641,7 @@ def main():
                            "what": "one whole step (S-matrix build + 40000-probe scan), device time"},
             "serving": serving,
             "batch": batch,
+            "autotune": tune,
             "clocks": clk,
         }
         print(json.dumps(res), flush=True)

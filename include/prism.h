@@ -274,6 +274,30 @@ int prism_server_stats(prism_server *server, prism_server_info *out);
 /* Finish the queued and running requests, release every S-matrix and stop the worker. */
 void prism_server_destroy(prism_server *server);
 
+/* ---- autotuner ------------------------------------------------------------------------
+ *
+ * The build is two streaming passes per slice (Calculation Time section: its cost grows with
+ * beams x slices x N^2); their fastest launch shape (threads or interleaved columns per CTA,
+ * cp.async staging or not) depends on N and the beam batch.  prism_plan_autotune times every
+ * compiled shape of the row pass (PRISM_TUNE_ROW) and the column pass (PRISM_TUNE_COL) on the
+ * plan's own wave scratch (5 launches each after 2 warm-ups, CUDA events on the plan's stream)
+ * and keeps the fastest for the plan's later builds.  Shapes exist for N = 256 ... 2048; smaller
+ * grids keep their single shape.  Every shape computes bitwise the same result.  Results are
+ * cached for the process per (pass, N, batch).  Synchronous; overwrites the wave scratch only (the
+ * S-matrix is untouched).  The paper has no counterpart. */
+#define PRISM_TUNE_ROW 0
+#define PRISM_TUNE_COL 1
+#define PRISM_TUNE_MAX_SHAPES 8
+typedef struct prism_tune_entry {
+    int n_shapes;                     /* shapes listed for the pass                              */
+    int chosen;                       /* index of the shape in use (-1: the single default shape)  */
+    int default_shape;                /* index of the untuned default (-1 if N has no shapes)      */
+    double ms[PRISM_TUNE_MAX_SHAPES]; /* mean time per launch of each shape, -1 if not compiled   */
+} prism_tune_entry;
+int prism_plan_autotune(prism_plan *plan);
+int prism_plan_tune_result(const prism_plan *plan, int kind, prism_tune_entry *out);
+const char *prism_tune_shape_name(int kind, int shape);
+
 /* ---- batches of uneven cells: one captured CUDA graph ------------------------------
  *
  * Many independent simulations of different sizes, slice counts, f and precision (the paper's
@@ -305,10 +329,11 @@ typedef struct prism_batch_info {
 typedef struct prism_batch prism_batch;
 
 /* Validate every cell, create its plan (INVALID/UNSUPPORTED as prism_plan_create, with the cell
- * index in the message), upload its scan inputs and capture the graph.  n_branches in [1, 16]
- * (0 = min(n_cells, 4)).  hbm_budget_bytes bounds the sum of the plans' device memory (0 = no
+ * index in the message), upload its scan inputs, optionally autotune it (flags), and capture the
+ * graph.  n_branches in [1, 16] (0 = min(n_cells, 4)).  hbm_budget_bytes bounds the sum of the plans' device memory (0 = no
  * limit; BUDGET if exceeded).  The graph is launched into cuda_stream (NULL = legacy default). */
-int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches,
+#define PRISM_BATCH_AUTOTUNE 1  /* flags: autotune every cell's plan before the capture */
+int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches, int flags,
                        void *cuda_stream, prism_batch **out);
 /* Enqueue one run of the whole batch (asynchronous on the batch's stream). */
 int prism_batch_run(prism_batch *batch);

@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -352,6 +354,9 @@ struct prism_plan {
     float2 *win = nullptr;     // 16-bit mode: scan window scratch
     size_t win_cap = 0;
     int *dev_err = nullptr;    // device error word
+    int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
+    double tune_ms[2][PRISM_TUNE_MAX_SHAPES];
+    bool tuned[2] = {false, false};
     float2 *prop_x = nullptr, *prop_y = nullptr;
     int *aa_kmax = nullptr;
     float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr;
@@ -644,14 +649,19 @@ static int build_launches(prism_plan *P, const float *V_dev) {
             ra.trans = P->t + (size_t)p * px;
             ra.n_rows = nb * g.ny;
             ra.beam0 = b0;
-            rc = plan_launch(P, p == 0 ? PRISM_K_ROW_PLANE : PRISM_K_ROW,
-                             [&] { return launch_row(g.nx, p == 0 ? ROW_PLANE : ROW_STD, ra, P->stream); });
+            rc = plan_launch(P, p == 0 ? PRISM_K_ROW_PLANE : PRISM_K_ROW, [&] {
+                return p > 0 && P->tune_shape[0] >= 0 ? launch_row_shape(g.nx, P->tune_shape[0], ra, P->stream)
+                                                      : launch_row(g.nx, p == 0 ? ROW_PLANE : ROW_STD, ra, P->stream);
+            });
             if (rc) return rc;
             const int pi = P->T.slice_prop[p];
             ColArgs ca = col_args(P->T, P->wave, P->prop_x + (size_t)pi * g.nx, P->prop_y + (size_t)pi * g.ny,
                                   P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
             ca.batch = nb;
-            rc = plan_launch(P, PRISM_K_COL, [&] { return launch_col(g.ny, COL_STD, ca, P->stream); });
+            rc = plan_launch(P, PRISM_K_COL, [&] {
+                return P->tune_shape[1] >= 0 ? launch_col_shape(g.ny, P->tune_shape[1], ca, P->stream)
+                                             : launch_col(g.ny, COL_STD, ca, P->stream);
+            });
             if (rc) return rc;
         }
         RowArgs ro = row_args(P);
@@ -1173,6 +1183,97 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
 
 }  // namespace prism
 
+// ------------------------------------------------------------------ autotuner
+struct TuneKey {
+    int kind, n, batch;
+    bool operator<(const TuneKey &o) const {
+        return kind != o.kind ? kind < o.kind : n != o.n ? n < o.n : batch < o.batch;
+    }
+};
+struct TuneVal {
+    int chosen;
+    double ms[PRISM_TUNE_MAX_SHAPES];
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune_cache;
+
+extern "C" int prism_plan_autotune(prism_plan *P) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    const prism_grid &g = P->g;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int rc = PRISM_OK;
+    for (int kind = 0; kind < 2 && !rc; ++kind) {
+        const int n = kind == 0 ? g.nx : g.ny;
+        const TuneKey key{kind, n, P->batch};
+        for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->tune_ms[kind][v] = -1.0;
+        P->tuned[kind] = true;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                P->tune_shape[kind] = it->second.chosen;
+                for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->tune_ms[kind][v] = it->second.ms[v];
+                continue;
+            }
+        }
+        int best = -1;
+        double best_ms = 0;
+        for (int v = 0; v < tune_shapes(kind) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
+            if (!tune_shape_valid(kind, n, v)) continue;
+            RowArgs ra = row_args(P);
+            ra.trans = P->t;
+            ra.n_rows = P->batch * g.ny;
+            ColArgs ca = col_args(P->T, P->wave, P->prop_x, P->prop_y, P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
+            ca.batch = P->batch;
+            auto once = [&]() {
+                return kind == 0 ? launch_row_shape(g.nx, v, ra, P->stream) : launch_col_shape(g.ny, v, ca, P->stream);
+            };
+            cudaError_t e = cudaSuccess;
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, P->stream);
+            for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = once();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = fail(PRISM_ERR_CUDA, std::string("autotune ") + tune_shape_name(kind, v) + ": " + cudaGetErrorString(e));
+                break;
+            }
+            P->tune_ms[kind][v] = ms / 5.0;
+            if (best < 0 || ms / 5.0 < best_ms) {
+                best = v;
+                best_ms = ms / 5.0;
+            }
+        }
+        if (rc) break;
+        P->tune_shape[kind] = best;
+        TuneVal tv;
+        tv.chosen = best;
+        for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) tv.ms[v] = P->tune_ms[kind][v];
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = tv;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_entry *out) {
+    if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "bad tune kind");
+    const int n = kind == 0 ? P->g.nx : P->g.ny;
+    out->n_shapes = std::min(tune_shapes(kind), PRISM_TUNE_MAX_SHAPES);
+    out->chosen = P->tune_shape[kind];
+    out->default_shape = tune_shape_valid(kind, n, tune_default_shape(kind, n)) ? tune_default_shape(kind, n) : -1;
+    for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) out->ms[v] = P->tuned[kind] ? P->tune_ms[kind][v] : -1.0;
+    return PRISM_OK;
+}
+
+extern "C" const char *prism_tune_shape_name(int kind, int shape) { return tune_shape_name(kind, shape); }
+
 // ------------------------------------------------------------------ batches of cells (one CUDA graph)
 struct prism_batch {
     std::vector<prism_plan *> plans;
@@ -1204,7 +1305,7 @@ static void batch_release(prism_batch *B) {
     delete B;
 }
 
-extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches,
+extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches, int flags,
                                   void *cuda_stream, prism_batch **out) {
     if (!out) return fail(PRISM_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -1241,6 +1342,7 @@ extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t h
         prism_plan *P = nullptr;
         if ((rc = prism_plan_create(&c.grid, 0, B->origin, &P))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
         B->plans.push_back(P);
+        if ((flags & PRISM_BATCH_AUTOTUNE) && (rc = prism_plan_autotune(P))) return bail(rc);
         ScanArgs a;
         if ((rc = scan_prepare(P, &c.probe, &c.scan, &c.det, a, false))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
         a.out = c.out_dev;

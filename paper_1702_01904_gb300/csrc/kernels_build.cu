@@ -1,17 +1,11 @@
-// kernels_build.cu -- multislice kernels for sm_103a: slice transmission, the row pass
-// (row IFFT, x t_p, row FFT) and the column pass (column FFT, x propagator, column IFFT),
-// used both by the compact S-matrix build and by the per-probe multislice baseline.
-//
-// One multislice step (Eq. Multislice, transmit then propagate) is split into two streaming
-// passes over a wave stack [batch][ny][nx] kept in the mixed domain (x-Fourier, y-real):
-//   row pass p   : psi_p = IFFT_x(Phi_{p-1});  Z_p = FFT_x(psi_p * t_p)
-//   column pass p: Phi_p = IFFT_y( P_p(q) * FFT_y(Z_p) ) / (nx ny)
-// so that IFFT_x(Phi_p) is the real-space wave after slice p.  Each pass reads and writes the
-// stack once; the 1/(nx ny) of the inverse transform is folded into the propagator table.
+// kernels_build.cu -- multislice kernels for sm_103a: slice transmission, the row and column
+// passes at their default launch shapes (templates in pass_kernels.cuh), probe shift phases and
+// detector bins; used both by the compact S-matrix build and by the per-probe multislice baseline.
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
 #include "params.h"
+#include "pass_kernels.cuh"
 
 namespace prism {
 
@@ -46,220 +40,7 @@ cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigm
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ launch geometry
-// Persistent launches: as many CTAs as can be resident at once (occupancy x SM count), each
-// looping over its share of rows or column tiles.
-template <class K>
-static cudaError_t set_smem(K kernel, size_t smem) {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaSuccess;
-}
-
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
-    }
-    return n;
-}
-
-template <class K>
-static cudaError_t persistent_grid(K kernel, int threads, size_t smem, long long work, int *grid, bool persist = true) {
-    cudaError_t e = set_smem(kernel, smem);
-    if (e != cudaSuccess) return e;
-    if (!persist) {
-        *grid = (int)work;
-        return cudaSuccess;
-    }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    if (e != cudaSuccess) return e;
-    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sm_count();
-    *grid = (int)(work < cap ? work : cap);
-    return cudaSuccess;
-}
-
-// ------------------------------------------------------------------ async copies
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// ------------------------------------------------------------------ row pass
-// Each slot (T lanes of one warp) owns one row at a time and walks rows row0, row0 + stride, ...
-// The next row streams into the slot's shared-memory staging buffer (cp.async) while the current
-// row is transformed; the slice's transmission row is loaded into registers before the inverse
-// FFT so that its latency hides behind the transform.
-template <int NX>
-struct RowCfg {
-    using FS = FftShape<NX>;
-    static constexpr int T = FS::T;
-    static constexpr int E = FS::E;
-    static constexpr bool STAGE = false;      // cp.async staging of the next row
-    static constexpr bool PERSIST = true;     // grid = resident CTAs, each looping over rows
-    static constexpr bool T_EARLY = E <= 32;  // E extra complex registers for t_p
-    static constexpr int THREADS = NX >= 512 ? 128 : 256;
-    static constexpr int SLOTS = THREADS / T;  // rows per CTA in flight
-    static constexpr int EXF = FS::N1 * (FS::N2 + 1);
-    static constexpr int EXI = FS::N2 * (FS::N1 + 1);
-    static constexpr int EX = EXF > EXI ? EXF : EXI;
-    static constexpr int SLOT_F2 = (STAGE ? NX : 0) + EX;  // staging row + exchange, float2
-    static constexpr size_t SMEM = (size_t)(2 * NX + SLOTS * SLOT_F2) * sizeof(float2);
-};
-
-template <int NX, int MODE>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS) k_row(const __grid_constant__ RowArgs a) {
-    using C = RowCfg<NX>;
-    using FS = FftShape<NX>;
-    using Fwd = FwdFft<NX>;
-    using Inv = InvFft<NX>;
-    constexpr int T = C::T, E = FS::E;
-    extern __shared__ float2 smem[];
-    // FFT stage twiddles (forward, inverse) in shared memory, then one region per slot
-    float2 *twf = smem, *twi = smem + NX;
-    for (int i = threadIdx.x; i < NX; i += C::THREADS) {
-        twf[i] = a.tw_fwd[i];
-        twi[i] = a.tw_inv[i];
-    }
-    __syncthreads();
-    const int slot = threadIdx.x / T, t = threadIdx.x % T;
-    float2 *stg = smem + 2 * NX + slot * C::SLOT_F2;
-    float2 *exbuf = stg + (C::STAGE ? NX : 0);
-    WarpExchange<FS::N1, FS::N2, T> exF{exbuf};
-    WarpExchange<FS::N2, FS::N1, T> exI{exbuf};
-    const int stride = gridDim.x * C::SLOTS;
-    const int iters = (a.n_rows + stride - 1) / stride;  // uniform over the grid
-    const int row0 = blockIdx.x * C::SLOTS + slot;
-
-    // rows past the end are redone on the last row without storing, so every lane of a warp
-    // takes part in every exchange
-    auto locate = [&](int row, int &b, int &y) {
-        row = row < a.n_rows ? row : a.n_rows - 1;
-        if (MODE == ROW_OUT && a.downsample == 2) {
-            const int nyh = a.ny >> 1;
-            b = row / nyh;
-            y = 2 * (row - b * nyh);
-        } else {
-            b = row / a.ny;
-            y = row - b * a.ny;
-        }
-    };
-    // stage a whole row into this slot's buffer: NX*8 bytes in 16-byte pieces, E/2 per lane
-    auto stage = [&](int row) {
-        int b, y;
-        locate(row, b, y);
-        const float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
-#pragma unroll
-        for (int k = 0; k < E / 2; ++k) {
-            const int e = 2 * (t + T * k);
-            cp_async16(stg + e, w + e);
-        }
-        cp_async_commit();
-    };
-
-    if constexpr (MODE != ROW_PLANE && C::STAGE) stage(row0);
-    for (int it = 0; it < iters; ++it) {
-        const int row = row0 + it * stride;
-        const bool valid = row < a.n_rows;
-        int b, y;
-        locate(row, b, y);
-        float2 v[E];
-        if constexpr (MODE == ROW_PLANE) {
-            // psi_b(r) = exp(2 pi i (m f x / nx + n f y / ny)), phase reduced exactly in integers
-            const int m = a.beam_mn[2 * (a.beam0 + b)];
-            const int n = a.beam_mn[2 * (a.beam0 + b) + 1];
-            const long long den = (long long)NX * a.ny;
-            long long ky = ((long long)n * a.f * y) % a.ny;
-            if (ky < 0) ky += a.ny;
-            const long long yterm = ky * NX;
-            const float inv_den = 1.0f / (float)den;  // den is a power of two: exact
-            const float2 *tp = a.trans + (size_t)y * NX;
-#pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int x = Fwd::in_elem(r, t);
-                long long kx = ((long long)m * a.f * x) % NX;
-                if (kx < 0) kx += NX;
-                long long num = kx * a.ny + yterm;
-                if (num >= den) num -= den;
-                float s, c;
-                sincospif(2.0f * ((float)num * inv_den), &s, &c);
-                v[r] = cmul(make_float2(c, s), __ldcg(tp + x));
-            }
-        } else {
-            if constexpr (C::STAGE) {
-                cp_async_wait_all();
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = stg[Inv::in_elem(r, t)];
-                __syncwarp();  // the buffer is refilled next
-                if (it + 1 < iters) stage(row + stride);
-            } else {
-                const float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = __ldcs(w + Inv::in_elem(r, t));
-            }
-            if constexpr (MODE == ROW_STD) {
-                // t_p is shared by all beams: L2-cached, not L1 (keeps L1 for the FFT's traffic)
-                const float2 *tp = a.trans + (size_t)y * NX;
-                if constexpr (C::T_EARLY) {
-                    float2 tv[E];
-#pragma unroll
-                    for (int r = 0; r < E; ++r) tv[r] = __ldcg(tp + Inv::out_elem(r, t));
-                    Inv::run(v, t, twi, a.tw, exI);
-#pragma unroll
-                    for (int r = 0; r < E; ++r) v[r] = cmul(v[r], tv[r]);
-                } else {
-                    Inv::run(v, t, twi, a.tw, exI);
-#pragma unroll
-                    for (int r = 0; r < E; ++r) v[r] = cmul(v[r], __ldcg(tp + Inv::out_elem(r, t)));
-                }
-            } else {
-                Inv::run(v, t, twi, a.tw, exI);
-            }
-        }
-        if constexpr (MODE == ROW_OUT) {
-            // real-space exit wave; with downsample 2 the band limit (|k| < n/4) makes every second
-            // sample the exact half-resolution wave of the inner Fourier square
-            if (valid) {
-                if (a.downsample == 2) {
-                    const int nxs = NX / 2, nys = a.ny / 2;
-                    float2 *srow = a.s_out + ((size_t)(a.beam0 + b) * nys + (y >> 1)) * nxs;
-#pragma unroll
-                    for (int r = 0; r < E; ++r) {
-                        const int x = Inv::out_elem(r, t);
-                        if (!(x & 1)) srow[x >> 1] = v[r];
-                    }
-                } else {
-                    float2 *srow = a.s_out + ((size_t)(a.beam0 + b) * a.ny + y) * NX;
-#pragma unroll
-                    for (int r = 0; r < E; ++r) srow[Inv::out_elem(r, t)] = v[r];
-                }
-            }
-        } else {
-            Fwd::run(v, t, twf, a.tw, exF);
-            if (valid) {
-                float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
-#pragma unroll
-                for (int r = 0; r < E; ++r) __stcs(w + Fwd::out_elem(r, t), v[r]);
-            }
-        }
-    }
-}
-
-template <int NX, int MODE>
-static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
-    using C = RowCfg<NX>;
-    int grid = 0;
-    cudaError_t e = persistent_grid(k_row<NX, MODE>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS, &grid, C::PERSIST);
-    if (e != cudaSuccess) return e;
-    k_row<NX, MODE><<<grid, C::THREADS, C::SMEM, s>>>(a);
-    return cudaGetLastError();
-}
-
+// ------------------------------------------------------------------ default launch shapes
 template <int NX>
 static cudaError_t row_dispatch(RowMode mode, const RowArgs &a, cudaStream_t s) {
     if (a.n_rows <= 0) return cudaSuccess;
@@ -285,155 +66,9 @@ cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s) {
     }
 }
 
-// ------------------------------------------------------------------ column pass
-// A CTA owns W interleaved columns (one tile, NY x W) at a time and walks tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...; the next tile streams into a shared-memory staging buffer
-// (cp.async, 16-byte pieces of the W*8-byte row segments) while the current one is transformed.
-template <int NY>
-struct ColCfg {
-    using FS = FftShape<NY>;
-    static constexpr int W = NY >= 2048 ? 4 : NY >= 1024 ? 8 : 16;  // interleaved columns per CTA
-    static constexpr int THREADS = FS::T * W;
-    static constexpr bool STAGE = true;    // cp.async staging of the next tile
-    static constexpr bool SMEM_TW = false; // stage twiddles in shared memory (else L1 broadcast loads)
-    static constexpr bool PERSIST = true;  // grid = resident CTAs, each looping over tiles
-    static constexpr int MINB = (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
-    static constexpr int EX = ColExSize<NY, W>::value;
-    static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
-};
-
-template <int NY, int MODE>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, ColCfg<NY>::MINB) k_col(const __grid_constant__ ColArgs a) {
-    using C = ColCfg<NY>;
-    using FS = FftShape<NY>;
-    using Fwd = FwdFft<NY>;
-    using Inv = InvFft<NY>;
-    constexpr int W = C::W, E = FS::E, THREADS = C::THREADS;
-    extern __shared__ float2 smem[];
-    // FFT stage twiddles (forward, inverse), staging tile [NY][W], exchange
-    const float2 *twf = a.tw_fwd, *twi = a.tw_inv;
-    if constexpr (C::SMEM_TW) {
-        float2 *tws = smem;
-        for (int i = threadIdx.x; i < NY; i += THREADS) {
-            tws[i] = a.tw_fwd[i];
-            tws[NY + i] = a.tw_inv[i];
-        }
-        __syncthreads();
-        twf = tws;
-        twi = tws + NY;
-    }
-    float2 *stg = smem + (C::SMEM_TW ? 2 * NY : 0);
-    float2 *exb = stg + (C::STAGE ? NY * W : 0);
-    const int c = threadIdx.x % W, t = threadIdx.x / W;
-    ColExchange<FS::N1, FS::N2, W> exF{exb, c};
-    ColExchange<FS::N2, FS::N1, W> exI{exb, c};
-    const int tiles_x = a.nx / W;
-    const int ntiles = tiles_x * a.batch;
-    const int iters = (ntiles + gridDim.x - 1) / gridDim.x;  // uniform over the grid
-
-    // tiles past the end are redone on the last tile without storing (every thread joins every
-    // __syncthreads of the exchange)
-    auto locate = [&](int tile, int &b, int &kx0) {
-        tile = tile < ntiles ? tile : ntiles - 1;
-        b = tile / tiles_x;
-        kx0 = (tile - b * tiles_x) * W;
-    };
-    auto stage = [&](int tile) {
-        int b, kx0;
-        locate(tile, b, kx0);
-        const float2 *base = a.wave + (size_t)b * NY * a.nx + kx0;
-        constexpr int PIECES = NY * W / 2;  // 16-byte pieces of the tile
-#pragma unroll
-        for (int k = 0; k < PIECES / THREADS; ++k) {
-            const int i = threadIdx.x + THREADS * k;
-            const int row = i / (W / 2), cc = 2 * (i % (W / 2));
-            cp_async16(stg + row * W + cc, base + (size_t)row * a.nx + cc);
-        }
-        cp_async_commit();
-    };
-
-    if constexpr (MODE != COL_PROBE && C::STAGE) stage(blockIdx.x);
-    // without persistence every CTA owns exactly one tile and there is no loop (a loop would let
-    // the compiler hoist the loop-invariant twiddle loads and hold them in registers)
-    const int n_it = C::PERSIST || C::STAGE ? iters : 1;
-    for (int it = 0; it < n_it; ++it) {
-        const int tile = blockIdx.x + it * gridDim.x;
-        const bool valid = tile < ntiles;
-        int b, kx0;
-        locate(tile, b, kx0);
-        const int kx = kx0 + c;
-
-        float2 *col = a.wave + (size_t)b * NY * a.nx + kx;
-        float2 v[E];
-        if constexpr (MODE == COL_PROBE) {
-            // Psi0(q) = A(q) e^{-i chi(q)} e^{-2 pi i q.r0}, generated in the inverse transform's input layout
-            const float2 sx = a.shift_x[(size_t)b * a.nx + kx];
-            const float2 *sy = a.shift_y + (size_t)b * NY;
-#pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int ky = Inv::in_elem(r, t);
-                v[r] = cmul(cmul(__ldg(a.probe_base + (size_t)ky * a.nx + kx), sx), __ldg(sy + ky));
-            }
-        } else {
-            if constexpr (C::STAGE) {
-                cp_async_wait_all();
-                __syncthreads();
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = stg[Fwd::in_elem(r, t) * W + c];
-                __syncthreads();  // the staging buffer is refilled next
-                if (it + 1 < iters) stage(tile + gridDim.x);
-            } else {
-#pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = col[(size_t)Fwd::in_elem(r, t) * a.nx];
-            }
-            Fwd::template run<decltype(exF), !C::SMEM_TW>(v, t, twf, a.tw, exF);
-            // Fresnel propagator exp(-i pi lambda t |q|^2) (separable) inside the anti-aliasing
-            // aperture, which on column kx is |ky| <= aa_kmax[kx]
-            const float2 px = __ldg(a.prop_x + kx);
-            const int kymax = __ldg(a.aa_kmax + kx);
-#pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int ky = Fwd::out_elem(r, t);
-                const int kys = ky < (NY >> 1) ? ky : ky - NY;
-                const int aky = kys < 0 ? -kys : kys;
-                v[r] = aky <= kymax ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
-            }
-            if constexpr (MODE == COL_DETECT) {
-                if (valid) {
-                    float *icol = a.inten + (size_t)b * NY * a.nx + kx;
-#pragma unroll
-                    for (int r = 0; r < E; ++r) icol[(size_t)Fwd::out_elem(r, t) * a.nx] = v[r].x * v[r].x + v[r].y * v[r].y;
-                }
-                continue;
-            }
-        }
-        Inv::template run<decltype(exI), !C::SMEM_TW>(v, t, twi, a.tw, exI);
-        if constexpr (MODE == COL_PROBE) {
-#pragma unroll
-            for (int r = 0; r < E; ++r) v[r] = cscale(v[r], a.probe_scale);
-        }
-        if (valid) {
-#pragma unroll
-            for (int r = 0; r < E; ++r) col[(size_t)Inv::out_elem(r, t) * a.nx] = v[r];
-        }
-    }
-}
-
-template <int NY, int MODE>
-static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
-    using C = ColCfg<NY>;
-    int grid = 0;
-    cudaError_t e = persistent_grid(k_col<NY, MODE>, C::THREADS, C::SMEM, (long long)(a.nx / C::W) * a.batch, &grid, C::PERSIST);
-    if (e != cudaSuccess) return e;
-    k_col<NY, MODE><<<grid, C::THREADS, C::SMEM, s>>>(a);
-    return cudaGetLastError();
-}
-
 template <int NY>
 static cudaError_t col_dispatch(ColMode mode, const ColArgs &a, cudaStream_t s) {
-    using C = ColCfg<NY>;
     if (a.batch <= 0) return cudaSuccess;
-    if (a.nx % C::W) return cudaErrorInvalidValue;
     switch (mode) {
         case COL_STD: return col_go<NY, COL_STD>(a, s);
         case COL_PROBE: return col_go<NY, COL_PROBE>(a, s);

@@ -1,0 +1,145 @@
+// kernels_tune.cu -- the alternative launch shapes of the two multislice passes that the autotuner
+// times (ROW_STD and COL_STD, N = 256 ... 2048).  A shape changes only how rows or columns are
+// spread over threads and whether the next row/tile is staged through shared memory with
+// cp.async; every shape computes bitwise the same transform.
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "params.h"
+#include "pass_kernels.cuh"
+
+namespace prism {
+
+namespace {
+
+struct Shape {
+    int a;     // row pass: threads per CTA; column pass: interleaved columns per CTA
+    bool stg;  // cp.async staging of the next row / tile
+};
+constexpr Shape ROW_SHAPES[] = {{128, false}, {256, false}, {128, true}, {256, true}};
+constexpr Shape COL_SHAPES[] = {{4, true}, {8, true}, {16, true}, {4, false}, {8, false}, {16, false}};
+constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
+constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
+const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged"};
+const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W16"};
+
+template <int N, int I>
+constexpr bool row_ok() {
+    using C = RowCfg<N, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>;
+    return C::SMEM <= 227 * 1024 && ROW_SHAPES[I].a % C::T == 0 && ROW_SHAPES[I].a <= 1024;
+}
+template <int N, int I>
+constexpr bool col_ok() {
+    using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg>;
+    return C::SMEM <= 227 * 1024 && C::THREADS <= 1024;
+}
+
+template <int N, int I>
+cudaError_t row_shape(const RowArgs &a, cudaStream_t s) {
+    if (a.n_rows <= 0) return cudaSuccess;
+    return row_go<N, ROW_STD, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>(a, s);
+}
+template <int N, int I>
+cudaError_t col_shape(const ColArgs &a, cudaStream_t s) {
+    if (a.batch <= 0) return cudaSuccess;
+    return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg>(a, s);
+}
+
+template <int N>
+cudaError_t row_n(int v, const RowArgs &a, cudaStream_t s) {
+    switch (v) {
+        case 0: return row_shape<N, 0>(a, s);
+        case 1: return row_shape<N, 1>(a, s);
+        case 2: return row_shape<N, 2>(a, s);
+        case 3: return row_shape<N, 3>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+template <int N>
+cudaError_t col_n(int v, const ColArgs &a, cudaStream_t s) {
+    switch (v) {
+        case 0: return col_shape<N, 0>(a, s);
+        case 1: return col_shape<N, 1>(a, s);
+        case 2: return col_shape<N, 2>(a, s);
+        case 3: return col_shape<N, 3>(a, s);
+        case 4: return col_shape<N, 4>(a, s);
+        case 5: return col_shape<N, 5>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+template <int N>
+bool row_valid_n(int v) {
+    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>()};
+    return v >= 0 && v < N_ROW && ok[v];
+}
+template <int N>
+bool col_valid_n(int v) {
+    constexpr bool ok[N_COL] = {col_ok<N, 0>(), col_ok<N, 1>(), col_ok<N, 2>(), col_ok<N, 3>(), col_ok<N, 4>(), col_ok<N, 5>()};
+    return v >= 0 && v < N_COL && ok[v];
+}
+
+}  // namespace
+
+int tune_shapes(int kind) { return kind == 0 ? N_ROW : kind == 1 ? N_COL : 0; }
+
+const char *tune_shape_name(int kind, int v) {
+    if (kind == 0 && v >= 0 && v < N_ROW) return ROW_NAMES[v];
+    if (kind == 1 && v >= 0 && v < N_COL) return COL_NAMES[v];
+    return "?";
+}
+
+int tune_default_shape(int kind, int n) {
+    if (kind == 0) {
+        const int thr = n >= 512 ? 128 : 256;  // row_default_threads, unstaged
+        for (int v = 0; v < N_ROW; ++v)
+            if (ROW_SHAPES[v].a == thr && !ROW_SHAPES[v].stg) return v;
+    } else if (kind == 1) {
+        const int w = n >= 2048 ? 4 : n >= 1024 ? 8 : 16;  // col_default_w, staged
+        for (int v = 0; v < N_COL; ++v)
+            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg) return v;
+    }
+    return -1;
+}
+
+bool tune_shape_valid(int kind, int n, int v) {
+    if (kind == 0) {
+        switch (n) {
+            case 256: return row_valid_n<256>(v);
+            case 512: return row_valid_n<512>(v);
+            case 1024: return row_valid_n<1024>(v);
+            case 2048: return row_valid_n<2048>(v);
+        }
+    } else if (kind == 1) {
+        switch (n) {
+            case 256: return col_valid_n<256>(v);
+            case 512: return col_valid_n<512>(v);
+            case 1024: return col_valid_n<1024>(v);
+            case 2048: return col_valid_n<2048>(v);
+        }
+    }
+    return false;
+}
+
+cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s) {
+    if (!tune_shape_valid(0, nx, v)) return cudaErrorInvalidValue;
+    switch (nx) {
+        case 256: return row_n<256>(v, a, s);
+        case 512: return row_n<512>(v, a, s);
+        case 1024: return row_n<1024>(v, a, s);
+        case 2048: return row_n<2048>(v, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s) {
+    if (!tune_shape_valid(1, ny, v)) return cudaErrorInvalidValue;
+    switch (ny) {
+        case 256: return col_n<256>(v, a, s);
+        case 512: return col_n<512>(v, a, s);
+        case 1024: return col_n<1024>(v, a, s);
+        case 2048: return col_n<2048>(v, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace prism

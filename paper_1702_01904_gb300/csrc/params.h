@@ -128,6 +128,13 @@ bool scan_tc_supported(int nw);
 // not fit; window scratch bytes for that grid
 int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py);
 size_t scan_tc_win_bytes(int nw, int grid);
+// autotuner launch shapes of ROW_STD (kind 0) and COL_STD (kind 1), N = 256 ... 2048 (kernels_tune.cu)
+int tune_shapes(int kind);
+const char *tune_shape_name(int kind, int v);
+int tune_default_shape(int kind, int n);
+bool tune_shape_valid(int kind, int n, int v);
+cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s);
+cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s);
 // smallest scan-window / FFT sizes the kernels are instantiated for
 bool row_supported(int n);
 bool col_supported(int n);

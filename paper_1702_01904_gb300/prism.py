@@ -30,6 +30,11 @@ PRISM_PRECISION_FP32 = 0
 PRISM_PRECISION_FP16 = 1
 PRISM_PRECISION_BF16 = 2
 
+PRISM_TUNE_ROW = 0
+PRISM_TUNE_COL = 1
+PRISM_TUNE_MAX_SHAPES = 8
+PRISM_BATCH_AUTOTUNE = 1
+
 # every entry point declared in include/prism.h
 EXPORTED = [
     "prism_plan_create", "prism_plan_destroy", "prism_sync", "prism_last_error",
@@ -42,6 +47,7 @@ EXPORTED = [
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
     "prism_selftest_tcgen05",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
+    "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name",
 ]
 
 
@@ -95,6 +101,10 @@ class PrismServerInfo(ctypes.Structure):
 _lib = None
 
 
+class PrismTuneEntry(ctypes.Structure):
+    _fields_ = [("n_shapes", c_int), ("chosen", c_int), ("default_shape", c_int), ("ms", c_double * 8)]
+
+
 class PrismCell(ctypes.Structure):
     _fields_ = [("grid", PrismGrid), ("V_dev", c_void_p), ("probe", PrismProbe), ("scan", PrismScan),
                 ("det", PrismDetector), ("out_dev", c_void_p)]
@@ -135,7 +145,10 @@ def load(path: str = LIB_PATH):
         "prism_plan_beams": (c_int, [P, POINTER(c_int), POINTER(c_int), c_int]),
         "prism_plan_smatrix": (c_int, [P, POINTER(P)]),
         "prism_plan_smatrix_copy": (c_int, [P, P]),
-        "prism_batch_create": (c_int, [POINTER(PrismCell), c_int, c_size_t, c_int, P, POINTER(P)]),
+        "prism_batch_create": (c_int, [POINTER(PrismCell), c_int, c_size_t, c_int, c_int, P, POINTER(P)]),
+        "prism_plan_autotune": (c_int, [P]),
+        "prism_plan_tune_result": (c_int, [P, c_int, POINTER(PrismTuneEntry)]),
+        "prism_tune_shape_name": (c_char_p, [c_int, c_int]),
         "prism_batch_run": (c_int, [P]),
         "prism_batch_sync": (c_int, [P]),
         "prism_batch_info_get": (c_int, [P, POINTER(PrismBatchInfo)]),
@@ -392,10 +405,11 @@ def make_cell(grid, V_dev, probe, scan, det, out_dev):
     return c
 
 
-def prism_batch_create(cells, hbm_budget_bytes=0, n_branches=0, cuda_stream=None):
+def prism_batch_create(cells, hbm_budget_bytes=0, n_branches=0, cuda_stream=None, flags=0):
     arr = (PrismCell * len(cells))(*cells)
     b = c_void_p()
-    _check(load().prism_batch_create(arr, len(cells), hbm_budget_bytes, n_branches, _stream(cuda_stream), byref(b)))
+    _check(load().prism_batch_create(arr, len(cells), hbm_budget_bytes, n_branches, flags, _stream(cuda_stream),
+                                     byref(b)))
     return b
 
 
@@ -415,3 +429,18 @@ def prism_batch_info_get(batch):
 
 def prism_batch_destroy(batch):
     load().prism_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------ autotuner
+def prism_plan_autotune(plan):
+    _check(load().prism_plan_autotune(plan))
+
+
+def prism_plan_tune_result(plan, kind):
+    e = PrismTuneEntry()
+    _check(load().prism_plan_tune_result(plan, kind, byref(e)))
+    return e
+
+
+def prism_tune_shape_name(kind, shape):
+    return load().prism_tune_shape_name(kind, shape).decode()

@@ -94,6 +94,21 @@ class PrismSimulation:
     def sync(self):
         P.prism_sync(self.plan)
 
+    def autotune(self):
+        """Time every launch shape of the row and column passes on this plan and keep the fastest
+        (prism_plan_autotune); returns {pass: {"chosen": name, "default": name, "ms": {name: ms}}}."""
+        P.prism_plan_autotune(self.plan)
+        return self.tune_result()
+
+    def tune_result(self):
+        out = {}
+        for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col")):
+            e = P.prism_plan_tune_result(self.plan, kind)
+            name = (lambda v: P.prism_tune_shape_name(kind, v) if v >= 0 else "default")
+            out[label] = {"chosen": name(e.chosen), "default": name(e.default_shape),
+                          "ms": {P.prism_tune_shape_name(kind, v): e.ms[v] for v in range(e.n_shapes) if e.ms[v] >= 0}}
+        return out
+
     # -- introspection
     def beams(self):
         return P.prism_plan_beams(self.plan)
@@ -163,7 +178,7 @@ class Batch:
     outputs (``self.outs[i]``, [px*py][nbins]) written at every ``run``; V's contents may change
     between runs."""
 
-    def __init__(self, cells, hbm_budget_bytes: int = 0, n_branches: int = 0, stream=None):
+    def __init__(self, cells, hbm_budget_bytes: int = 0, n_branches: int = 0, stream=None, autotune: bool = False):
         _require_cuda()
         P.load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -187,7 +202,8 @@ class Batch:
             self._keep.append((V, sc, g))
             self.outs.append(out)
         torch.cuda.current_stream().synchronize()
-        self.batch = P.prism_batch_create(cs, hbm_budget_bytes, n_branches, self.stream)
+        self.batch = P.prism_batch_create(cs, hbm_budget_bytes, n_branches, self.stream,
+                                          P.PRISM_BATCH_AUTOTUNE if autotune else 0)
         self.info = P.prism_batch_info_get(self.batch)
 
     def run(self):

@@ -69,6 +69,8 @@ int main(void) {
   printf("prism_batch_info %zu\\n", sizeof(prism_batch_info));
   F(prism_cell, V_dev) F(prism_cell, probe) F(prism_cell, scan) F(prism_cell, det) F(prism_cell, out_dev)
   F(prism_batch_info, graph_nodes) F(prism_batch_info, kernel_launches) F(prism_batch_info, device_bytes)
+  printf("prism_tune_entry %zu\\n", sizeof(prism_tune_entry));
+  F(prism_tune_entry, default_shape) F(prism_tune_entry, ms)
   return 0;
 }
 """)
@@ -78,7 +80,7 @@ int main(void) {
                                                                 check=True).stdout.split("\n") if line)
     cls = {"prism_grid": P.PrismGrid, "prism_probe": P.PrismProbe, "prism_scan": P.PrismScan,
            "prism_detector": P.PrismDetector, "prism_info": P.PrismInfo, "prism_cell": P.PrismCell,
-           "prism_batch_info": P.PrismBatchInfo}
+           "prism_batch_info": P.PrismBatchInfo, "prism_tune_entry": P.PrismTuneEntry}
     for k, v in out.items():
         if "." in k:
             s, m = k.split(".")

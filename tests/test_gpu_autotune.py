@@ -1,0 +1,83 @@
+"""Autotuner: every launch shape of the row and column passes computes bitwise the same transform,
+so an autotuned plan (or batch) must reproduce the default plan's S-matrix and detector stack
+exactly, whatever shapes it picks."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1702_01904_gb300 import prism as P
+from paper_1702_01904_gb300.runtime import Batch, PrismSimulation
+
+pytestmark = pytest.mark.gpu
+
+DET = P.make_detector(0.0, 1.0, 100)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    from paper_1702_01904_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    yield
+    torch.cuda.synchronize()
+
+
+def rand_v(H, n, seed, amp=120.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return torch.from_numpy((amp * rng.random((H, n, n))).astype(np.float32)).cuda()
+
+
+def run(grid, V, tune, x0, y0):
+    sim = PrismSimulation(grid)
+    res = sim.autotune() if tune else None
+    sim.build(V)
+    out = sim.scan(P.make_probe(20.0, c1=8.0), x0, y0, DET, px=len(x0), py=1).cpu().numpy()
+    S = sim.smatrix().cpu().numpy()
+    sim.close()
+    return out, S, res
+
+
+@pytest.mark.parametrize("n,cell,f,prec", [(256, 16.0, 4, P.PRISM_PRECISION_FP32), (512, 32.0, 8, P.PRISM_PRECISION_FP16)])
+def test_autotuned_plan_is_bitwise_identical(n, cell, f, prec):
+    grid = P.make_grid(n, n, 3, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0, precision=prec)
+    V = rand_v(3, n, 11)
+    x0 = np.linspace(0.0, cell, 13, endpoint=False)
+    y0 = np.linspace(1.0, 3.0, 13)
+    a, Sa, _ = run(grid, V, False, x0, y0)
+    b, Sb, res = run(grid, V, True, x0, y0)
+    assert np.array_equal(a, b) and np.array_equal(Sa, Sb)
+    for label in ("row", "col"):
+        ms = res[label]["ms"]
+        assert len(ms) >= 2 and all(v > 0 for v in ms.values())
+        assert res[label]["chosen"] in ms and res[label]["default"] in ms
+        assert ms[res[label]["chosen"]] == min(ms.values())
+    # a second plan of the same shape reuses the cached choice
+    sim = PrismSimulation(grid)
+    assert sim.autotune() == res
+    sim.close()
+
+
+def test_small_grid_has_only_the_default_shape():
+    grid = P.make_grid(64, 64, 2, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0)
+    sim = PrismSimulation(grid)
+    res = sim.autotune()
+    assert res["row"]["chosen"] == "default" and res["row"]["ms"] == {}
+    sim.close()
+
+
+def test_autotuned_batch_equals_untuned():
+    cells = []
+    for i, (n, cell, f, H) in enumerate([(256, 16.0, 4, 3), (512, 32.0, 8, 2), (128, 12.8, 2, 2)]):
+        x0 = np.linspace(0.0, 4.0, 8)
+        cells.append(dict(grid=P.make_grid(n, n, H, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0), V=rand_v(H, n, 20 + i),
+                          probe=P.make_probe(20.0), x0=x0, y0=np.full(8, 1.5), det=DET))
+    outs = []
+    for tune in (False, True):
+        b = Batch(cells, n_branches=2, autotune=tune)
+        b.run()
+        b.sync()
+        outs.append([o.cpu().numpy() for o in b.outs])
+        b.close()
+    for u, t in zip(*outs):
+        assert np.array_equal(u, t)
