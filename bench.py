@@ -264,8 +264,10 @@ def batch_leg(n_cells=64, runs=2, n_branches=4, autotune=True):
         k = np.arange(-int(r) - 1, int(r) + 2)
         nb = int(np.count_nonzero(k[:, None] ** 2 + k[None, :] ** 2 <= r * r * (1 + 1e-12)))
         beams_slices += nb * w.n_slices
-        # build passes stream the wave stack twice per slice (32 B per beam-pixel) plus t_p
-        build_bytes += nb * w.n_slices * w.nx * w.ny * 32 + w.n_slices * w.nx * w.ny * 8
+        # build passes stream the kept columns of the wave stack twice per slice (32 B per kept
+        # beam-pixel) plus t_p
+        fk = (2 * (int(math.ceil(w.aa_frac * w.nx / 2)) - 1) + 1) / w.nx
+        build_bytes += nb * w.n_slices * w.nx * w.ny * 32 * fk + w.n_slices * w.nx * w.ny * 8
         probes += w.scan_px * w.scan_py
         key = f"{w.nx}px_f{w.f}"
         mix[key] = mix.get(key, 0) + 1
@@ -552,13 +554,18 @@ def main():
     peak_note = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
     px = w.nx * w.ny
-    # per-launch algorithmic bytes: wave stack read + write (8 B per complex64 pixel each way) for
-    # all beams, plus the slice's transmission function for the row pass
+    # kept fraction of the mixed-domain wave: the propagator's anti-aliasing aperture zeroes every
+    # column |kx| >= K+1 (K = ceil(aa_frac nx / 2) - 1 on a square cell), and the passes neither
+    # read nor write those columns
+    K = int(math.ceil(w.aa_frac * w.nx / 2)) - 1
+    fk = (2 * K + 1) / w.nx
+    # per-launch algorithmic bytes: the kept part of the wave stack read + written (8 B per complex64
+    # pixel each way) for all beams, plus the slice's transmission function for the row pass
     alg = {
-        "row": 2 * Bn * px * 8 + px * 8,
-        "col": 2 * Bn * px * 8,
-        "row_plane": Bn * px * 8 + px * 8,
-        "row_out": Bn * (px // 2) * 8 + Bn * (px // 4) * 8,
+        "row": 2 * Bn * px * 8 * fk + px * 8,
+        "col": 2 * Bn * px * 8 * fk,
+        "row_plane": Bn * px * 8 * fk + px * 8,
+        "row_out": Bn * (px // 2) * 8 * fk + Bn * (px // 4) * 8,
         "transmission": w.n_slices * px * (4 + 8),
         # 16-bit mode: FP32 S of the batch read twice (scale, convert), 16-bit pixel-major S written
         "quantize": 2 * Bn * (px // 4) * 8 + (px // 4) * 2 * ((Bn + 7) // 8 * 8) * 2,

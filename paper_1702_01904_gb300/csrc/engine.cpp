@@ -164,6 +164,7 @@ struct GridTables {
     std::vector<double> prop_dz;      // distinct thicknesses
     std::vector<float2> prop_x, prop_y;
     std::vector<int> aa_kmax;
+    int kx_half = 0;                  // columns |kx| < kx_half pass the aperture (0: all columns)
     double q_aa;
     std::vector<float2> twr_f, twr_i, twc_f, twc_i;
 };
@@ -241,6 +242,14 @@ static int build_grid_tables(const prism_grid *g, GridTables &T) {
         }
         T.aa_kmax[kx] = kmax;
     }
+    // columns that pass the aperture: |kx| <= K, a symmetric interval (else no pruning)
+    int K = -1;
+    for (int kx = 0; kx < T.nx; ++kx)
+        if (T.aa_kmax[kx] >= 0) K = std::max(K, std::abs(signed_index(kx, T.nx)));
+    bool interval = K >= 0;
+    for (int kx = 0; kx < T.nx && interval; ++kx)
+        interval = (T.aa_kmax[kx] >= 0) == (std::abs(signed_index(kx, T.nx)) <= K);
+    T.kx_half = interval && K + 1 < T.nx / 2 ? K + 1 : 0;
     int a1, a2;
     fft_split(T.nx, &a1, &a2);
     T.twr_f = stage_table(T.nx, a1, a2);
@@ -603,6 +612,7 @@ static RowArgs row_args(prism_plan *P) {
     a.ny = P->g.ny;
     a.f = P->g.f;
     a.downsample = P->g.downsample;
+    a.kx_half = P->T.kx_half;
     a.tw = P->tw64;
     return a;
 }
@@ -658,6 +668,7 @@ static int build_launches(prism_plan *P, const float *V_dev) {
             ColArgs ca = col_args(P->T, P->wave, P->prop_x + (size_t)pi * g.nx, P->prop_y + (size_t)pi * g.ny,
                                   P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
             ca.batch = nb;
+            ca.kx_half = P->T.kx_half;
             rc = plan_launch(P, PRISM_K_COL, [&] {
                 return P->tune_shape[1] >= 0 ? launch_col_shape(g.ny, P->tune_shape[1], ca, P->stream)
                                              : launch_col(g.ny, COL_STD, ca, P->stream);
@@ -897,6 +908,17 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             }
         }
     }
+    // the row passes may skip the columns the aperture zeroes only if the initial probe is zero
+    // there too (a probe aperture wider than the anti-aliasing aperture keeps every column)
+    int kx_half = T.kx_half;
+    for (int ky = 0; ky < ny && kx_half; ++ky)
+        for (int kx = kx_half; kx <= nx - kx_half; ++kx) {
+            const float2 v = pbase[(size_t)ky * nx + kx];
+            if (v.x != 0.f || v.y != 0.f) {
+                kx_half = 0;
+                break;
+            }
+        }
     std::vector<int> off, idx;
     detector_csr(nx, ny, g.cell_x, g.cell_y, 1, T.lam, det, off, idx);
     if (scratch_bytes == 0) scratch_bytes = (size_t)1 << 30;
@@ -977,12 +999,16 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             ra.tw_inv = twr_i;
             ra.ny = ny;
             ra.n_rows = nb * ny;
+            ra.kx_half = kx_half;  // every row pass reads a wave band-limited in x (aperture and probe)
             ra.tw = tw;
             if ((rc = check(launch_row(nx, ROW_STD, ra, st), "row pass"))) return done(rc);
             const int pi = T.slice_prop[p];
             ColArgs ca = col_args(T, wave, prop_x + (size_t)pi * nx, prop_y + (size_t)pi * ny, aa, twc_f, twc_i, tw);
             ca.batch = nb;
             ca.inten = inten;
+            // the detecting pass reads every column (the initial probe left exact zeros in the
+            // columns the row passes skip) and writes every intensity
+            ca.kx_half = p + 1 == g.n_slices ? 0 : kx_half;
             if ((rc = check(launch_col(ny, p + 1 == g.n_slices ? COL_DETECT : COL_STD, ca, st), "column pass"))) return done(rc);
         }
         BinArgs ba;
@@ -1227,6 +1253,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
             ra.n_rows = P->batch * g.ny;
             ColArgs ca = col_args(P->T, P->wave, P->prop_x, P->prop_y, P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
             ca.batch = P->batch;
+            ca.kx_half = P->T.kx_half;
             auto once = [&]() {
                 return kind == 0 ? launch_row_shape(g.nx, v, ra, P->stream) : launch_col_shape(g.ny, v, ca, P->stream);
             };

@@ -15,13 +15,15 @@ namespace {
 struct Shape {
     int a;     // row pass: threads per CTA; column pass: interleaved columns per CTA
     bool stg;  // cp.async staging of the next row / tile
+    int mb;    // column pass: CTAs per SM the registers must allow (0: default rule)
 };
-constexpr Shape ROW_SHAPES[] = {{128, false}, {256, false}, {128, true}, {256, true}};
-constexpr Shape COL_SHAPES[] = {{4, true}, {8, true}, {16, true}, {4, false}, {8, false}, {16, false}};
+constexpr Shape ROW_SHAPES[] = {{128, false, 0}, {256, false, 0}, {128, true, 0}, {256, true, 0}};
+constexpr Shape COL_SHAPES[] = {{4, true, 0}, {8, true, 0}, {16, true, 0}, {4, false, 0}, {8, false, 0}, {16, false, 0},
+                                {8, false, 2}, {4, true, 3}};
 constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
 constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
 const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged"};
-const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W16"};
+const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W16", "W8, 2/SM", "W4, staged, 3/SM"};
 
 template <int N, int I>
 constexpr bool row_ok() {
@@ -30,8 +32,8 @@ constexpr bool row_ok() {
 }
 template <int N, int I>
 constexpr bool col_ok() {
-    using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg>;
-    return C::SMEM <= 227 * 1024 && C::THREADS <= 1024;
+    using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>;
+    return C::SMEM <= 227 * 1024 && C::THREADS <= 1024 && (size_t)C::MINB * (C::SMEM + 1024) <= 228 * 1024;
 }
 
 template <int N, int I>
@@ -42,7 +44,7 @@ cudaError_t row_shape(const RowArgs &a, cudaStream_t s) {
 template <int N, int I>
 cudaError_t col_shape(const ColArgs &a, cudaStream_t s) {
     if (a.batch <= 0) return cudaSuccess;
-    return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg>(a, s);
+    return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>(a, s);
 }
 
 template <int N>
@@ -64,6 +66,8 @@ cudaError_t col_n(int v, const ColArgs &a, cudaStream_t s) {
         case 3: return col_shape<N, 3>(a, s);
         case 4: return col_shape<N, 4>(a, s);
         case 5: return col_shape<N, 5>(a, s);
+        case 6: return col_shape<N, 6>(a, s);
+        case 7: return col_shape<N, 7>(a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -74,7 +78,8 @@ bool row_valid_n(int v) {
 }
 template <int N>
 bool col_valid_n(int v) {
-    constexpr bool ok[N_COL] = {col_ok<N, 0>(), col_ok<N, 1>(), col_ok<N, 2>(), col_ok<N, 3>(), col_ok<N, 4>(), col_ok<N, 5>()};
+    constexpr bool ok[N_COL] = {col_ok<N, 0>(), col_ok<N, 1>(), col_ok<N, 2>(), col_ok<N, 3>(),
+                                col_ok<N, 4>(), col_ok<N, 5>(), col_ok<N, 6>(), col_ok<N, 7>()};
     return v >= 0 && v < N_COL && ok[v];
 }
 
@@ -96,7 +101,7 @@ int tune_default_shape(int kind, int n) {
     } else if (kind == 1) {
         const int w = n >= 2048 ? 4 : n >= 1024 ? 8 : 16;  // col_default_w, staged
         for (int v = 0; v < N_COL; ++v)
-            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg) return v;
+            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg && COL_SHAPES[v].mb == 0) return v;
     }
     return -1;
 }

@@ -29,6 +29,10 @@ struct RowArgs {
     int f;                     // PLANE
     int beam0;                 // first beam of this batch (PLANE, OUT)
     int downsample;            // OUT
+    int kx_half;               // > 0: only kx = -(kx_half-1) ... kx_half-1 of the mixed-domain wave are
+                               // non-zero (the propagator's anti-aliasing aperture zeroes the rest):
+                               // loads there are replaced by exact zeros and stores are skipped
+                               // (STD, PLANE, OUT); 0: every kx
     Tw64 tw;
 };
 
@@ -47,6 +51,8 @@ struct ColArgs {
     int nx;
     int batch;
     float probe_scale;         // PROBE: 1 / (nx ny)
+    int kx_half;               // > 0: only the column tiles holding kx = -(kx_half-1) ... kx_half-1 are
+                               // processed (every other column is zero after the propagator); 0: all
     Tw64 tw;
 };
 

@@ -123,7 +123,10 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
             y = row - b * a.ny;
         }
     };
-    // stage a whole row into this slot's buffer: NX*8 bytes in 16-byte pieces, E/2 per lane
+    // kx (FFT order) that can be non-zero in the mixed domain: the column pass zeroes the others
+    auto keep = [&](int e) { return a.kx_half == 0 || e < a.kx_half || e > NX - a.kx_half; };
+    // stage a whole row into this slot's buffer: NX*8 bytes in 16-byte pieces, E/2 per lane (pieces
+    // of two zero columns are skipped)
     auto stage = [&](int row) {
         int b, y;
         locate(row, b, y);
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
 #pragma unroll
         for (int k = 0; k < E / 2; ++k) {
             const int e = 2 * (t + T * k);
-            cp_async16(stg + e, w + e);
+            if (keep(e) || keep(e + 1)) cp_async16(stg + e, w + e);
         }
         cp_async_commit();
     };
@@ -169,13 +172,19 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                 cp_async_wait_all();
                 __syncwarp();
 #pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = stg[Inv::in_elem(r, t)];
+                for (int r = 0; r < E; ++r) {
+                    const int e = Inv::in_elem(r, t);
+                    v[r] = keep(e) ? stg[e] : make_float2(0.f, 0.f);
+                }
                 __syncwarp();  // the buffer is refilled next
                 if (it + 1 < iters) stage(row + stride);
             } else {
                 const float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
 #pragma unroll
-                for (int r = 0; r < E; ++r) v[r] = __ldcs(w + Inv::in_elem(r, t));
+                for (int r = 0; r < E; ++r) {
+                    const int e = Inv::in_elem(r, t);
+                    v[r] = keep(e) ? __ldcs(w + e) : make_float2(0.f, 0.f);
+                }
             }
             if constexpr (MODE == ROW_STD) {
                 // t_p is shared by all beams: L2-cached, not L1 (keeps L1 for the FFT's traffic)
@@ -219,7 +228,10 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
             if (valid) {
                 float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
 #pragma unroll
-                for (int r = 0; r < E; ++r) __stcs(w + Fwd::out_elem(r, t), v[r]);
+                for (int r = 0; r < E; ++r) {
+                    const int e = Fwd::out_elem(r, t);
+                    if (keep(e)) __stcs(w + e, v[r]);
+                }
             }
         }
     }
@@ -247,8 +259,9 @@ static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
 template <int NY>
 constexpr int col_default_w() { return NY >= 2048 ? 4 : NY >= 1024 ? 8 : 16; }
 
-// WC interleaved columns per CTA, STG: cp.async staging of the next tile (launch shape only)
-template <int NY, int WC = col_default_w<NY>(), bool STG = true>
+// WC interleaved columns per CTA, STG: cp.async staging of the next tile, MB: CTAs per SM the
+// register allocation must allow (0: the default rule) -- launch shape only
+template <int NY, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
 struct ColCfg {
     using FS = FftShape<NY>;
     static constexpr int W = WC;           // interleaved columns per CTA
@@ -256,14 +269,14 @@ struct ColCfg {
     static constexpr bool STAGE = STG;     // cp.async staging of the next tile
     static constexpr bool SMEM_TW = false; // stage twiddles in shared memory (else L1 broadcast loads)
     static constexpr bool PERSIST = true;  // grid = resident CTAs, each looping over tiles
-    static constexpr int MINB = (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
+    static constexpr int MINB = MB > 0 ? MB : (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
     static constexpr int EX = ColExSize<NY, W>::value;
     static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true>
-__global__ void __launch_bounds__(ColCfg<NY, WC, STG>::THREADS, ColCfg<NY, WC, STG>::MINB) k_col(const __grid_constant__ ColArgs a) {
-    using C = ColCfg<NY, WC, STG>;
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
+__global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, WC, STG, MB>::MINB) k_col(const __grid_constant__ ColArgs a) {
+    using C = ColCfg<NY, WC, STG, MB>;
     using FS = FftShape<NY>;
     using Fwd = FwdFft<NY>;
     using Inv = InvFft<NY>;
@@ -286,7 +299,16 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG>::THREADS, ColCfg<NY, WC, S
     const int c = threadIdx.x % W, t = threadIdx.x / W;
     ColExchange<FS::N1, FS::N2, W> exF{exb, c};
     ColExchange<FS::N2, FS::N1, W> exI{exb, c};
-    const int tiles_x = a.nx / W;
+    // column tiles of W columns: all of them, or (kx_half > 0) only the low ones [0, lo W) and the
+    // high ones [hs W, nx), which hold every kx the anti-aliasing aperture lets through
+    const int tw_all = a.nx / W;
+    int lo = tw_all, hs = tw_all;
+    if (a.kx_half > 0) {
+        lo = (a.kx_half + W - 1) / W;
+        hs = (a.nx - a.kx_half + 1) / W;
+        if (lo >= hs) lo = hs = tw_all;
+    }
+    const int tiles_x = lo + (tw_all - hs);
     const int ntiles = tiles_x * a.batch;
     const int iters = (ntiles + gridDim.x - 1) / gridDim.x;  // uniform over the grid
 
@@ -295,7 +317,8 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG>::THREADS, ColCfg<NY, WC, S
     auto locate = [&](int tile, int &b, int &kx0) {
         tile = tile < ntiles ? tile : ntiles - 1;
         b = tile / tiles_x;
-        kx0 = (tile - b * tiles_x) * W;
+        const int ti = tile - b * tiles_x;
+        kx0 = (ti < lo ? ti : hs + (ti - lo)) * W;
     };
     auto stage = [&](int tile) {
         int b, kx0;
@@ -378,18 +401,29 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG>::THREADS, ColCfg<NY, WC, S
     }
 }
 
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true>
+// column tiles a launch processes (the kernel's tile enumeration)
+static inline long long col_tiles(int nx, int w, int kx_half, int batch) {
+    int lo = nx / w, hs = nx / w;
+    if (kx_half > 0) {
+        lo = (kx_half + w - 1) / w;
+        hs = (nx - kx_half + 1) / w;
+        if (lo >= hs) lo = hs = nx / w;
+    }
+    return (long long)(lo + (nx / w - hs)) * batch;
+}
+
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
 static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
-    using C = ColCfg<NY, WC, STG>;
+    using C = ColCfg<NY, WC, STG, MB>;
     if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024) {
         return cudaErrorInvalidConfiguration;
     } else {
         if (a.nx % C::W) return cudaErrorInvalidValue;
         int grid = 0;
-        cudaError_t e = persistent_grid(k_col<NY, MODE, WC, STG>, C::THREADS, C::SMEM, (long long)(a.nx / C::W) * a.batch,
+        cudaError_t e = persistent_grid(k_col<NY, MODE, WC, STG, MB>, C::THREADS, C::SMEM, col_tiles(a.nx, C::W, a.kx_half, a.batch),
                                         &grid, C::PERSIST);
         if (e != cudaSuccess) return e;
-        k_col<NY, MODE, WC, STG><<<grid, C::THREADS, C::SMEM, s>>>(a);
+        k_col<NY, MODE, WC, STG, MB><<<grid, C::THREADS, C::SMEM, s>>>(a);
         return cudaGetLastError();
     }
 }
