@@ -165,6 +165,7 @@ struct GridTables {
     std::vector<float2> prop_x, prop_y;
     std::vector<int> aa_kmax;
     int kx_half = 0;                  // columns |kx| < kx_half pass the aperture (0: all columns)
+    int band4 = 0;                    // every column passes at most |ky| < ny/4
     double q_aa;
     std::vector<float2> twr_f, twr_i, twc_f, twc_i;
 };
@@ -250,6 +251,7 @@ static int build_grid_tables(const prism_grid *g, GridTables &T) {
     for (int kx = 0; kx < T.nx && interval; ++kx)
         interval = (T.aa_kmax[kx] >= 0) == (std::abs(signed_index(kx, T.nx)) <= K);
     T.kx_half = interval && K + 1 < T.nx / 2 ? K + 1 : 0;
+    T.band4 = *std::max_element(T.aa_kmax.begin(), T.aa_kmax.end()) < T.ny / 4;
     int a1, a2;
     fft_split(T.nx, &a1, &a2);
     T.twr_f = stage_table(T.nx, a1, a2);
@@ -669,6 +671,7 @@ static int build_launches(prism_plan *P, const float *V_dev) {
                                   P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
             ca.batch = nb;
             ca.kx_half = P->T.kx_half;
+            ca.band4 = P->T.band4;
             rc = plan_launch(P, PRISM_K_COL, [&] {
                 return P->tune_shape[1] >= 0 ? launch_col_shape(g.ny, P->tune_shape[1], ca, P->stream)
                                              : launch_col(g.ny, COL_STD, ca, P->stream);
@@ -1009,6 +1012,7 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             // the detecting pass reads every column (the initial probe left exact zeros in the
             // columns the row passes skip) and writes every intensity
             ca.kx_half = p + 1 == g.n_slices ? 0 : kx_half;
+            ca.band4 = T.band4;
             if ((rc = check(launch_col(ny, p + 1 == g.n_slices ? COL_DETECT : COL_STD, ca, st), "column pass"))) return done(rc);
         }
         BinArgs ba;
@@ -1254,6 +1258,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
             ColArgs ca = col_args(P->T, P->wave, P->prop_x, P->prop_y, P->aa_kmax, P->twc_f, P->twc_i, P->tw64);
             ca.batch = P->batch;
             ca.kx_half = P->T.kx_half;
+            ca.band4 = P->T.band4;
             auto once = [&]() {
                 return kind == 0 ? launch_row_shape(g.nx, v, ra, P->stream) : launch_col_shape(g.ny, v, ca, P->stream);
             };

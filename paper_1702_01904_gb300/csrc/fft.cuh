@@ -20,6 +20,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "params.h"  // Tw64: W_64^j = exp(-2 pi i j / 64), computed on the host in double
 
 namespace prism {
@@ -245,8 +248,38 @@ struct BlockFft {
     }
 
     // element index held in register r (input / output layouts)
-    __device__ __forceinline__ static int in_elem(int r, int t) { return N2 * (r / J) + t + T * (r % J); }
-    __device__ __forceinline__ static int out_elem(int r, int t) { return t + T * (r % I) + N1 * (r / I); }
+    __host__ __device__ __forceinline__ static constexpr int in_elem(int r, int t) { return N2 * (r / J) + t + T * (r % J); }
+    __host__ __device__ __forceinline__ static constexpr int out_elem(int r, int t) { return t + T * (r % I) + N1 * (r / I); }
+};
+
+// Band classes of the registers of a transform of length N for the band |k| < N/4 (FFT order):
+// BAND_OUT if register r holds an element outside the band in every thread, BAND_IN if inside in
+// every thread, BAND_MIXED otherwise.  With the band known at compile time, a register that is
+// BAND_OUT in the input is a literal zero and one that is BAND_OUT in the output is never used, so
+// the compiler removes their arithmetic from the first and the last register DFT.
+enum { BAND_IN = 0, BAND_OUT = 1, BAND_MIXED = 2 };
+
+// fn(std::integral_constant<int, r>) for r = 0 ... N-1, unrolled at compile time (lets the body
+// branch on compile-time properties of the register index)
+template <class Fn, int... Is>
+__device__ __forceinline__ void static_for_impl(Fn &fn, std::integer_sequence<int, Is...>) {
+    (fn(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class Fn>
+__device__ __forceinline__ void static_for(Fn fn) {
+    static_for_impl(fn, std::make_integer_sequence<int, N>{});
+}
+template <class F, int N>
+struct BandClass {
+    __host__ __device__ static constexpr bool in_band(int e) { return e < N / 4 || e > N - N / 4; }
+    __host__ __device__ static constexpr int of(int r, bool input) {
+        bool any_in = false, any_out = false;
+        for (int t = 0; t < F::T; ++t) {
+            const int e = input ? F::in_elem(r, t) : F::out_elem(r, t);
+            (in_band(e) ? any_in : any_out) = true;
+        }
+        return any_in && any_out ? BAND_MIXED : any_in ? BAND_IN : BAND_OUT;
+    }
 };
 
 template <int N>

@@ -1,5 +1,6 @@
 // kernels_tune.cu -- the alternative launch shapes of the two multislice passes that the autotuner
-// times (ROW_STD and COL_STD, N = 256 ... 2048).  A shape changes only how rows or columns are
+// times (ROW_STD and COL_STD, N = 256 ... 2048): the column shapes and the shape tables here, the
+// row shapes in kernels_tune_row.cu (a separate unit so that both compile in parallel).  A shape changes only how rows or columns are
 // spread over threads and whether the next row/tile is staged through shared memory with
 // cp.async; every shape computes bitwise the same transform.
 #include <cuda_runtime.h>
@@ -7,29 +8,19 @@
 #include "fft.cuh"
 #include "params.h"
 #include "pass_kernels.cuh"
+#include "tune_shapes.cuh"
 
 namespace prism {
 
 namespace {
 
-struct Shape {
-    int a;     // row pass: threads per CTA; column pass: interleaved columns per CTA
-    bool stg;  // cp.async staging of the next row / tile
-    int mb;    // column pass: CTAs per SM the registers must allow (0: default rule)
-};
-constexpr Shape ROW_SHAPES[] = {{128, false, 0}, {256, false, 0}, {128, true, 0}, {256, true, 0}};
-constexpr Shape COL_SHAPES[] = {{4, true, 0}, {8, true, 0}, {16, true, 0}, {4, false, 0}, {8, false, 0}, {16, false, 0},
-                                {8, false, 2}, {4, true, 3}};
-constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
-constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
+using tune::COL_SHAPES;
+using tune::N_COL;
+using tune::N_ROW;
+using tune::ROW_SHAPES;
 const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged"};
 const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W16", "W8, 2/SM", "W4, staged, 3/SM"};
 
-template <int N, int I>
-constexpr bool row_ok() {
-    using C = RowCfg<N, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>;
-    return C::SMEM <= 227 * 1024 && ROW_SHAPES[I].a % C::T == 0 && ROW_SHAPES[I].a <= 1024;
-}
 template <int N, int I>
 constexpr bool col_ok() {
     using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>;
@@ -37,26 +28,11 @@ constexpr bool col_ok() {
 }
 
 template <int N, int I>
-cudaError_t row_shape(const RowArgs &a, cudaStream_t s) {
-    if (a.n_rows <= 0) return cudaSuccess;
-    return row_go<N, ROW_STD, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>(a, s);
-}
-template <int N, int I>
 cudaError_t col_shape(const ColArgs &a, cudaStream_t s) {
     if (a.batch <= 0) return cudaSuccess;
     return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>(a, s);
 }
 
-template <int N>
-cudaError_t row_n(int v, const RowArgs &a, cudaStream_t s) {
-    switch (v) {
-        case 0: return row_shape<N, 0>(a, s);
-        case 1: return row_shape<N, 1>(a, s);
-        case 2: return row_shape<N, 2>(a, s);
-        case 3: return row_shape<N, 3>(a, s);
-    }
-    return cudaErrorInvalidValue;
-}
 template <int N>
 cudaError_t col_n(int v, const ColArgs &a, cudaStream_t s) {
     switch (v) {
@@ -70,11 +46,6 @@ cudaError_t col_n(int v, const ColArgs &a, cudaStream_t s) {
         case 7: return col_shape<N, 7>(a, s);
     }
     return cudaErrorInvalidValue;
-}
-template <int N>
-bool row_valid_n(int v) {
-    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>()};
-    return v >= 0 && v < N_ROW && ok[v];
 }
 template <int N>
 bool col_valid_n(int v) {
@@ -108,12 +79,7 @@ int tune_default_shape(int kind, int n) {
 
 bool tune_shape_valid(int kind, int n, int v) {
     if (kind == 0) {
-        switch (n) {
-            case 256: return row_valid_n<256>(v);
-            case 512: return row_valid_n<512>(v);
-            case 1024: return row_valid_n<1024>(v);
-            case 2048: return row_valid_n<2048>(v);
-        }
+        return tune_row_valid(n, v);
     } else if (kind == 1) {
         switch (n) {
             case 256: return col_valid_n<256>(v);
@@ -127,13 +93,7 @@ bool tune_shape_valid(int kind, int n, int v) {
 
 cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s) {
     if (!tune_shape_valid(0, nx, v)) return cudaErrorInvalidValue;
-    switch (nx) {
-        case 256: return row_n<256>(v, a, s);
-        case 512: return row_n<512>(v, a, s);
-        case 1024: return row_n<1024>(v, a, s);
-        case 2048: return row_n<2048>(v, a, s);
-    }
-    return cudaErrorInvalidValue;
+    return tune_row_launch(nx, v, a, s);
 }
 
 cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s) {

@@ -53,6 +53,9 @@ struct ColArgs {
     float probe_scale;         // PROBE: 1 / (nx ny)
     int kx_half;               // > 0: only the column tiles holding kx = -(kx_half-1) ... kx_half-1 are
                                // processed (every other column is zero after the propagator); 0: all
+    int band4;                 // 1: the aperture keeps |ky| < ny/4 on every column (aa_kmax < ny/4), so
+                               // the column transforms may drop that band's complement at compile
+                               // time (STD, DETECT)
     Tw64 tw;
 };
 

@@ -86,7 +86,8 @@ struct RowCfg {
     static constexpr size_t SMEM = (size_t)(2 * NX + SLOTS * SLOT_F2) * sizeof(float2);
 };
 
-template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false>
+// BL: the kept columns are exactly |kx| < NX/4 (kx_half == NX/4), known at compile time
+template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool BL = false>
 __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) {
     using C = RowCfg<NX, THR, STG>;
     using FS = FftShape<NX>;
@@ -124,7 +125,10 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
         }
     };
     // kx (FFT order) that can be non-zero in the mixed domain: the column pass zeroes the others
-    auto keep = [&](int e) { return a.kx_half == 0 || e < a.kx_half || e > NX - a.kx_half; };
+    auto keep = [&](int e) {
+        if constexpr (BL) return e < NX / 4 || e > NX - NX / 4;
+        else return a.kx_half == 0 || e < a.kx_half || e > NX - a.kx_half;
+    };
     // stage a whole row into this slot's buffer: NX*8 bytes in 16-byte pieces, E/2 per lane (pieces
     // of two zero columns are skipped)
     auto stage = [&](int row) {
@@ -171,20 +175,26 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
             if constexpr (C::STAGE) {
                 cp_async_wait_all();
                 __syncwarp();
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
+                static_for<E>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    constexpr int cls = BL ? BandClass<Inv, NX>::of(r, true) : BAND_MIXED;
                     const int e = Inv::in_elem(r, t);
-                    v[r] = keep(e) ? stg[e] : make_float2(0.f, 0.f);
-                }
+                    if constexpr (cls == BAND_OUT) v[r] = make_float2(0.f, 0.f);
+                    else if constexpr (cls == BAND_IN) v[r] = stg[e];
+                    else v[r] = keep(e) ? stg[e] : make_float2(0.f, 0.f);
+                });
                 __syncwarp();  // the buffer is refilled next
                 if (it + 1 < iters) stage(row + stride);
             } else {
                 const float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
+                static_for<E>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    constexpr int cls = BL ? BandClass<Inv, NX>::of(r, true) : BAND_MIXED;
                     const int e = Inv::in_elem(r, t);
-                    v[r] = keep(e) ? __ldcs(w + e) : make_float2(0.f, 0.f);
-                }
+                    if constexpr (cls == BAND_OUT) v[r] = make_float2(0.f, 0.f);
+                    else if constexpr (cls == BAND_IN) v[r] = __ldcs(w + e);
+                    else v[r] = keep(e) ? __ldcs(w + e) : make_float2(0.f, 0.f);
+                });
             }
             if constexpr (MODE == ROW_STD) {
                 // t_p is shared by all beams: L2-cached, not L1 (keeps L1 for the FFT's traffic)
@@ -227,14 +237,29 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
             Fwd::run(v, t, twf, a.tw, exF);
             if (valid) {
                 float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
+                static_for<E>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    constexpr int cls = BL ? BandClass<Fwd, NX>::of(r, false) : BAND_MIXED;
                     const int e = Fwd::out_elem(r, t);
-                    if (keep(e)) __stcs(w + e, v[r]);
-                }
+                    if constexpr (cls == BAND_IN) __stcs(w + e, v[r]);
+                    else if constexpr (cls == BAND_MIXED) {
+                        if (keep(e)) __stcs(w + e, v[r]);
+                    }
+                });
             }
         }
     }
+}
+
+template <int NX, int MODE, int THR, bool STG, bool BL>
+static cudaError_t row_go_bl(const RowArgs &a, cudaStream_t s) {
+    using C = RowCfg<NX, THR, STG>;
+    int grid = 0;
+    cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG, BL>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
+                                    &grid, C::PERSIST);
+    if (e != cudaSuccess) return e;
+    k_row<NX, MODE, THR, STG, BL><<<grid, C::THREADS, C::SMEM, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false>
@@ -243,12 +268,11 @@ static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
     if constexpr (C::SMEM > 227 * 1024 || THR % C::T != 0 || THR > 1024) {
         return cudaErrorInvalidConfiguration;
     } else {
-        int grid = 0;
-        cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
-                                        &grid, C::PERSIST);
-        if (e != cudaSuccess) return e;
-        k_row<NX, MODE, THR, STG><<<grid, C::THREADS, C::SMEM, s>>>(a);
-        return cudaGetLastError();
+        // the compile-time band for the default aperture (aa_frac 1/2 on a square grid: |kx| < NX/4)
+        if constexpr (NX >= 64) {
+            if (a.kx_half * 4 == NX) return row_go_bl<NX, MODE, THR, STG, true>(a, s);
+        }
+        return row_go_bl<NX, MODE, THR, STG, false>(a, s);
     }
 }
 
@@ -274,7 +298,8 @@ struct ColCfg {
     static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
+// BL: every column keeps at most |ky| < NY/4 (band4), known at compile time
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool BL = false>
 __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, WC, STG, MB>::MINB) k_col(const __grid_constant__ ColArgs a) {
     using C = ColCfg<NY, WC, STG, MB>;
     using FS = FftShape<NY>;
@@ -373,13 +398,18 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, W
             // aperture, which on column kx is |ky| <= aa_kmax[kx]
             const float2 px = __ldg(a.prop_x + kx);
             const int kymax = __ldg(a.aa_kmax + kx);
-#pragma unroll
-            for (int r = 0; r < E; ++r) {
-                const int ky = Fwd::out_elem(r, t);
-                const int kys = ky < (NY >> 1) ? ky : ky - NY;
-                const int aky = kys < 0 ? -kys : kys;
-                v[r] = aky <= kymax ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
-            }
+            static_for<E>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr int cls = BL ? BandClass<Fwd, NY>::of(r, false) : BAND_MIXED;
+                if constexpr (cls == BAND_OUT) {
+                    v[r] = make_float2(0.f, 0.f);  // outside |ky| < NY/4 on every column
+                } else {
+                    const int ky = Fwd::out_elem(r, t);
+                    const int kys = ky < (NY >> 1) ? ky : ky - NY;
+                    const int aky = kys < 0 ? -kys : kys;
+                    v[r] = aky <= kymax ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
+                }
+            });
             if constexpr (MODE == COL_DETECT) {
                 if (valid) {
                     float *icol = a.inten + (size_t)b * NY * a.nx + kx;
@@ -420,10 +450,19 @@ static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
     } else {
         if (a.nx % C::W) return cudaErrorInvalidValue;
         int grid = 0;
-        cudaError_t e = persistent_grid(k_col<NY, MODE, WC, STG, MB>, C::THREADS, C::SMEM, col_tiles(a.nx, C::W, a.kx_half, a.batch),
-                                        &grid, C::PERSIST);
+        const long long work = col_tiles(a.nx, C::W, a.kx_half, a.batch);
+        cudaError_t e;
+        if constexpr (NY >= 64 && MODE != COL_PROBE) {
+            if (a.band4) {
+                e = persistent_grid(k_col<NY, MODE, WC, STG, MB, true>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
+                if (e != cudaSuccess) return e;
+                k_col<NY, MODE, WC, STG, MB, true><<<grid, C::THREADS, C::SMEM, s>>>(a);
+                return cudaGetLastError();
+            }
+        }
+        e = persistent_grid(k_col<NY, MODE, WC, STG, MB, false>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
         if (e != cudaSuccess) return e;
-        k_col<NY, MODE, WC, STG, MB><<<grid, C::THREADS, C::SMEM, s>>>(a);
+        k_col<NY, MODE, WC, STG, MB, false><<<grid, C::THREADS, C::SMEM, s>>>(a);
         return cudaGetLastError();
     }
 }

@@ -1,0 +1,25 @@
+// tune_shapes.cuh -- launch shapes of the row and column passes that the autotuner times
+// (kernels_tune.cu: column shapes and the tables; kernels_tune_row.cu: row shapes).
+#pragma once
+
+namespace prism {
+namespace tune {
+
+struct Shape {
+    int a;     // row pass: threads per CTA; column pass: interleaved columns per CTA
+    bool stg;  // cp.async staging of the next row / tile
+    int mb;    // column pass: CTAs per SM the registers must allow (0: default rule)
+};
+constexpr Shape ROW_SHAPES[] = {{128, false, 0}, {256, false, 0}, {128, true, 0}, {256, true, 0}};
+constexpr Shape COL_SHAPES[] = {{4, true, 0}, {8, true, 0}, {16, true, 0}, {4, false, 0}, {8, false, 0}, {16, false, 0},
+                                {8, false, 2}, {4, true, 3}};
+constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
+constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
+
+}  // namespace tune
+
+// row shapes (kernels_tune_row.cu)
+bool tune_row_valid(int n, int v);
+cudaError_t tune_row_launch(int nx, int v, const RowArgs &a, cudaStream_t s);
+
+}  // namespace prism
