@@ -313,7 +313,8 @@ def ncu_case(precision="fp32"):
     w = specimens.workload_amorphous_carbon(n_slices=4, alpha_mrad=20.0 if half else 9.0)
     V = torch.from_numpy(w.potential()).cuda()
     x0, y0 = w.scan_positions()
-    code = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16}[precision]
+    code = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16,
+            "fp16x2": PR.PRISM_PRECISION_FP16X2}[precision]
     sim = PrismSimulation(PR.grid_from_workload(w, precision=code))
     det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
     probe = PR.make_probe(w.alpha_mrad)
@@ -338,7 +339,7 @@ def main():
     ap.add_argument("--ms-probes", type=int, default=1024, help="probes timed for the multislice baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp16x2"], default="fp32",
                     help="S-matrix storage / beam-sum arithmetic of the headline line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-cells leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes of the passes")
@@ -407,7 +408,8 @@ def main():
     V = V_host.cuda()
     x0, y0 = w.scan_positions()
     P = len(x0)
-    PREC = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16}
+    PREC = {"fp32": PR.PRISM_PRECISION_FP32, "fp16": PR.PRISM_PRECISION_FP16, "bf16": PR.PRISM_PRECISION_BF16,
+            "fp16x2": PR.PRISM_PRECISION_FP16X2}
     grid = PR.grid_from_workload(w, precision=PREC[args.precision])
     grid32 = PR.grid_from_workload(w)
     det = PR.make_detector(DET["start_mrad"], DET["step_mrad"], DET["nbins"])
@@ -503,7 +505,7 @@ def main():
         prec_leg = {}
         if rank == 0 and not args.no_precision_leg:
             ref_out = out.cpu().numpy().astype(np.float64)
-            for name in ("fp32", "fp16", "bf16"):
+            for name in ("fp32", "fp16", "bf16", "fp16x2"):
                 if name == args.precision:
                     continue
                 s2 = PrismSimulation(PR.grid_from_workload(w, precision=PREC[name]), 0, stream)
@@ -626,7 +628,8 @@ def main():
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16 S / f32 accumulate", "bf16": "bf16 S / f32 accumulate"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16 S / f32 accumulate", "bf16": "bf16 S / f32 accumulate",
+                      "fp16x2": "f16 value + f16 remainder S / f32 accumulate"}[args.precision],
             "data": "synthetic (seeded amorphous-carbon phantom; the paper's Pt/a-C coordinates are not available)",
             "config": {**workload_config(w, Bn), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": world * P * args.steps / (e2e_ms / 1000.0), "unit": UNIT,

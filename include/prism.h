@@ -65,7 +65,11 @@ extern "C" {
  *                PRISM_PRECISION_FP32 (complex64 S, FP32 CUDA-core sum), or
  *                PRISM_PRECISION_FP16 / PRISM_PRECISION_BF16: S stored pixel-major in 16-bit
  *                floats with one power-of-two scale per beam, the beam sum run on the tensor
- *                cores with FP32 accumulation (scan windows of 16, 32 or 64 pixels).  The build
+ *                cores with FP32 accumulation (scan windows of 16, 32 or 64 pixels), or
+ *                PRISM_PRECISION_FP16X2: the same with every S value and coefficient stored as an
+ *                FP16 value plus the FP16 rounding of its remainder and three tensor-core products
+ *                per step (value x value + value x remainder + remainder x value), FP32-class
+ *                accuracy with the storage of FP32.  The build
  *                (transmission, FFTs, propagator) is FP32 in every mode.  Ignored by
  *                multislice_scan_run.  Zero-initialised structs select FP32.
  */
@@ -85,6 +89,7 @@ typedef struct prism_grid {
 #define PRISM_PRECISION_FP32 0
 #define PRISM_PRECISION_FP16 1
 #define PRISM_PRECISION_BF16 2
+#define PRISM_PRECISION_FP16X2 3
 
 /* Probe: aperture semi-angle (A(q) = 1 where lambda|q| <= alpha), defocus C1 and spherical
  * aberration C3 (Angstrom) in chi(q) = pi lambda q^2 C1 + (pi/2) lambda^3 q^4 C3, and tilt
@@ -347,7 +352,8 @@ void prism_batch_destroy(prism_batch *batch);
 int prism_plan_info(const prism_plan *plan, prism_info *out);
 
 /* Bytes of the stored S-matrix: B * nx_s * ny_s * 8 in FP32 mode; nx_s * ny_s * K * 2 + 4 * K / 2
- * (16-bit values, K = 2 * roundup(B, 8), plus the per-beam scales) in FP16/BF16 mode. */
+ * (16-bit values, K = 2 * roundup(B, 8), plus the per-beam scales) in FP16/BF16 mode; twice the
+ * 16-bit part in FP16X2 mode. */
 int prism_plan_smatrix_bytes(const prism_plan *plan, size_t *out);
 
 /* Beam indices (m, n) of the plane-wave set, q_mn = (m f / cell_x, n f / cell_y), in the

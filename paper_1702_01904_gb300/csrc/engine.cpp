@@ -432,6 +432,11 @@ static int grow(DevArena &A, void **p, size_t *cap, size_t need) {
     return PRISM_OK;
 }
 
+// tensor-core scan mode of a 16-bit precision (kernels_tc.cu: 0 FP16, 1 BF16, 2 FP16 value + remainder)
+static int tc_mode(int prec) { return prec == PRISM_PRECISION_BF16 ? 1 : prec == PRISM_PRECISION_FP16X2 ? 2 : 0; }
+// 16-bit rows stored per pixel
+static int tc_parts(int prec) { return prec == PRISM_PRECISION_FP16X2 ? 2 : 1; }
+
 extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes, void *cuda_stream, prism_plan **out) {
     if (!out) return fail(PRISM_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -448,8 +453,9 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     const int nwx = nxs / g.f, nwy = nys / g.f;
     if (nwx != nwy || !scan_supported(nwx))
         return fail(PRISM_ERR_UNSUPPORTED, "scan window must be square with 8, 16, 32, 64 or 128 pixels");
-    if (g.precision != PRISM_PRECISION_FP32 && g.precision != PRISM_PRECISION_FP16 && g.precision != PRISM_PRECISION_BF16)
-        return fail(PRISM_ERR_INVALID, "precision must be PRISM_PRECISION_FP32, _FP16 or _BF16");
+    if (g.precision != PRISM_PRECISION_FP32 && g.precision != PRISM_PRECISION_FP16 && g.precision != PRISM_PRECISION_BF16 &&
+        g.precision != PRISM_PRECISION_FP16X2)
+        return fail(PRISM_ERR_INVALID, "precision must be PRISM_PRECISION_FP32, _FP16, _BF16 or _FP16X2");
     const bool half = g.precision != PRISM_PRECISION_FP32;
     if (half && !scan_tc_supported(nwx))
         return fail(PRISM_ERR_UNSUPPORTED, "16-bit precision needs a scan window of 16, 32 or 64 pixels");
@@ -497,7 +503,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
         return fail(PRISM_ERR_INVALID, "empty beam set");
     }
     P->kp = 2 * ((P->nbeams + 7) / 8 * 8);
-    if (half ? scan_tc_grid(P->nw, P->kp, P->prec == PRISM_PRECISION_BF16, 1, 1) <= 0 : scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
+    if (half ? scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), 1, 1) <= 0 : scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
         delete P;
         return fail(PRISM_ERR_UNSUPPORTED, "too many beams for the scan kernel's shared memory");
     }
@@ -515,7 +521,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     // FP32 mode keeps S for all beams; 16-bit mode keeps the pixel-major 16-bit S plus one FP32
     // beam batch that the quantiser reads
     const size_t sbeam = (size_t)nxs * nys * 8;
-    const size_t s16_bytes = half ? (size_t)nxs * nys * P->kp * 2 + (size_t)P->kp / 2 * sizeof(float) : 0;
+    const size_t s16_bytes = half ? (size_t)nxs * nys * P->kp * 2 * tc_parts(g.precision) + (size_t)P->kp / 2 * sizeof(float) : 0;
     const size_t w_bytes = px * 8;
     const size_t per_beam = w_bytes + (half ? sbeam : 0);
     const size_t fixed = t_bytes + (half ? s16_bytes : (size_t)P->nbeams * sbeam) + (1 << 20);
@@ -546,10 +552,10 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.alloc((void **)&P->t, t_bytes))) return bail(rc);
     if ((rc = A.alloc((void **)&P->S, s_bytes))) return bail(rc);
     if (half) {
-        if ((rc = A.alloc(&P->S16, (size_t)nxs * nys * P->kp * 2))) return bail(rc);
+        if ((rc = A.alloc(&P->S16, (size_t)nxs * nys * P->kp * 2 * tc_parts(P->prec)))) return bail(rc);
         if ((rc = A.alloc((void **)&P->scale, (size_t)P->kp / 2 * sizeof(float)))) return bail(rc);
         // padded beams stay zero in S16 (their coefficients are zero too, and 0 * 0 must not be NaN)
-        CUDA_TRY(cudaMemsetAsync(P->S16, 0, (size_t)nxs * nys * P->kp * 2, P->stream));
+        CUDA_TRY(cudaMemsetAsync(P->S16, 0, (size_t)nxs * nys * P->kp * 2 * tc_parts(P->prec), P->stream));
         CUDA_TRY(cudaMemsetAsync(P->scale, 0, (size_t)P->kp / 2 * sizeof(float), P->stream));
     }
     if ((rc = A.alloc((void **)&P->dev_err, sizeof(int)))) return bail(rc);
@@ -692,7 +698,7 @@ static int build_launches(prism_plan *P, const float *V_dev) {
             q.nb = nb;
             q.npix = P->nxs * P->nys;
             q.kp = P->kp;
-            q.bf16 = P->prec == PRISM_PRECISION_BF16;
+            q.mode = tc_mode(P->prec);
             rc = plan_launch(P, PRISM_K_QUANT, [&] { return launch_quantize(q, P->stream); });
             if (rc) return rc;
         }
@@ -797,7 +803,7 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
 static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
     *grid = 0;
     if (P->prec == PRISM_PRECISION_FP32) return PRISM_OK;
-    *grid = scan_tc_grid(P->nw, P->kp, P->prec == PRISM_PRECISION_BF16, a.scan_px, a.scan_py);
+    *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), a.scan_px, a.scan_py);
     if (*grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
     int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid));
     if (rc) return rc;
@@ -807,8 +813,7 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
 
 static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
     if (P->prec == PRISM_PRECISION_FP32) return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
-    const int bf = P->prec == PRISM_PRECISION_BF16;
-    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, bf, grid, a, P->stream); });
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), grid, a, P->stream); });
 }
 
 static int scan_launch(prism_plan *P, ScanArgs &a) {
@@ -1049,7 +1054,7 @@ extern "C" int prism_plan_info(const prism_plan *P, prism_info *out) {
 extern "C" int prism_plan_smatrix_bytes(const prism_plan *P, size_t *out) {
     if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
     *out = P->prec == PRISM_PRECISION_FP32 ? (size_t)P->nbeams * P->nxs * P->nys * 8
-                                            : (size_t)P->nxs * P->nys * P->kp * 2 + (size_t)P->kp / 2 * sizeof(float);
+                                            : (size_t)P->nxs * P->nys * P->kp * 2 * tc_parts(P->prec) + (size_t)P->kp / 2 * sizeof(float);
     return PRISM_OK;
 }
 
@@ -1065,7 +1070,7 @@ extern "C" int prism_plan_beams(const prism_plan *P, int *m, int *n, int capacit
 
 extern "C" int prism_plan_smatrix(const prism_plan *P, const void **dev_ptr) {
     if (!P || !dev_ptr) return fail(PRISM_ERR_INVALID, "NULL argument");
-    if (P->prec != PRISM_PRECISION_FP32) return fail(PRISM_ERR_INVALID, "S is stored in 16 bits: use prism_plan_smatrix_copy");
+    if (P->prec != PRISM_PRECISION_FP32) return fail(PRISM_ERR_INVALID, "S is stored in 16-bit parts: use prism_plan_smatrix_copy");
     *dev_ptr = P->S;
     return PRISM_OK;
 }
@@ -1081,7 +1086,7 @@ extern "C" int prism_plan_smatrix_copy(prism_plan *P, float *out_dev) {
         return PRISM_OK;
     }
     cudaError_t e = launch_dequantize(P->S16, P->scale, (float2 *)out_dev, P->nbeams, (int)npix, P->kp,
-                                      P->prec == PRISM_PRECISION_BF16, P->stream);
+                                      tc_mode(P->prec), P->stream);
     if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string("dequantize: ") + cudaGetErrorString(e));
     return PRISM_OK;
 }

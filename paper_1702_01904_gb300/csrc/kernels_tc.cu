@@ -93,8 +93,12 @@ cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s) {
 // real-space exit wave is divided by a power-of-two scale (the smallest power of two above its
 // largest |Re| or |Im|, so the division is exact and the values lie in (-1, 1)) and rounded to
 // FP16 or BF16.  The layout is pixel-major: pixel j holds (Re, Im) of beams 0..B-1 at
-// S16[j*kp + 2b], beams B..kp/2-1 are zero.  That row is the K dimension of the tensor-core beam
-// sum.
+// S16[j*K + 2b], beams B..K/2-1 are zero.  That row is the K dimension of the tensor-core beam
+// sum.  Split mode (TC_SPLIT) stores two FP16 rows per pixel, S16[j*2K + 2b] the rounded value hi
+// and S16[j*2K + K + 2b] the rounding of the remainder lo = v - hi, so that hi + lo carries about
+// 22 significant bits.
+
+enum TcMode { TC_FP16 = 0, TC_BF16 = 1, TC_SPLIT = 2 };
 
 template <bool BF>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -115,6 +119,12 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
         const __half2 v = *reinterpret_cast<const __half2 *>(&w);
         return __half22float2(v);
     }
+}
+// (x, y) -> FP16 pair of the values and FP16 pair of their rounding remainders
+__device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t &lo) {
+    hi = pack2<false>(x, y);
+    const float2 h = unpack2<false>(hi);
+    lo = pack2<false>(x - h.x, y - h.y);  // x - h is exact in FP32 (the low bits of x), rounded once
 }
 
 // smallest power of two strictly above x >= 0 (1 for x == 0), from the exponent field
@@ -149,11 +159,12 @@ __global__ void __launch_bounds__(512) k_beam_scale(const QuantArgs a) {
 
 // 32 pixels x 32 beams per tile through shared memory: coalesced reads along pixels of one beam,
 // coalesced 4-byte (Re, Im) writes along the beams of one pixel
-template <bool BF>
+template <int MODE>
 __global__ void __launch_bounds__(256) k_quantize(const QuantArgs a) {
     __shared__ float2 tile[32][33];
     const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int pix0 = blockIdx.x * 32;
+    const size_t row = (size_t)(MODE == TC_SPLIT ? 2 : 1) * a.kp / 2;  // 32-bit words per pixel
     for (int c0 = 0; c0 < a.nb; c0 += 32) {
         for (int j = ty; j < 32; j += 8) {
             const int b = c0 + j;
@@ -167,20 +178,33 @@ __global__ void __launch_bounds__(256) k_quantize(const QuantArgs a) {
             for (int p = ty; p < 32; p += 8) {
                 if (pix0 + p >= a.npix) break;
                 const float2 v = tile[lane][p];
-                dst[((size_t)(pix0 + p) * a.kp) / 2 + a.beam0 + b] = pack2<BF>(v.x * inv, v.y * inv);
+                uint32_t *d = dst + (size_t)(pix0 + p) * row + a.beam0 + b;
+                if constexpr (MODE == TC_SPLIT) {
+                    uint32_t hi, lo;
+                    split2(v.x * inv, v.y * inv, hi, lo);
+                    d[0] = hi;
+                    d[a.kp / 2] = lo;
+                } else {
+                    d[0] = pack2<MODE == TC_BF16>(v.x * inv, v.y * inv);
+                }
             }
         }
         __syncthreads();
     }
 }
 
-template <bool BF>
+template <int MODE>
 __global__ void k_dequantize(const uint32_t *S16, const float *scale, float2 *out, int n_beams, int npix, int kp) {
     const size_t n = (size_t)n_beams * npix;
+    const size_t row = (size_t)(MODE == TC_SPLIT ? 2 : 1) * kp / 2;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / npix);
         const size_t j = i - (size_t)b * npix;
-        const float2 v = unpack2<BF>(S16[(j * kp) / 2 + b]);
+        float2 v = unpack2<MODE == TC_BF16>(S16[j * row + b]);
+        if constexpr (MODE == TC_SPLIT) {
+            const float2 l = unpack2<false>(S16[j * row + kp / 2 + b]);
+            v = make_float2(v.x + l.x, v.y + l.y);
+        }
         out[i] = make_float2(v.x * scale[b], v.y * scale[b]);
     }
 }
@@ -191,22 +215,27 @@ cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int blocks = (a.npix + 31) / 32;
-    if (a.bf16)
-        k_quantize<true><<<blocks, 256, 0, s>>>(a);
-    else
-        k_quantize<false><<<blocks, 256, 0, s>>>(a);
+    switch (a.mode) {
+        case TC_FP16: k_quantize<TC_FP16><<<blocks, 256, 0, s>>>(a); break;
+        case TC_BF16: k_quantize<TC_BF16><<<blocks, 256, 0, s>>>(a); break;
+        case TC_SPLIT: k_quantize<TC_SPLIT><<<blocks, 256, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp, int bf16,
+cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp, int mode,
                               cudaStream_t s) {
     const size_t n = (size_t)n_beams * npix;
     if (n == 0) return cudaSuccess;
     const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-    if (bf16)
-        k_dequantize<true><<<blocks, 256, 0, s>>>((const uint32_t *)S16, scale, out, n_beams, npix, kp);
-    else
-        k_dequantize<false><<<blocks, 256, 0, s>>>((const uint32_t *)S16, scale, out, n_beams, npix, kp);
+    const uint32_t *src = (const uint32_t *)S16;
+    switch (mode) {
+        case TC_FP16: k_dequantize<TC_FP16><<<blocks, 256, 0, s>>>(src, scale, out, n_beams, npix, kp); break;
+        case TC_BF16: k_dequantize<TC_BF16><<<blocks, 256, 0, s>>>(src, scale, out, n_beams, npix, kp); break;
+        case TC_SPLIT: k_dequantize<TC_SPLIT><<<blocks, 256, 0, s>>>(src, scale, out, n_beams, npix, kp); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -222,14 +251,19 @@ cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, 
 // each probe's window pixels to a per-CTA global scratch.  When the group is done the windows come
 // back through shared memory for the window FFT, |.|^2 and the bins (the epilogue of the FP32
 // path).  A group whose union tile is larger than its windows together is run probe by probe.
-template <int NW>
+// Split mode: A and Bc are each a value part and a remainder part (hi, lo) and every K step issues
+// hi*hi + hi*lo + lo*hi into the same FP32 accumulator (the lo*lo term is below FP32 rounding),
+// which carries the products to about 22 significant bits.
+template <int NW, bool SPLIT = false>
 struct TcCfg {
     using FS = FftShape<NW>;
     static constexpr int GX = 8, GY = 4, G = GX * GY, N = 2 * G;
     static constexpr int BLOCK = 256;
-    static constexpr int STAGES = 3;
-    static constexpr int KCMAX = 64;                        // K (16-bit values) per ring stage
-    static constexpr int STAGE_BYTES = 128 * KCMAX * 2;     // 128 pixels x KCMAX
+    static constexpr int PARTS = SPLIT ? 2 : 1;              // hi (and lo) operand parts
+    static constexpr int STAGES = SPLIT ? 2 : 3;
+    static constexpr int KCMAX = SPLIT ? 32 : 64;            // K (16-bit values) per ring stage
+    static constexpr int PART_BYTES = 128 * KCMAX * 2;       // 128 pixels x KCMAX of one part
+    static constexpr int STAGE_BYTES = PARTS * PART_BYTES;
     static constexpr int RING = STAGES * STAGE_BYTES;
     static constexpr int PW = NW + 8;
     static constexpr int EW = NW >= 64 ? 2 : NW == 32 ? 8 : 16;  // windows per epilogue pass
@@ -242,8 +276,9 @@ struct TcCfg {
     static constexpr int META = 256;                        // ints
     static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16;
     static constexpr uint32_t TMEM_COLS = 2 * N;            // two accumulators
+    __host__ __device__ static constexpr size_t bmat_bytes(int kp) { return (size_t)PARTS * kp * N * 2; }
     __host__ __device__ static constexpr size_t region0(int kp) {
-        const size_t r = (size_t)RING + (size_t)kp * N * 2;
+        const size_t r = (size_t)RING + bmat_bytes(kp);
         return ((r > EPI ? r : EPI) + 127) & ~(size_t)127;
     }
     __host__ __device__ static constexpr size_t smem(int kp) { return region0(kp) + MISC; }
@@ -254,9 +289,10 @@ struct TcCfg {
 // probe, [200+e] its probe index
 
 
-template <int NW, bool BF>
+template <int NW, int MODE>
 __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
-    using C = TcCfg<NW>;
+    constexpr bool BF = MODE == TC_BF16, SPLIT = MODE == TC_SPLIT;
+    using C = TcCfg<NW, SPLIT>;
     constexpr int G = C::G, N = C::N, GX = C::GX, GY = C::GY, BLOCK = C::BLOCK, PW = C::PW, S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int kp = a.kp;
@@ -319,8 +355,16 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
             const int k = 2 * b;
             unsigned char *core = bmat + ((k >> 3) * (N / 8)) * 128 + (k & 7) * 2;
             const int n0 = 2 * p, n1 = 2 * p + 1;
-            *reinterpret_cast<uint32_t *>(core + (n0 >> 3) * 128 + (n0 & 7) * 16) = pack2<BF>(ar, -ai);
-            *reinterpret_cast<uint32_t *>(core + (n1 >> 3) * 128 + (n1 & 7) * 16) = pack2<BF>(ai, ar);
+            uint32_t *w0 = reinterpret_cast<uint32_t *>(core + (n0 >> 3) * 128 + (n0 & 7) * 16);
+            uint32_t *w1 = reinterpret_cast<uint32_t *>(core + (n1 >> 3) * 128 + (n1 & 7) * 16);
+            if constexpr (SPLIT) {
+                const size_t lo_off = (size_t)kp * N * 2 / sizeof(uint32_t);  // the remainder matrix
+                split2(ar, -ai, w0[0], w0[lo_off]);
+                split2(ai, ar, w1[0], w1[lo_off]);
+            } else {
+                *w0 = pack2<BF>(ar, -ai);
+                *w1 = pack2<BF>(ai, ar);
+            }
         }
         // group geometry (warp 0, one lane per slot): window origins of Eq. RegionBounds, union tile
         if (warp == 0) {
@@ -385,9 +429,12 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                     if (idx < npx) {
                         const int ty = idx / tw, tx = idx - ty * tw;
                         const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
-                        const uint16_t *src = S16 + gp * kp + k0;
+                        const uint16_t *src = S16 + gp * (C::PARTS * kp) + k0;
                         unsigned char *dst = ring + ((st0 + ls) % S) * C::STAGE_BYTES + (m >> 3) * 128 + (m & 7) * 16;
-                        for (int kc = lane & 1; kc < kn / 8; kc += 2) cp_async16(dst + kc * 2048, src + kc * 8);
+                        for (int kc = lane & 1; kc < kn / 8; kc += 2) {
+                            cp_async16(dst + kc * 2048, src + kc * 8);
+                            if constexpr (SPLIT) cp_async16(dst + C::PART_BYTES + kc * 2048, src + kp + kc * 8);
+                        }
                     }
                 }
                 cp_async_commit();
@@ -415,11 +462,11 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 }
                 tc::fence_before_sync();
             };
-            load(0);
-            load(1);
+#pragma unroll
+            for (int l = 0; l < S - 1; ++l) load(l);
             for (int ls = 0; ls < nsteps; ++ls) {
                 const uint32_t s = st0 + ls;
-                cp_async_wait<1>();
+                cp_async_wait<S - 2>();
                 tc::fence_proxy_async();
                 if (__syncthreads_or(my_fail)) {
                     dead = true;
@@ -431,15 +478,22 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                     const int k0 = c * kcs, kn = min(kcs, kp - k0);
                     const uint32_t abase = tc::smem_u32(ring + (s % S) * C::STAGE_BYTES);
                     for (int j = 0; j < kn / 16; ++j) {
+                        const uint32_t d = tmem + (uint32_t)((mt & 1) * N);
+                        const uint32_t boff = (uint32_t)((k0 / 16 + j) * 2 * (N / 8)) * 128;
                         const uint64_t ad = tc::smem_desc(abase + j * 4096, 2048, 128);
-                        const uint64_t bd = tc::smem_desc(bbase + (uint32_t)((k0 / 16 + j) * 2 * (N / 8)) * 128, (N / 8) * 128, 128);
-                        tc::mma_f16(tmem + (uint32_t)((mt & 1) * N), ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                        const uint64_t bd = tc::smem_desc(bbase + boff, (N / 8) * 128, 128);
+                        tc::mma_f16(d, ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            const uint32_t blo = (uint32_t)((size_t)kp * N * 2);
+                            tc::mma_f16(d, ad, tc::smem_desc(bbase + blo + boff, (N / 8) * 128, 128), idesc, 1u);
+                            tc::mma_f16(d, tc::smem_desc(abase + C::PART_BYTES + j * 4096, 2048, 128), bd, idesc, 1u);
+                        }
                     }
                     tc::mma_commit(&mbar[s % S]);
                 }
-                // ring slot (s + 2) % S was read by step s - 1: wait for its MMAs before refilling it
+                // ring slot (s + S - 1) % S was read by step s - 1: wait for its MMAs before refilling it
                 if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
-                load(ls + 2);
+                load(ls + S - 1);
                 if (c == 0 && mt >= 1) drain(mt - 1);
             }
             st = st0 + nsteps;
@@ -494,13 +548,14 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
 
 bool scan_tc_supported(int nw) { return nw == 16 || nw == 32 || nw == 64; }
 
-template <int NW, bool BF>
+template <int NW, int MODE>
 static int tc_grid(int kp, int scan_px, int scan_py) {
-    using C = TcCfg<NW>;
+    using C = TcCfg<NW, MODE == TC_SPLIT>;
     const size_t smem = C::smem(kp);
     if (smem > 227 * 1024) return 0;
-    if (cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
         return 0;
     // Resident CTAs per SM from the kernel's own limits.  The runtime's occupancy query reports one
     // CTA per SM for every kernel that uses tcgen05, but CTAs whose registers, shared memory and
@@ -508,7 +563,7 @@ static int tc_grid(int kp, int scan_px, int scan_py) {
     // allocation that does not fit waits for another CTA to free its columns).
     cudaFuncAttributes fa;
     int dev = 0, sms = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
-    if (cudaFuncGetAttributes(&fa, k_scan_tc<NW, BF>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+    if (cudaFuncGetAttributes(&fa, k_scan_tc<NW, MODE>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
@@ -523,36 +578,56 @@ static int tc_grid(int kp, int scan_px, int scan_py) {
     return (int)std::max<long long>(1, std::min<long long>(groups, (long long)per_sm * sms));
 }
 
-int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py) {
+template <int NW>
+static int tc_grid_mode(int mode, int kp, int px, int py) {
+    switch (mode) {
+        case TC_FP16: return tc_grid<NW, TC_FP16>(kp, px, py);
+        case TC_BF16: return tc_grid<NW, TC_BF16>(kp, px, py);
+        case TC_SPLIT: return tc_grid<NW, TC_SPLIT>(kp, px, py);
+    }
+    return 0;
+}
+
+int scan_tc_grid(int nw, int kp, int mode, int scan_px, int scan_py) {
     switch (nw) {
-        case 16: return bf16 ? tc_grid<16, true>(kp, scan_px, scan_py) : tc_grid<16, false>(kp, scan_px, scan_py);
-        case 32: return bf16 ? tc_grid<32, true>(kp, scan_px, scan_py) : tc_grid<32, false>(kp, scan_px, scan_py);
-        case 64: return bf16 ? tc_grid<64, true>(kp, scan_px, scan_py) : tc_grid<64, false>(kp, scan_px, scan_py);
+        case 16: return tc_grid_mode<16>(mode, kp, scan_px, scan_py);
+        case 32: return tc_grid_mode<32>(mode, kp, scan_px, scan_py);
+        case 64: return tc_grid_mode<64>(mode, kp, scan_px, scan_py);
         default: return 0;
     }
 }
 
 size_t scan_tc_win_bytes(int nw, int grid) { return (size_t)grid * TcCfg<16>::G * nw * nw * sizeof(float2); }
-static_assert(TcCfg<16>::G == TcCfg<32>::G && TcCfg<16>::G == TcCfg<64>::G, "one group size for every window");
+static_assert(TcCfg<16>::G == TcCfg<32>::G && TcCfg<16>::G == TcCfg<64, true>::G, "one group size for every window");
 
-template <int NW, bool BF>
+template <int NW, int MODE>
 static cudaError_t tc_launch(int grid, const ScanArgs &a, cudaStream_t s) {
-    using C = TcCfg<NW>;
+    using C = TcCfg<NW, MODE == TC_SPLIT>;
     const size_t smem = C::smem(a.kp);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_scan_tc<NW, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_scan_tc<NW, BF><<<grid, C::BLOCK, smem, s>>>(a);
+    k_scan_tc<NW, MODE><<<grid, C::BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_tc(int nw, int bf16, int grid, const ScanArgs &a, cudaStream_t s) {
+template <int NW>
+static cudaError_t tc_launch_mode(int mode, int grid, const ScanArgs &a, cudaStream_t s) {
+    switch (mode) {
+        case TC_FP16: return tc_launch<NW, TC_FP16>(grid, a, s);
+        case TC_BF16: return tc_launch<NW, TC_BF16>(grid, a, s);
+        case TC_SPLIT: return tc_launch<NW, TC_SPLIT>(grid, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scan_tc(int nw, int mode, int grid, const ScanArgs &a, cudaStream_t s) {
     if (grid <= 0 || a.kp % 16 || a.kp < 2 * a.n_beams || !a.S16 || !a.beam_scale || !a.win) return cudaErrorInvalidValue;
     switch (nw) {
-        case 16: return bf16 ? tc_launch<16, true>(grid, a, s) : tc_launch<16, false>(grid, a, s);
-        case 32: return bf16 ? tc_launch<32, true>(grid, a, s) : tc_launch<32, false>(grid, a, s);
-        case 64: return bf16 ? tc_launch<64, true>(grid, a, s) : tc_launch<64, false>(grid, a, s);
+        case 16: return tc_launch_mode<16>(mode, grid, a, s);
+        case 32: return tc_launch_mode<32>(mode, grid, a, s);
+        case 64: return tc_launch_mode<64>(mode, grid, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

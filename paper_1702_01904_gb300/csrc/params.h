@@ -85,6 +85,7 @@ struct ScanArgs {
     int probe0;
     // 16-bit mode (tensor-core beam sum)
     const void *S16;           // [ny_s * nx_s][kp] 16-bit (re, im) of each beam, zero-padded beams
+                               // (split mode: [ny_s * nx_s][2][kp], value row then remainder row)
     const float *beam_scale;   // [B] power of two: S_b = S16_b * beam_scale[b]
     float2 *win;               // window scratch [grid][probes per group][nw][nw]
     int *err;                  // device error word (a bounded wait that ran out sets bit 0)
@@ -99,7 +100,7 @@ struct QuantArgs {
     void *S16;                 // [npix][kp]
     float *scale;              // [B]
     int beam0, nb, npix, kp;
-    int bf16;                  // 0: FP16, 1: BF16
+    int mode;                  // 0: FP16, 1: BF16, 2: FP16 value + FP16 remainder (two rows of kp)
 };
 
 struct ShiftArgs {
@@ -130,12 +131,12 @@ cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);
 // 16-bit mode (kernels_tc.cu)
 cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s);
 cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp,
-                              int bf16, cudaStream_t s);
-cudaError_t launch_scan_tc(int nw, int bf16, int grid, const ScanArgs &a, cudaStream_t s);
+                              int mode, cudaStream_t s);
+cudaError_t launch_scan_tc(int nw, int mode, int grid, const ScanArgs &a, cudaStream_t s);
 bool scan_tc_supported(int nw);
 // persistent grid of the tensor-core scan (resident CTAs, at most the probe groups), 0 if it does
 // not fit; window scratch bytes for that grid
-int scan_tc_grid(int nw, int kp, int bf16, int scan_px, int scan_py);
+int scan_tc_grid(int nw, int kp, int mode, int scan_px, int scan_py);
 size_t scan_tc_win_bytes(int nw, int grid);
 // autotuner launch shapes of ROW_STD (kind 0) and COL_STD (kind 1), N = 256 ... 2048 (kernels_tune.cu)
 int tune_shapes(int kind);

@@ -111,7 +111,9 @@ static size_t plan_bytes_estimate(const prism_grid &g) {
     const double rx = a / (lam * g.f / g.cell_x), ry = a / (lam * g.f / g.cell_y);
     const double beams = 3.15 * (rx + 1) * (ry + 1) + 8;
     const size_t px = (size_t)g.nx * g.ny;
-    const size_t s16 = g.precision != PRISM_PRECISION_FP32 ? (size_t)((beams + 8) * 4 * px / (g.downsample * g.downsample)) : 0;
+    const size_t s16 = g.precision != PRISM_PRECISION_FP32
+                           ? (size_t)((beams + 8) * 4 * px / (g.downsample * g.downsample)) * (g.precision == PRISM_PRECISION_FP16X2 ? 2 : 1)
+                           : 0;
     return (size_t)g.n_slices * px * 8 + (size_t)(beams * px * 8) + (size_t)(beams * px / (g.downsample * g.downsample) * 8) +
            s16 + ((size_t)2 << 20) + (size_t)g.n_slices * px * 4;
 }

@@ -29,6 +29,7 @@ PRISM_K_COUNT = 7
 PRISM_PRECISION_FP32 = 0
 PRISM_PRECISION_FP16 = 1
 PRISM_PRECISION_BF16 = 2
+PRISM_PRECISION_FP16X2 = 3
 
 PRISM_TUNE_ROW = 0
 PRISM_TUNE_COL = 1

@@ -104,10 +104,11 @@ def test_plan_arguments_rejected_before_any_device_call():
         with pytest.raises(P.PrismError) as e:
             P.prism_plan_create(g)
         return e.value.status
-    assert status(precision=3) == P.PRISM_ERR_INVALID
+    assert status(precision=4) == P.PRISM_ERR_INVALID
     assert status(precision=-1) == P.PRISM_ERR_INVALID
     # 16-bit S needs a 16, 32 or 64 pixel window: 64 px / 2 / f=4 is 8
     assert status(precision=P.PRISM_PRECISION_FP16, f=4) == P.PRISM_ERR_UNSUPPORTED
     assert status(precision=P.PRISM_PRECISION_BF16, f=4) == P.PRISM_ERR_UNSUPPORTED
+    assert status(precision=P.PRISM_PRECISION_FP16X2, f=4) == P.PRISM_ERR_UNSUPPORTED
     assert status(nx=100) == P.PRISM_ERR_UNSUPPORTED
     assert status(f=0) == P.PRISM_ERR_INVALID

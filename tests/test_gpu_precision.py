@@ -1,5 +1,6 @@
 """Reduced-precision PRISM on the GPU: S-matrix stored in FP16 or BF16 with one power-of-two scale per
-beam, beam sum of Eq. PRISMfinal on the tcgen05 tensor cores with FP32 accumulation.
+beam, beam sum of Eq. PRISMfinal on the tcgen05 tensor cores with FP32 accumulation; and the split
+mode FP16X2 (value + remainder, three products per step), which is held to the FP32 bars.
 
 Bars.  Stored values: each dequantised S element is within half a unit in the last place of its
 16-bit value of the FP32 S (unit roundoff u = 2^-11 FP16, 2^-8 BF16, relative to the element, plus
@@ -31,11 +32,12 @@ from paper_1702_01904_gb300.runtime import PrismSimulation
 pytestmark = pytest.mark.gpu
 
 DET = dict(start_mrad=0.0, step_mrad=1.0, nbins=100)
-HALF = {"fp16": P.PRISM_PRECISION_FP16, "bf16": P.PRISM_PRECISION_BF16}
-U = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+HALF = {"fp16": P.PRISM_PRECISION_FP16, "bf16": P.PRISM_PRECISION_BF16, "fp16x2": P.PRISM_PRECISION_FP16X2}
+# relative representation bound of a stored value (fp16x2: value + remainder, about 22 bits)
+U = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "fp16x2": 2.0 ** -21}
 # (image mean floor, relative L2 bar) tiers and the absolute bar for images below every floor
 TIERS = {"fp16": ([(1e-3, 2e-3), (1e-5, 1e-2)], 5e-7), "bf16": ([(1e-3, 1e-2)], 2e-5),
-         "fp32": ([(1e-7, 1e-4)], 1e-9)}
+         "fp32": ([(1e-7, 1e-4)], 1e-9), "fp16x2": ([(1e-7, 1e-4)], 1e-9)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,7 +107,7 @@ def report(name, data):
 
 
 # ------------------------------------------------------------------ stored values
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp16x2"])
 def test_dequantised_smatrix_within_half_ulp(prec):
     g = grid_dict(128, 128, 12.8, 12.8, 3, 2.0, 2)
     V = rand_v(3, 128, 128, 21)
@@ -120,11 +122,12 @@ def test_dequantised_smatrix_within_half_ulp(prec):
         a32 = np.stack([S32[b].real, S32[b].imag]).astype(np.float64)
         aq = np.stack([Sq[b].real, Sq[b].imag]).astype(np.float64)
         scale = 2.0 ** (np.floor(np.log2(np.abs(a32).max())) + 1)
-        tiny = scale * (2.0 ** -24 if prec == "fp16" else 2.0 ** -133)
+        tiny = scale * (2.0 ** -133 if prec == "bf16" else 2.0 ** -24)
         assert np.all(np.abs(aq - a32) <= U[prec] * np.abs(a32) + tiny), b
     info = sim.info
     kp = 2 * ((info.n_beams + 7) // 8 * 8)
-    assert P.prism_plan_smatrix_bytes(sim.plan) == info.nx_s * info.ny_s * kp * 2 + kp // 2 * 4
+    parts = 2 if prec == "fp16x2" else 1
+    assert P.prism_plan_smatrix_bytes(sim.plan) == info.nx_s * info.ny_s * kp * 2 * parts + kp // 2 * 4
     with pytest.raises(P.PrismError):
         P.prism_plan_smatrix(sim.plan)
 
@@ -133,17 +136,24 @@ def test_dequantised_smatrix_within_half_ulp(prec):
 CASES = [
     dict(n=64, cell=8.0, H=3, f=2, nw=16),
     dict(n=128, cell=12.8, H=2, f=2, nw=32),
-    dict(n=128, cell=12.8, H=2, f=1, nw=64),
+    dict(n=256, cell=12.8, H=2, f=2, nw=64),
+    dict(n=128, cell=12.8, H=2, f=1, nw=64),   # 529 beams: K = 1072
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"nw{c['nw']}")
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp16x2"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"nw{c['nw']}-f{c['f']}")
 def test_tc_scan_matches_oracle(case, prec):
     n = case["n"]
     g = grid_dict(n, n, case["cell"], case["cell"], case["H"], 2.0, case["f"])
     V = rand_v(case["H"], n, n, 22)
     probe = dict(alpha_mrad=20.0, c1=15.0, c3=2.0e4)
+    if prec == "fp16x2" and case["f"] == 1:
+        # the value and remainder coefficient matrices of 529 beams (2 x 137 KB) exceed shared memory
+        with pytest.raises(P.PrismError) as e:
+            PrismSimulation(c_grid(g, HALF[prec]))
+        assert e.value.status == P.PRISM_ERR_UNSUPPORTED
+        return
     S, m, nn = O.smatrix_build(V, g)
     # (1) scattered, wrapped positions: every group is run probe by probe
     rng = np.random.Generator(np.random.PCG64(23))
@@ -162,7 +172,7 @@ def test_tc_scan_matches_oracle(case, prec):
     sim.close()
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp16x2"])
 def test_tc_small_workload(prec):
     w = specimens.workload_small()
     V = w.potential()
@@ -197,7 +207,8 @@ def test_precision_sweep_nanoparticle(nanoparticle, f, beams, nw):
     w, V, g, x0, y0, ref = nanoparticle(f)
     probe = P.make_probe(w.alpha_mrad)
     rows = {}
-    for prec, code in [("fp32", P.PRISM_PRECISION_FP32), ("fp16", HALF["fp16"]), ("bf16", HALF["bf16"])]:
+    for prec, code in [("fp32", P.PRISM_PRECISION_FP32), ("fp16", HALF["fp16"]), ("bf16", HALF["bf16"]),
+                       ("fp16x2", HALF["fp16x2"])]:
         sim, out = run(g, V, code, probe, x0, y0, w.scan_px, w.scan_py)
         assert sim.info.n_beams == beams and sim.info.nw_x == nw
         check(out, ref, prec)
@@ -219,6 +230,9 @@ def test_tc_carbon_workload_full_size():
     probe = P.make_probe(w.alpha_mrad)
     s32, o32 = run(g, V, P.PRISM_PRECISION_FP32, probe, x0, y0, w.scan_px, w.scan_py)
     s32.close()
+    sx, ox2 = run(g, V, HALF["fp16x2"], probe, x0, y0, w.scan_px, w.scan_py)
+    relx = check(ox2, o32, "fp16x2")
+    sx.close()
     sim, o16 = run(g, V, HALF["fp16"], probe, x0, y0, w.scan_px, w.scan_py)
     rel = check(o16, o32, "fp16")
     # sampled probes against the oracle (one direct multislice of each periodic probe)
@@ -231,7 +245,7 @@ def test_tc_carbon_workload_full_size():
     again = sim.scan(probe, x0, y0, det_c(DET), px=w.scan_px, py=w.scan_py).cpu().numpy()
     assert np.array_equal(again, o16)
     report("carbon_fp16_vs_fp32", dict(workload=w.name, max=float(rel.max()), median=float(np.median(rel)),
-                                       sampled_vs_oracle=float(e)))
+                                       sampled_vs_oracle=float(e), fp16x2_max=float(relx.max())))
     sim.close()
 
 
