@@ -137,20 +137,28 @@ def inside_aperture(qx, qy, lam, alpha_rad):
     return ax * ax + ay * ay <= alpha_rad * alpha_rad * (1.0 + BEAM_SLACK)
 
 
-def beam_set(nx, ny, cell_x, cell_y, kv, f, alpha_mrad):
-    """Plane-wave indices (m, n): q_mn = (m f / cx, n f / cy), sqrt(m^2+n^2) f lambda dq <= alpha_max.
+def interpolation_factors(grid):
+    """(f_x, f_y): the interpolation factor along x and along y (PRISM Algorithm section allows a
+    different factor per axis; "f_y" absent or 0 means f_y = f)."""
+    f = grid["f"]
+    return f, (grid.get("f_y") or f)
 
-    (PRISM Algorithm section, plane-wave set.)  Returns int arrays m, n ordered n-major.
+
+def beam_set(nx, ny, cell_x, cell_y, kv, f, alpha_mrad, f_y=None):
+    """Plane-wave indices (m, n): q_mn = (m f_x / cx, n f_y / cy) with lambda |q_mn| <= alpha_max
+    (PRISM Algorithm section, plane-wave set; f_y = f unless given).  Returns int arrays m, n
+    ordered n-major.
     """
+    fy = f if not f_y else f_y
     lam = wavelength(kv)
     alpha = alpha_mrad * 1e-3
     mmax = int(math.floor(alpha / (lam * f / cell_x))) + 1
-    nmax = int(math.floor(alpha / (lam * f / cell_y))) + 1
+    nmax = int(math.floor(alpha / (lam * fy / cell_y))) + 1
     ms, ns = [], []
     for n in range(-nmax, nmax + 1):
         for m in range(-mmax, mmax + 1):
             qx = float(m * f) / cell_x
-            qy = float(n * f) / cell_y
+            qy = float(n * fy) / cell_y
             if inside_aperture(qx, qy, lam, alpha):
                 ms.append(m)
                 ns.append(n)
@@ -182,14 +190,14 @@ def smatrix_build(v_slices, grid, beams=None):
     Returns (S [B][ny'][nx'] complex128, m, n).
     """
     nx, ny, cx, cy = grid["nx"], grid["ny"], grid["cell_x"], grid["cell_y"]
-    f = grid["f"]
-    m, n = beam_set(nx, ny, cx, cy, grid["kv"], f, grid["alpha_mrad"]) if beams is None else beams
+    f, fy = interpolation_factors(grid)
+    m, n = beam_set(nx, ny, cx, cy, grid["kv"], f, grid["alpha_mrad"], fy) if beams is None else beams
     trans = transmission(v_slices, grid["kv"])
     props = slice_propagators(grid)
     ds = grid.get("downsample", 2)
     out = []
     for b in range(len(m)):
-        psi = plane_wave(nx, ny, cx, cy, float(m[b] * f) / cx, float(n[b] * f) / cy)
+        psi = plane_wave(nx, ny, cx, cy, float(m[b] * f) / cx, float(n[b] * fy) / cy)
         psi = multislice(psi, trans, props)
         out.append(fourier_crop_half(psi) if ds == 2 else psi)
     return np.array(out), m, n
@@ -220,10 +228,10 @@ def probe_coefficients(m, n, grid, probe, x0, y0):
     """alpha_mn(r0) = A(q - q_t) exp(-i chi(q - q_t)) exp(-2 pi i q.(r0 - h tan theta))
     (PRISM Algorithm section, coefficients and tilt)."""
     lam = wavelength(grid["kv"])
-    f = grid["f"]
+    f, fy = interpolation_factors(grid)
     qtx, qty, sx, sy = tilt_terms(grid, probe)
     qx = (m * f).astype(np.float64) / grid["cell_x"]
-    qy = (n * f).astype(np.float64) / grid["cell_y"]
+    qy = (n * fy).astype(np.float64) / grid["cell_y"]
     dqx = qx - qtx
     dqy = qy - qty
     a = inside_aperture(dqx, dqy, lam, probe["alpha_mrad"] * 1e-3)
@@ -268,13 +276,13 @@ def prism_scan(S, m, n, grid, probe, det, x0s, y0s, full_window=False):
     Returns [P][nbins] float64.
     """
     nb, nyd, nxd = S.shape
-    f = grid["f"]
+    f, fy = interpolation_factors(grid)
     if full_window:
         nwx, nwy = nxd, nyd
         bins = window_bins(grid, det, nwx, nwy, (1, grid["cell_x"]), (1, grid["cell_y"]))
     else:
-        nwx, nwy = nxd // f, nyd // f
-        bins = window_bins(grid, det, nwx, nwy, (f, grid["cell_x"]), (f, grid["cell_y"]))
+        nwx, nwy = nxd // f, nyd // fy
+        bins = window_bins(grid, det, nwx, nwy, (f, grid["cell_x"]), (fy, grid["cell_y"]))
     out = np.zeros((len(x0s), det["nbins"]))
     for p in range(len(x0s)):
         a = probe_coefficients(m, n, grid, probe, x0s[p], y0s[p])
@@ -295,8 +303,8 @@ def prism_cbed(S, m, n, grid, probe, x0s, y0s):
     |FFT_Nw(psi)|^2 in units of the incident intensity, window frequencies in FFT order.
     Returns [P][nw_y][nw_x] float64."""
     nb, nyd, nxd = S.shape
-    f = grid["f"]
-    nwx, nwy = nxd // f, nyd // f
+    f, fy = interpolation_factors(grid)
+    nwx, nwy = nxd // f, nyd // fy
     out = np.zeros((len(x0s), nwy, nwx))
     for p in range(len(x0s)):
         a = probe_coefficients(m, n, grid, probe, x0s[p], y0s[p])
@@ -327,23 +335,24 @@ def prism_probe_direct(v_slices, grid, probe, det, x0, y0):
     is one multislice of its d/f-periodic incident wave, stored as the S-matrix would be, then the
     same window, FFT and bins.  Cost: one multislice per probe, usable at any grid size.
     """
-    nx, ny, cx, cy, f = grid["nx"], grid["ny"], grid["cell_x"], grid["cell_y"], grid["f"]
-    m, n = beam_set(nx, ny, cx, cy, grid["kv"], f, grid["alpha_mrad"])
+    nx, ny, cx, cy = grid["nx"], grid["ny"], grid["cell_x"], grid["cell_y"]
+    f, fy = interpolation_factors(grid)
+    m, n = beam_set(nx, ny, cx, cy, grid["kv"], f, grid["alpha_mrad"], fy)
     a = probe_coefficients(m, n, grid, probe, x0, y0)
     psi = np.zeros((ny, nx), dtype=np.complex128)
     for b in range(len(m)):
-        psi += a[b] * plane_wave(nx, ny, cx, cy, float(m[b] * f) / cx, float(n[b] * f) / cy)
+        psi += a[b] * plane_wave(nx, ny, cx, cy, float(m[b] * f) / cx, float(n[b] * fy) / cy)
     psi = multislice(psi, transmission(v_slices, grid["kv"]), slice_propagators(grid))
     if grid.get("downsample", 2) == 2:
         psi = fourier_crop_half(psi)
     nyd, nxd = psi.shape
-    nwx, nwy = nxd // f, nyd // f
+    nwx, nwy = nxd // f, nyd // fy
     sx = window_origin(x0, cx, nxd, nwx)
     sy = window_origin(y0, cy, nyd, nwy)
     win = psi[((sy + np.arange(nwy)) % nyd)[:, None], ((sx + np.arange(nwx)) % nxd)[None, :]]
     norm = float(np.sum(np.abs(a) ** 2))
     inten = np.abs(fft2(win)) ** 2 / ((nwx * nwy) ** 2 * norm)
-    bins = window_bins(grid, det, nwx, nwy, (f, cx), (f, cy))
+    bins = window_bins(grid, det, nwx, nwy, (f, cx), (fy, cy))
     return bin_sum(inten, bins, det["nbins"])
 
 

@@ -476,3 +476,109 @@ def test_frozen_phonon_average():
     S2, _, _ = O.smatrix_build(v2, g)
     mix = O.frozen_phonon_scan([v1, v2], g, PROBE, DET, xs, ys)
     assert np.max(np.abs(mix - 0.5 * (single + O.prism_scan(S2, m, n, g, PROBE, DET, xs, ys)))) < 1e-15
+
+
+# ------------------------------------------------------------------ separate interpolation factors f_x, f_y
+def test_rectangular_beam_lattice_is_the_even_rows_of_the_square_one():
+    # f_y = 2 f: the beams (m, n) with (m f / c)^2 + (2 n f / c)^2 inside the aperture are exactly
+    # the square-lattice beams (m, n') with n' even, n = n' / 2
+    for n_px, cell, f in [(256, 16.0, 4), (512, 32.0, 4), (128, 12.8, 1)]:
+        m, n = O.beam_set(n_px, n_px, cell, cell, 300.0, f, 20.0, 2 * f)
+        ms, ns = O.beam_set(n_px, n_px, cell, cell, 300.0, f, 20.0)
+        want = {(int(a), int(b) // 2) for a, b in zip(ms, ns) if b % 2 == 0}
+        assert set(zip(m.tolist(), n.tolist())) == want and len(m) == len(want)
+    # f_x = 2 f_y: the even columns of the f_y lattice
+    for n_px, cell, fy in [(256, 16.0, 2), (512, 50.0, 4)]:
+        m, n = O.beam_set(n_px, n_px, cell, cell, 300.0, 2 * fy, 20.0, fy)
+        ms, ns = O.beam_set(n_px, n_px, cell, cell, 300.0, fy, 20.0)
+        want = {(int(a) // 2, int(b)) for a, b in zip(ms, ns) if a % 2 == 0}
+        assert set(zip(m.tolist(), n.tolist())) == want and len(m) == len(want)
+
+
+def test_single_slice_rectangular_window_bruteforce():
+    # one slice, dz = 0, f_x = 2, f_y = 4: periodic probe on the (2 dq, 4 dq) lattice, transmit,
+    # anti-aliasing filter, half-resolution grid, a 16 x 8 window by loops, its DFT by loops
+    n, cell, fx, fy = 64, 8.0, 2, 4
+    g = dict(small_grid(n=n, cell=cell, H=1, f=fx, dz=0.0), f_y=fy)
+    v = rand_potential(g, 17)
+    S, m, nb = O.smatrix_build(v, g)
+    lam = O.wavelength(300.0)
+    sig = O.interaction_constant(300.0)
+    x0, y0 = 3.61, 7.7
+    pr = O.prism_scan(S, m, nb, g, PROBE, DET, np.array([x0]), np.array([y0]))[0]
+    xr = np.arange(n) * (cell / n)
+    psi = np.zeros((n, n), complex)
+    norm = 0.0
+    for b in range(len(m)):
+        qx, qy = m[b] * fx / cell, nb[b] * fy / cell
+        c = np.exp(-2j * math.pi * (qx * x0 + qy * y0))
+        norm += abs(c) ** 2
+        psi += c * np.exp(2j * math.pi * (qx * xr[None, :] + qy * xr[:, None]))
+    psi = psi * np.exp(1j * sig * v[0].astype(float))
+    k = O.signed_freq_index(n)
+    spec = np.fft.fft2(psi)
+    half = np.zeros((n // 2, n // 2), complex)
+    for iy in range(n):
+        for ix in range(n):
+            if -n // 4 <= k[iy] < n // 4 and -n // 4 <= k[ix] < n // 4:
+                if (k[ix] / cell) ** 2 + (k[iy] / cell) ** 2 < (0.25 * n / cell) ** 2:
+                    half[k[iy] % (n // 2), k[ix] % (n // 2)] = spec[iy, ix]
+    low = np.fft.ifft2(half) / 4.0
+    nd = n // 2
+    nwx, nwy = nd // fx, nd // fy
+    px = cell / nd
+    sx = int(math.floor(x0 / px + 0.5)) - nwx // 2
+    sy = int(math.floor(y0 / px + 0.5)) - nwy // 2
+    win = np.zeros((nwy, nwx), complex)
+    for v_ in range(nwy):
+        for u in range(nwx):
+            win[v_, u] = low[(sy + v_) % nd, (sx + u) % nd]
+    ref = np.zeros(DET["nbins"])
+    kwx, kwy = O.signed_freq_index(nwx), O.signed_freq_index(nwy)
+    for ky in range(nwy):
+        for kx in range(nwx):
+            s = 0j
+            for v_ in range(nwy):
+                for u in range(nwx):
+                    s += win[v_, u] * np.exp(-2j * math.pi * (kx * u / nwx + ky * v_ / nwy))
+            th = 1000 * lam * math.hypot(kwx[kx] * fx / cell, kwy[ky] * fy / cell)
+            if th < DET["nbins"]:
+                ref[int(th)] += abs(s) ** 2 / ((nwx * nwy) ** 2 * norm)
+    assert np.max(np.abs(pr - ref)) < 1e-12
+
+
+def test_rectangular_crop_off_equals_multislice_of_periodic_probe():
+    g = dict(small_grid(n=64, cell=8.0, H=3, f=1), f_y=2)
+    v = rand_potential(g, 18)
+    S, m, n = O.smatrix_build(v, g)
+    x0, y0 = 5.1, 1.35
+    pr = O.prism_scan(S, m, n, g, PROBE, DET, np.array([x0]), np.array([y0]), full_window=True)[0]
+    a = O.probe_coefficients(m, n, g, PROBE, x0, y0)
+    psi = sum(a[b] * O.plane_wave(64, 64, 8.0, 8.0, m[b] / 8.0, n[b] * 2 / 8.0) for b in range(len(m)))
+    psi = O.multislice(psi, O.transmission(v, 300.0), O.propagator(64, 64, 8.0, 8.0, 300.0, 2.0))
+    inten = np.abs(np.fft.fft2(psi)) ** 2 / (64 ** 4 * np.sum(np.abs(a) ** 2))
+    lam = O.wavelength(300.0)
+    ref = np.zeros(DET["nbins"])
+    k = O.signed_freq_index(64)
+    for iy in range(64):
+        for ix in range(64):
+            th = 1000 * lam * math.hypot(k[ix] / 8.0, k[iy] / 8.0)
+            if th < DET["nbins"]:
+                ref[int(th)] += inten[iy, ix]
+    assert np.max(np.abs(pr - ref)) < 1e-12
+
+
+def test_rectangular_window_empty_sample_one_pixel_per_beam_and_linearity():
+    g = dict(small_grid(n=64, cell=8.0, H=2, f=4), f_y=2)
+    S, m, n = O.smatrix_build(np.zeros((2, 64, 64), np.float32), g)
+    out = O.prism_scan(S, m, n, g, PROBE, DET, np.array([2.2]), np.array([6.9]))[0]
+    lam = O.wavelength(300.0)
+    ref = np.zeros(DET["nbins"])
+    for b in range(len(m)):
+        ref[int(1000 * lam * math.hypot(m[b] * 4 / 8.0, n[b] * 2 / 8.0))] += 1.0 / len(m)
+    assert np.max(np.abs(out - ref)) < 1e-12
+    v = rand_potential(g, 19)
+    S, m, n = O.smatrix_build(v, g)
+    for x0, y0 in [(0.0, 0.0), (6.3, 2.9)]:
+        a = O.prism_scan(S, m, n, g, PROBE, DET, np.array([x0]), np.array([y0]))[0]
+        assert np.max(np.abs(a - O.prism_probe_direct(v, g, PROBE, DET, x0, y0))) < 1e-12
