@@ -72,6 +72,10 @@ extern "C" {
  *                accuracy with the storage of FP32.  The build
  *                (transmission, FFTs, propagator) is FP32 in every mode.  Ignored by
  *                multislice_scan_run.  Zero-initialised structs select FP32.
+ *   f_y          interpolation factor along y when it differs from f (f is then the factor along
+ *                x; the paper allows one per axis): beams q_mn = (m f / cell_x, n f_y / cell_y),
+ *                scan windows of nx_s / f x ny_s / f_y pixels.  0 means f_y = f.  Unequal windows
+ *                need FP32 precision and window sides of 16, 32 or 64 pixels.
  */
 typedef struct prism_grid {
     int nx, ny, n_slices;
@@ -84,6 +88,7 @@ typedef struct prism_grid {
     double aa_frac;
     double alpha_max_mrad;
     int precision;
+    int f_y;
 } prism_grid;
 
 #define PRISM_PRECISION_FP32 0

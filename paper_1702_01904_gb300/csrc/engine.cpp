@@ -263,15 +263,15 @@ static int build_grid_tables(const prism_grid *g, GridTables &T) {
 }
 
 // CSR of pixels grouped by detector bin: bin = floor((1000 lambda |q| - start) / step), q =
-// (k * mult) / cell, pixel index ky * nx + kx in FFT order.
-static void detector_csr(int nx, int ny, double cell_x, double cell_y, int mult, double lam,
+// (k_x mult_x / cell_x, k_y mult_y / cell_y), pixel index ky * nx + kx in FFT order.
+static void detector_csr(int nx, int ny, double cell_x, double cell_y, int mult_x, int mult_y, double lam,
                          const prism_detector *det, std::vector<int> &off, std::vector<int> &idx) {
     std::vector<int> bin((size_t)nx * ny);
     off.assign(det->nbins + 1, 0);
     for (int ky = 0; ky < ny; ++ky) {
-        const double qy = ((double)signed_index(ky, ny) * mult) / cell_y;
+        const double qy = ((double)signed_index(ky, ny) * mult_y) / cell_y;
         for (int kx = 0; kx < nx; ++kx) {
-            const double qx = ((double)signed_index(kx, nx) * mult) / cell_x;
+            const double qx = ((double)signed_index(kx, nx) * mult_x) / cell_x;
             const double theta = 1000.0 * lam * std::sqrt(qx * qx + qy * qy);
             const double bf = std::floor((theta - det->start_mrad) / det->step_mrad);
             int b = -1;
@@ -351,7 +351,7 @@ struct prism_plan {
     GridTables T;
     cudaStream_t stream = nullptr;
     int device = 0;
-    int nxs = 0, nys = 0, nw = 0, nbeams = 0, batch = 0;
+    int nxs = 0, nys = 0, nw = 0, nwy = 0, fy = 1, nbeams = 0, batch = 0;  // nw: window x side
     std::vector<int> bm, bn;
     bool built = false;
     size_t budget = 0;
@@ -370,7 +370,7 @@ struct prism_plan {
     bool tuned[2] = {false, false};
     float2 *prop_x = nullptr, *prop_y = nullptr;
     int *aa_kmax = nullptr;
-    float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr;
+    float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr, *tww_fy = nullptr;
     int *beam_mn = nullptr;
     double *beam_q = nullptr;  // qx[B] then qy[B]
     // grown on demand
@@ -444,19 +444,23 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if (rc) return rc;
     const prism_grid &g = *grid;
     if (g.f < 1) return fail(PRISM_ERR_INVALID, "f must be >= 1");
+    if (g.f_y < 0) return fail(PRISM_ERR_INVALID, "f_y must be >= 0 (0: f_y = f)");
+    const int fy = g.f_y > 0 ? g.f_y : g.f;
     if (g.downsample != 1 && g.downsample != 2) return fail(PRISM_ERR_INVALID, "downsample must be 1 or 2");
     if (g.downsample == 2 && g.aa_frac > 0.5) return fail(PRISM_ERR_INVALID, "downsample 2 needs aa_frac <= 0.5");
     if (!(g.alpha_max_mrad > 0) || !std::isfinite(g.alpha_max_mrad)) return fail(PRISM_ERR_INVALID, "alpha_max_mrad must be positive");
-    if ((g.nx % (g.downsample * g.f)) || (g.ny % (g.downsample * g.f)))
-        return fail(PRISM_ERR_INVALID, "nx and ny must be divisible by downsample * f");
+    if ((g.nx % (g.downsample * g.f)) || (g.ny % (g.downsample * fy)))
+        return fail(PRISM_ERR_INVALID, "nx must be divisible by downsample * f and ny by downsample * f_y");
     const int nxs = g.nx / g.downsample, nys = g.ny / g.downsample;
-    const int nwx = nxs / g.f, nwy = nys / g.f;
-    if (nwx != nwy || !scan_supported(nwx))
-        return fail(PRISM_ERR_UNSUPPORTED, "scan window must be square with 8, 16, 32, 64 or 128 pixels");
+    const int nwx = nxs / g.f, nwy = nys / fy;
+    const auto side_ok = [](int n) { return n == 16 || n == 32 || n == 64; };
+    if (nwx == nwy ? !scan_supported(nwx) : !(side_ok(nwx) && side_ok(nwy)))
+        return fail(PRISM_ERR_UNSUPPORTED, "scan window must be square with 8, 16, 32, 64 or 128 pixels, or have sides of 16, 32 or 64");
     if (g.precision != PRISM_PRECISION_FP32 && g.precision != PRISM_PRECISION_FP16 && g.precision != PRISM_PRECISION_BF16 &&
         g.precision != PRISM_PRECISION_FP16X2)
         return fail(PRISM_ERR_INVALID, "precision must be PRISM_PRECISION_FP32, _FP16, _BF16 or _FP16X2");
     const bool half = g.precision != PRISM_PRECISION_FP32;
+    if (half && nwx != nwy) return fail(PRISM_ERR_UNSUPPORTED, "16-bit precision needs a square scan window (f_y = f on a square grid)");
     if (half && !scan_tc_supported(nwx))
         return fail(PRISM_ERR_UNSUPPORTED, "16-bit precision needs a scan window of 16, 32 or 64 pixels");
 
@@ -472,6 +476,8 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     P->nxs = nxs;
     P->nys = nys;
     P->nw = nwx;
+    P->nwy = nwy;
+    P->fy = fy;
     P->prec = g.precision;
     rc = build_grid_tables(&g, P->T);
     if (rc) {
@@ -482,12 +488,12 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     const double lam = P->T.lam;
     const double alpha = g.alpha_max_mrad * 1e-3;
     const int mmax = (int)std::floor(alpha / (lam * g.f / g.cell_x)) + 1;
-    const int nmax = (int)std::floor(alpha / (lam * g.f / g.cell_y)) + 1;
+    const int nmax = (int)std::floor(alpha / (lam * fy / g.cell_y)) + 1;
     std::vector<double> bq;
     for (int n = -nmax; n <= nmax; ++n)
         for (int m = -mmax; m <= mmax; ++m) {
             const double qx = (double)(m * g.f) / g.cell_x;
-            const double qy = (double)(n * g.f) / g.cell_y;
+            const double qy = (double)(n * fy) / g.cell_y;
             if (inside_aperture(qx, qy, lam, alpha)) {
                 if (!(qx * qx + qy * qy < P->T.q_aa * P->T.q_aa)) {
                     delete P;
@@ -503,7 +509,8 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
         return fail(PRISM_ERR_INVALID, "empty beam set");
     }
     P->kp = 2 * ((P->nbeams + 7) / 8 * 8);
-    if (half ? scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), 1, 1) <= 0 : scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024) {
+    if (half ? scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), 1, 1) <= 0
+             : nwx == nwy ? scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024 : !scan_rect_supported(nwx, nwy, P->nbeams)) {
         delete P;
         return fail(PRISM_ERR_UNSUPPORTED, "too many beams for the scan kernel's shared memory");
     }
@@ -513,7 +520,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
         mn[2 * b] = P->bm[b];
         mn[2 * b + 1] = P->bn[b];
         q[b] = (double)(P->bm[b] * g.f) / g.cell_x;
-        q[P->nbeams + b] = (double)(P->bn[b] * g.f) / g.cell_y;
+        q[P->nbeams + b] = (double)(P->bn[b] * fy) / g.cell_y;
     }
     // memory plan
     const size_t px = (size_t)g.nx * g.ny;
@@ -536,11 +543,13 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     P->batch = batch;
     const size_t s_bytes = (half ? (size_t)batch : (size_t)P->nbeams) * sbeam;
     P->tw64 = make_tw64();
-    std::vector<float2> tww_f;
+    std::vector<float2> tww_f, tww_fy;
     {
         int a1, a2;
         fft_split(P->nw, &a1, &a2);
         tww_f = stage_table(P->nw, a1, a2);
+        fft_split(P->nwy, &a1, &a2);
+        tww_fy = stage_table(P->nwy, a1, a2);
     }
     DevArena &A = P->arena;
     auto bail = [&](int code) {
@@ -569,6 +578,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.upload(&P->twc_f, P->T.twc_f))) return bail(rc);
     if ((rc = A.upload(&P->twc_i, P->T.twc_i))) return bail(rc);
     if ((rc = A.upload(&P->tww_f, tww_f))) return bail(rc);
+    if ((rc = A.upload(&P->tww_fy, tww_fy))) return bail(rc);
     if ((rc = A.upload(&P->beam_mn, mn))) return bail(rc);
     if ((rc = A.upload(&P->beam_q, q))) return bail(rc);
     if ((rc = A.alloc((void **)&P->base, (size_t)P->nbeams * sizeof(float2)))) return bail(rc);
@@ -619,6 +629,7 @@ static RowArgs row_args(prism_plan *P) {
     a.beam_mn = P->beam_mn;
     a.ny = P->g.ny;
     a.f = P->g.f;
+    a.f_y = P->fy;
     a.downsample = P->g.downsample;
     a.kx_half = P->T.kx_half;
     a.tw = P->tw64;
@@ -734,7 +745,7 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     double count = 0;
     for (int b = 0; b < B; ++b) {
         const double qx = (double)(P->bm[b] * P->g.f) / P->g.cell_x;
-        const double qy = (double)(P->bn[b] * P->g.f) / P->g.cell_y;
+        const double qy = (double)(P->bn[b] * P->fy) / P->g.cell_y;
         const double dqx = qx - tl.qtx;
         const double dqy = qy - tl.qty;
         if (inside_aperture(dqx, dqy, lam, probe->alpha_mrad * 1e-3)) {
@@ -757,7 +768,7 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     // window bin map (q = k f / cell on the window grid), cached per detector
     if (det && (P->det_nbins != det->nbins || P->det_key[0] != det->start_mrad || P->det_key[1] != det->step_mrad)) {
         std::vector<int> off, idx;
-        detector_csr(P->nw, P->nw, P->g.cell_x, P->g.cell_y, P->g.f, lam, det, off, idx);
+        detector_csr(P->nw, P->nwy, P->g.cell_x, P->g.cell_y, P->g.f, P->fy, lam, det, off, idx);
         std::vector<int> all(off);
         all.insert(all.end(), idx.begin(), idx.end());
         if ((rc = grow(P->arena, (void **)&P->bin_buf, &P->bin_cap, all.size() * sizeof(int)))) return rc;
@@ -774,13 +785,14 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     a.qy = P->beam_q + B;
     a.base = P->base;
     a.tw_fwd = P->tww_f;
+    a.tw_fwd_y = P->tww_fy;
     a.bin_off = det ? P->bin_buf : nullptr;
     a.bin_idx = det ? P->bin_buf + det->nbins + 1 : nullptr;
     a.px_s = pxs;
     a.py_s = pys;
     a.shift_x = tl.sx;
     a.shift_y = tl.sy;
-    const double nw2 = (double)P->nw * (double)P->nw;
+    const double nw2 = (double)P->nw * (double)P->nwy;
     a.inv_norm = count > 0 ? 1.0 / (nw2 * nw2 * count) : 0.0;
     a.n_beams = B;
     a.nx_s = P->nxs;
@@ -812,7 +824,8 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
 }
 
 static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
-    if (P->prec == PRISM_PRECISION_FP32) return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan(P->nw, a, P->stream); });
+    if (P->prec == PRISM_PRECISION_FP32)
+        return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_rect(P->nw, P->nwy, a, P->stream); });
     return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), grid, a, P->stream); });
 }
 
@@ -928,7 +941,7 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             }
         }
     std::vector<int> off, idx;
-    detector_csr(nx, ny, g.cell_x, g.cell_y, 1, T.lam, det, off, idx);
+    detector_csr(nx, ny, g.cell_x, g.cell_y, 1, 1, T.lam, det, off, idx);
     if (scratch_bytes == 0) scratch_bytes = (size_t)1 << 30;
     const int Pb = (int)std::max<long long>(1, std::min<long long>(Pn, (long long)(scratch_bytes / (px * 8))));
     const Tw64 tw = make_tw64();
@@ -1043,7 +1056,7 @@ extern "C" int prism_plan_info(const prism_plan *P, prism_info *out) {
     out->nx_s = P->nxs;
     out->ny_s = P->nys;
     out->nw_x = P->nw;
-    out->nw_y = P->nw;
+    out->nw_y = P->nwy;
     out->beam_batch = P->batch;
     out->wavelength = P->T.lam;
     out->sigma = P->T.sigma;
@@ -1205,7 +1218,7 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
             }
         }
     }
-    detector_csr(g.nx, g.ny, g.cell_x, g.cell_y, 1, T.lam, det, M.bin_off, M.bin_idx);
+    detector_csr(g.nx, g.ny, g.cell_x, g.cell_y, 1, 1, T.lam, det, M.bin_off, M.bin_idx);
     const long long Pn = (long long)sc->px * sc->py;
     M.pos.resize((size_t)Pn * 2);
     for (long long i = 0; i < Pn; ++i) {
@@ -1391,7 +1404,7 @@ extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t h
         bytes += P->arena.bytes;
         const double px = (double)c.grid.nx * c.grid.ny;
         cost[i] = (double)P->nbeams * c.grid.n_slices * px * 32.0 +
-                  (double)a.n_probes * P->nbeams * P->nw * P->nw * (P->prec == PRISM_PRECISION_FP32 ? 8.0 : 1.0);
+                  (double)a.n_probes * P->nbeams * P->nw * P->nwy * (P->prec == PRISM_PRECISION_FP32 ? 8.0 : 1.0);
     }
     if (hbm_budget_bytes && bytes > hbm_budget_bytes)
         return fail(PRISM_ERR_BUDGET, "batch needs " + std::to_string(bytes) + " bytes, budget " + std::to_string(hbm_budget_bytes)), bail(PRISM_ERR_BUDGET);

@@ -173,44 +173,41 @@ static cudaError_t scan_dispatch(const ScanArgs &a, cudaStream_t s) {
 // flight while one is summed) and every thread owns tile pixels, so one shared-memory load feeds
 // the complex MACs of all G probes.  A group whose windows do not fit the tile is processed one
 // probe at a time.
-template <int NW>
+template <int NWX, int NWY>
 struct GroupCfg {
-    using FS = FftShape<NW>;
+    static constexpr int NWM = NWX > NWY ? NWX : NWY;
     static constexpr int G = 4;
     static constexpr int D = 16;                              // tile may exceed a window by D pixels
-    static constexpr int BLOCK = NW >= 64 ? 512 : NW >= 16 ? 256 : 64;
-    static constexpr int MAXTILE = NW * (NW + D);             // tile pixels
+    static constexpr int BLOCK = NWM >= 64 ? 512 : NWM >= 16 ? 256 : 64;
+    static constexpr int MAXTILE = (NWX + D) * NWY;           // tile pixels
     static constexpr int PIX = (MAXTILE + BLOCK - 1) / BLOCK; // tile pixels per thread
     static constexpr int PAIRS = (MAXTILE / 2 + BLOCK - 1) / BLOCK;  // 16-byte copies per thread
-    static constexpr int PW = NW + 8;                         // window row pitch (bank spread)
-    static constexpr int T = FS::T;
-    static constexpr int RSLOTS = BLOCK / T;
-    static constexpr int CW = BLOCK / T;
-    static constexpr int EXR = RSLOTS * FS::N1 * (FS::N2 + 1);
-    static constexpr int EXC = FS::N1 * (FS::N2 + 1) * CW;
-    static constexpr int EX = EXR > EXC ? EXR : EXC;
+    static constexpr int PW = NWX + 8;                        // window row pitch (bank spread)
+    static constexpr int EX = ExSize<NWX, NWY, BLOCK>::value;
     static constexpr int STAGES = 4;                          // cp.async pipeline depth (beams in flight)
-    static constexpr int BIG = (STAGES * MAXTILE > G * NW * PW) ? STAGES * MAXTILE : G * NW * PW;
-    static constexpr size_t SMEM_FIXED = (size_t)(BIG + EX + NW) * sizeof(float2) + 64 * sizeof(int);
+    static constexpr int BIG = (STAGES * MAXTILE > G * NWY * PW) ? STAGES * MAXTILE : G * NWY * PW;
+    static constexpr size_t SMEM_FIXED = (size_t)(BIG + EX + NWX + NWY) * sizeof(float2) + 64 * sizeof(int);
 };
 
-template <int NW>
-__global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __grid_constant__ ScanArgs a) {
-    using C = GroupCfg<NW>;
+template <int NWX, int NWY>
+__global__ void __launch_bounds__(GroupCfg<NWX, NWY>::BLOCK) k_scan_grouped(const __grid_constant__ ScanArgs a) {
+    using C = GroupCfg<NWX, NWY>;
     constexpr int BLOCK = C::BLOCK, PIX = C::PIX, G = C::G, PW = C::PW;
     extern __shared__ float2 smem[];
-    float2 *big = smem;                    // staging tiles [STAGES][MAXTILE], later windows [G][NW][PW]
+    float2 *big = smem;                    // staging tiles [STAGES][MAXTILE], later windows [G][NWY][PW]
     float2 *ex = big + C::BIG;             // FFT exchange
-    float2 *twf = ex + C::EX;              // window FFT stage twiddles [NW]
-    int *meta = reinterpret_cast<int *>(twf + NW);  // group geometry
+    float2 *twx = ex + C::EX;              // window FFT stage twiddles, rows [NWX] and columns [NWY]
+    float2 *twy = twx + NWX;
+    int *meta = reinterpret_cast<int *>(twy + NWY);  // group geometry
     float2 *alpha = reinterpret_cast<float2 *>(meta + 64);  // [G][n_beams]
     const int tid = threadIdx.x;
     const int p0 = a.probe0 + blockIdx.x * G;
     if (p0 >= a.n_probes) return;
     const int gn = min(G, a.n_probes - p0);
-    for (int i = tid; i < NW; i += BLOCK) twf[i] = a.tw_fwd[i];
+    for (int i = tid; i < NWX; i += BLOCK) twx[i] = a.tw_fwd[i];
+    for (int i = tid; i < NWY; i += BLOCK) twy[i] = a.tw_fwd_y[i];
     group_coefficients<G>(a, p0, gn, alpha, tid, BLOCK);
-    if (tid == 0) group_geometry<NW, G, C::D, C::MAXTILE>(a, p0, gn, meta);
+    if (tid == 0) group_geometry<NWX, NWY, G, C::D, C::MAXTILE>(a, p0, gn, meta);
     __syncthreads();
     const int nsub = meta[0];
     const size_t bstride = (size_t)a.ny_s * a.nx_s;
@@ -227,8 +224,8 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
             ty0 = meta[4];
         } else {
             ox1 = meta[8 + sg] & 1;
-            tw = NW + 2 * ox1;
-            th = NW;
+            tw = NWX + 2 * ox1;
+            th = NWY;
             tx0 = meta[8 + sg] - ox1;
             ty0 = meta[16 + sg];
         }
@@ -296,38 +293,69 @@ __global__ void __launch_bounds__(GroupCfg<NW>::BLOCK) k_scan_grouped(const __gr
             for (int p = 0; p < G; ++p) {
                 const bool act = all ? p < gn : p == 0;
                 const int wy = ty - (all ? meta[32 + p] : 0), wx = tx - (all ? meta[24 + p] : ox1);
-                if (act && i < npx && wy >= 0 && wy < NW && wx >= 0 && wx < NW) win[(p * NW + wy) * PW + wx] = acc[k][p];
+                if (act && i < npx && wy >= 0 && wy < NWY && wx >= 0 && wx < NWX) win[(p * NWY + wy) * PW + wx] = acc[k][p];
             }
         }
         __syncthreads();
-        window_epilogue<NW, BLOCK, G, PW>(a, win, ex, twf, all ? gn : 1, meta + 40 + (all ? 0 : sg), tid);
+        window_epilogue<NWX, NWY, BLOCK, G, PW>(a, win, ex, twx, twy, all ? gn : 1, meta + 40 + (all ? 0 : sg), tid);
         __syncthreads();  // windows and staging buffers are reused by the next sub-group
     }
 }
 
-template <int NW>
+template <int NWX, int NWY>
 static cudaError_t scan_grouped_dispatch(const ScanArgs &a, cudaStream_t s) {
-    using C = GroupCfg<NW>;
+    using C = GroupCfg<NWX, NWY>;
     const int n = a.n_probes - a.probe0;
     if (n <= 0) return cudaSuccess;
     const size_t smem = C::SMEM_FIXED + (size_t)C::G * a.n_beams * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_grouped<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_scan_grouped<NWX, NWY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_scan_grouped<NW><<<(n + C::G - 1) / C::G, C::BLOCK, smem, s>>>(a);
+    k_scan_grouped<NWX, NWY><<<(n + C::G - 1) / C::G, C::BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NW>
+template <int NWX, int NWY>
 static bool grouped_fits(int n_beams) {
-    return GroupCfg<NW>::SMEM_FIXED + (size_t)GroupCfg<NW>::G * n_beams * sizeof(float2) <= 227 * 1024;
+    return GroupCfg<NWX, NWY>::SMEM_FIXED + (size_t)GroupCfg<NWX, NWY>::G * n_beams * sizeof(float2) <= 227 * 1024;
+}
+
+// rectangular windows (separate interpolation factors f_x != f_y): grouped kernel only
+template <int NWX>
+static cudaError_t scan_rect_y(int nwy, const ScanArgs &a, cudaStream_t s) {
+    switch (nwy) {
+        case 16: return NWX != 16 && grouped_fits<NWX, 16>(a.n_beams) ? scan_grouped_dispatch<NWX, 16>(a, s) : cudaErrorInvalidValue;
+        case 32: return NWX != 32 && grouped_fits<NWX, 32>(a.n_beams) ? scan_grouped_dispatch<NWX, 32>(a, s) : cudaErrorInvalidValue;
+        case 64: return NWX != 64 && grouped_fits<NWX, 64>(a.n_beams) ? scan_grouped_dispatch<NWX, 64>(a, s) : cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scan_rect(int nwx, int nwy, const ScanArgs &a, cudaStream_t s) {
+    if (nwx == nwy) return launch_scan(nwx, a, s);
+    switch (nwx) {
+        case 16: return scan_rect_y<16>(nwy, a, s);
+        case 32: return scan_rect_y<32>(nwy, a, s);
+        case 64: return scan_rect_y<64>(nwy, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool scan_rect_supported(int nwx, int nwy, int n_beams) {
+    if (nwx == nwy) return scan_supported(nwx);
+    auto in = [](int n) { return n == 16 || n == 32 || n == 64; };
+    if (!in(nwx) || !in(nwy)) return false;
+    const size_t fixed = (nwx == 16 ? (nwy == 32 ? GroupCfg<16, 32>::SMEM_FIXED : GroupCfg<16, 64>::SMEM_FIXED)
+                          : nwx == 32 ? (nwy == 16 ? GroupCfg<32, 16>::SMEM_FIXED : GroupCfg<32, 64>::SMEM_FIXED)
+                                      : (nwy == 16 ? GroupCfg<64, 16>::SMEM_FIXED : GroupCfg<64, 32>::SMEM_FIXED));
+    return fixed + (size_t)4 * n_beams * sizeof(float2) <= 227 * 1024;
 }
 
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s) {
     switch (nw) {
-        case 8: return grouped_fits<8>(a.n_beams) ? scan_grouped_dispatch<8>(a, s) : scan_dispatch<8>(a, s);
-        case 16: return grouped_fits<16>(a.n_beams) ? scan_grouped_dispatch<16>(a, s) : scan_dispatch<16>(a, s);
-        case 32: return grouped_fits<32>(a.n_beams) ? scan_grouped_dispatch<32>(a, s) : scan_dispatch<32>(a, s);
-        case 64: return grouped_fits<64>(a.n_beams) ? scan_grouped_dispatch<64>(a, s) : scan_dispatch<64>(a, s);
+        case 8: return grouped_fits<8, 8>(a.n_beams) ? scan_grouped_dispatch<8, 8>(a, s) : scan_dispatch<8>(a, s);
+        case 16: return grouped_fits<16, 16>(a.n_beams) ? scan_grouped_dispatch<16, 16>(a, s) : scan_dispatch<16>(a, s);
+        case 32: return grouped_fits<32, 32>(a.n_beams) ? scan_grouped_dispatch<32, 32>(a, s) : scan_dispatch<32>(a, s);
+        case 64: return grouped_fits<64, 64>(a.n_beams) ? scan_grouped_dispatch<64, 64>(a, s) : scan_dispatch<64>(a, s);
         case 128: return scan_dispatch<128>(a, s);
         default: return cudaErrorInvalidValue;
     }

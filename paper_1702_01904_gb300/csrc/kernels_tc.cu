@@ -533,7 +533,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 }
             }
             __syncthreads();
-            window_epilogue<NW, BLOCK, C::EW, PW>(a, win, ex, twf, ne, meta + 200 + e0, tid);
+            window_epilogue<NW, NW, BLOCK, C::EW, PW>(a, win, ex, twf, twf, ne, meta + 200 + e0, tid);
             __syncthreads();
         }
     }

@@ -26,7 +26,8 @@ struct RowArgs {
     const int *beam_mn;        // PLANE: [B][2] (m, n)
     int ny;
     int n_rows;                // rows processed by this launch
-    int f;                     // PLANE
+    int f;                     // PLANE: interpolation factor along x
+    int f_y;                   // PLANE: interpolation factor along y
     int beam0;                 // first beam of this batch (PLANE, OUT)
     int downsample;            // OUT
     int kx_half;               // > 0: only kx = -(kx_half-1) ... kx_half-1 of the mixed-domain wave are
@@ -67,7 +68,8 @@ struct ScanArgs {
     const double *qx;          // [B] beam qx = m f / cell_x
     const double *qy;          // [B]
     const float2 *base;        // [B] A(q_b) exp(-i chi(q_b))
-    const float2 *tw_fwd;      // window FFT inter-stage twiddles
+    const float2 *tw_fwd;      // window FFT inter-stage twiddles (rows, length nw_x)
+    const float2 *tw_fwd_y;    // window FFT inter-stage twiddles (columns, length nw_y)
     const float2 *tw_inv;      // (unused by the forward-only window FFT; kept for symmetry)
     const int *bin_off;        // [nbins+1] CSR offsets into bin_idx
     const int *bin_idx;        // window pixel indices (ky*nw + kx) grouped by bin
@@ -125,6 +127,10 @@ cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigm
 cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s);
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
+// nw_x x nw_y windows (separate f_x, f_y): square ones as launch_scan, rectangular ones (16, 32, 64
+// per side) through the grouped kernel; scan_rect_supported says whether a launch can succeed
+cudaError_t launch_scan_rect(int nwx, int nwy, const ScanArgs &a, cudaStream_t s);
+bool scan_rect_supported(int nwx, int nwy, int n_beams);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
 cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
             const int m = a.beam_mn[2 * (a.beam0 + b)];
             const int n = a.beam_mn[2 * (a.beam0 + b) + 1];
             const long long den = (long long)NX * a.ny;
-            long long ky = ((long long)n * a.f * y) % a.ny;
+            long long ky = ((long long)n * a.f_y * y) % a.ny;
             if (ky < 0) ky += a.ny;
             const long long yterm = ky * NX;
             const float inv_den = 1.0f / (float)den;  // den is a power of two: exact

@@ -30,18 +30,18 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Geometry of a group of up to G consecutive probes (thread 0 only).  Window origins follow
-// Eq. RegionBounds in FP64; the union tile of the group's windows, relative to probe 0, starts on
-// an even column with an even width (16-byte aligned pixel pairs).  meta layout:
+// Geometry of a group of up to G consecutive probes (thread 0 only), NWX x NWY windows.  Window
+// origins follow Eq. RegionBounds in FP64; the union tile of the group's windows, relative to probe
+// 0, starts on an even column with an even width (16-byte aligned pixel pairs).  meta layout:
 //   [0] sub-groups (1: whole group on one tile, else one per probe)  [1] tile width  [2] tile height
 //   [3] tile x origin  [4] tile y origin  [8+p] window x origin  [16+p] window y origin
 //   [24+p] window x offset in the tile  [32+p] window y offset in the tile  [40+p] output row (p0 + p)
-template <int NW, int G, int D, int MAXTILE>
+template <int NWX, int NWY, int G, int D, int MAXTILE>
 __device__ void group_geometry(const ScanArgs &a, int p0, int gn, int *meta) {
     int sx[G], sy[G];
     for (int p = 0; p < gn; ++p) {
-        sx[p] = ((int)floor(a.x0[p0 + p] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
-        sy[p] = ((int)floor(a.y0[p0 + p] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
+        sx[p] = ((int)floor(a.x0[p0 + p] / a.px_s + 0.5) - NWX / 2) & (a.nx_s - 1);
+        sy[p] = ((int)floor(a.y0[p0 + p] / a.py_s + 0.5) - NWY / 2) & (a.ny_s - 1);
     }
     int dxmin = 0, dxmax = 0, dymin = 0, dymax = 0, dx[G], dy[G];
     for (int p = 0; p < gn; ++p) {
@@ -54,9 +54,9 @@ __device__ void group_geometry(const ScanArgs &a, int p0, int gn, int *meta) {
     }
     const int tx0 = (sx[0] + dxmin) & (a.nx_s - 1);
     const int shift = tx0 & 1;  // extra leading column to reach an even origin
-    const int tw = (dxmax - dxmin + NW + shift + 1) & ~1;
-    const int th = dymax - dymin + NW;
-    const bool fits = tw <= NW + D && th <= NW + D && tw * th <= MAXTILE;
+    const int tw = (dxmax - dxmin + NWX + shift + 1) & ~1;
+    const int th = dymax - dymin + NWY;
+    const bool fits = tw <= NWX + D && th <= NWY + D && tw * th <= MAXTILE;
     meta[0] = fits ? 1 : gn;
     for (int p = 0; p < G; ++p) {
         meta[8 + p] = sx[p < gn ? p : 0];
@@ -89,29 +89,38 @@ __device__ void group_coefficients(const ScanArgs &a, int p0, int gn, float2 *al
     }
 }
 
-// Window epilogue for nwin windows win[p][NW][PW] (psi in real space on entry): 2-D FFT of every
-// window (rows then columns, two-level FFTs), then the full diffraction pattern (if a.cbed) and
-// the annular bins (if a.out).
-// Window p is written to output row oidx[p] (shared memory).  G bounds nwin.
-template <int NW, int BLOCK, int G, int PW>
-__device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, const float2 *twf, int nwin,
-                                const int *oidx, int tid) {
-    using FS = FftShape<NW>;
-    using Fwd = FwdFft<NW>;
-    constexpr int T = FS::T, E = FS::E;
-    constexpr int RSLOTS = BLOCK / T, CW = BLOCK / T;
+// Window epilogue for nwin windows win[p][NWY][PW] (psi in real space on entry, NWX pixels per
+// row): 2-D FFT of every window (rows then columns, two-level FFTs; the stage twiddles of the row
+// and column lengths in twx and twy), then the full diffraction pattern (if a.cbed) and the
+// annular bins (if a.out).  Window p is written to output row oidx[p] (shared memory).  G bounds
+// nwin; ex holds ExSize<NWX, NWY, BLOCK>::value float2.
+template <int NWX, int NWY, int BLOCK>
+struct ExSize {
+    using FX = FftShape<NWX>;
+    using FY = FftShape<NWY>;
+    static constexpr int EXR = (BLOCK / FX::T) * FX::N1 * (FX::N2 + 1);
+    static constexpr int EXC = FY::N1 * (FY::N2 + 1) * (BLOCK / FY::T);
+    static constexpr int value = EXR > EXC ? EXR : EXC;
+};
+
+template <int NWX, int NWY, int BLOCK, int G, int PW>
+__device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, const float2 *twx, const float2 *twy,
+                                int nwin, const int *oidx, int tid) {
     {
+        using FS = FftShape<NWX>;
+        using Fwd = FwdFft<NWX>;
+        constexpr int T = FS::T, E = FS::E, RSLOTS = BLOCK / T;
         const int slot = tid / T, t = tid % T;
         WarpExchange<FS::N1, FS::N2, T> exr{ex + slot * (FS::N1 * (FS::N2 + 1))};
 #pragma unroll 1
-        for (int r0 = 0; r0 < G * NW; r0 += RSLOTS) {
+        for (int r0 = 0; r0 < G * NWY; r0 += RSLOTS) {
             const int row = r0 + slot;
-            const bool ok = row < nwin * NW;
-            const int rr = ok ? row : row % NW;
+            const bool ok = row < nwin * NWY;
+            const int rr = ok ? row : row % NWY;
             float2 v[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = win[rr * PW + Fwd::in_elem(r, t)];
-            Fwd::run(v, t, twf, a.tw, exr);
+            Fwd::run(v, t, twx, a.tw, exr);
             if (ok) {
 #pragma unroll
                 for (int r = 0; r < E; ++r) win[rr * PW + Fwd::out_elem(r, t)] = v[r];
@@ -120,19 +129,22 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
     }
     __syncthreads();
     {
+        using FS = FftShape<NWY>;
+        using Fwd = FwdFft<NWY>;
+        constexpr int T = FS::T, E = FS::E, CW = BLOCK / T;
         const int c = tid % CW, t = tid / CW;
         ColExchange<FS::N1, FS::N2, CW> exc{ex, c};
 #pragma unroll 1
-        for (int c0 = 0; c0 < G * NW; c0 += CW) {
+        for (int c0 = 0; c0 < G * NWX; c0 += CW) {
             const int col = c0 + c;
-            const bool ok = col < nwin * NW;
-            const int cc = ok ? col : col % NW;
-            float2 *w = win + (cc / NW) * NW * PW;
-            const int x = cc % NW;
+            const bool ok = col < nwin * NWX;
+            const int cc = ok ? col : col % NWX;
+            float2 *w = win + (cc / NWX) * NWY * PW;
+            const int x = cc % NWX;
             float2 v[E];
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = w[Fwd::in_elem(r, t) * PW + x];
-            Fwd::run(v, t, twf, a.tw, exc);
+            Fwd::run(v, t, twy, a.tw, exc);
             __syncthreads();
             if (ok) {
 #pragma unroll
@@ -141,13 +153,14 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
         }
     }
     __syncthreads();
-    constexpr int LNW = NW == 8 ? 3 : NW == 16 ? 4 : NW == 32 ? 5 : 6;
+    constexpr int LNW = NWX == 8 ? 3 : NWX == 16 ? 4 : NWX == 32 ? 5 : 6;  // u = ky * NWX + kx
+    constexpr int NP = NWX * NWY;
     if (a.cbed) {
         const float fnorm = (float)a.inv_norm;
-        for (int i = tid; i < nwin * NW * NW; i += BLOCK) {
-            const int p = i >> (2 * LNW), u = i & (NW * NW - 1);
-            const float2 z = win[(p * NW + (u >> LNW)) * PW + (u & (NW - 1))];
-            a.cbed[(size_t)oidx[p] * NW * NW + u] = (z.x * z.x + z.y * z.y) * fnorm;
+        for (int i = tid; i < nwin * NP; i += BLOCK) {
+            const int p = i / NP, u = i - p * NP;
+            const float2 z = win[(p * NWY + (u >> LNW)) * PW + (u & (NWX - 1))];
+            a.cbed[(size_t)oidx[p] * NP + u] = (z.x * z.x + z.y * z.y) * fnorm;
         }
     }
     // annular bins: one thread per (window, bin) walks the bin's pixel list with four interleaved
@@ -155,15 +168,15 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
     if (a.out) {
         for (int j = tid; j < nwin * a.nbins; j += BLOCK) {
             const int p = j / a.nbins, k = j - p * a.nbins;
-            const float2 *w = win + p * NW * PW;
+            const float2 *w = win + p * NWY * PW;
             const int e = __ldg(a.bin_off + k + 1);
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             int i = __ldg(a.bin_off + k);
             for (; i + 4 <= e; i += 4) {
                 const int u0 = __ldg(a.bin_idx + i), u1 = __ldg(a.bin_idx + i + 1);
                 const int u2 = __ldg(a.bin_idx + i + 2), u3 = __ldg(a.bin_idx + i + 3);
-                const float2 z0 = w[(u0 >> LNW) * PW + (u0 & (NW - 1))], z1 = w[(u1 >> LNW) * PW + (u1 & (NW - 1))];
-                const float2 z2 = w[(u2 >> LNW) * PW + (u2 & (NW - 1))], z3 = w[(u3 >> LNW) * PW + (u3 & (NW - 1))];
+                const float2 z0 = w[(u0 >> LNW) * PW + (u0 & (NWX - 1))], z1 = w[(u1 >> LNW) * PW + (u1 & (NWX - 1))];
+                const float2 z2 = w[(u2 >> LNW) * PW + (u2 & (NWX - 1))], z3 = w[(u3 >> LNW) * PW + (u3 & (NWX - 1))];
                 s0 = fmaf(z0.x, z0.x, fmaf(z0.y, z0.y, s0));
                 s1 = fmaf(z1.x, z1.x, fmaf(z1.y, z1.y, s1));
                 s2 = fmaf(z2.x, z2.x, fmaf(z2.y, z2.y, s2));
@@ -171,7 +184,7 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
             }
             for (; i < e; ++i) {
                 const int u = __ldg(a.bin_idx + i);
-                const float2 z = w[(u >> LNW) * PW + (u & (NW - 1))];
+                const float2 z = w[(u >> LNW) * PW + (u & (NWX - 1))];
                 s0 = fmaf(z.x, z.x, fmaf(z.y, z.y, s0));
             }
             const float val = (float)((double)((s0 + s1) + (s2 + s3)) * a.inv_norm);

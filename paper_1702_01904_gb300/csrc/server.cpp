@@ -108,7 +108,7 @@ static size_t plan_bytes_estimate(const prism_grid &g) {
     // transmission + wave stack of all beams + S-matrix + tables, matching prism_plan_create
     const double lam = prism_wavelength(g.kv);
     const double a = g.alpha_max_mrad * 1e-3;
-    const double rx = a / (lam * g.f / g.cell_x), ry = a / (lam * g.f / g.cell_y);
+    const double rx = a / (lam * g.f / g.cell_x), ry = a / (lam * (g.f_y > 0 ? g.f_y : g.f) / g.cell_y);
     const double beams = 3.15 * (rx + 1) * (ry + 1) + 8;
     const size_t px = (size_t)g.nx * g.ny;
     const size_t s16 = g.precision != PRISM_PRECISION_FP32

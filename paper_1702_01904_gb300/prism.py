@@ -63,7 +63,7 @@ class PrismGrid(ctypes.Structure):
                 ("cell_x", c_double), ("cell_y", c_double), ("dz", c_double),
                 ("slice_dz", POINTER(c_double)), ("kv", c_double), ("f", c_int),
                 ("downsample", c_int), ("aa_frac", c_double), ("alpha_max_mrad", c_double),
-                ("precision", c_int)]
+                ("precision", c_int), ("f_y", c_int)]
 
 
 class PrismProbe(ctypes.Structure):
@@ -203,9 +203,9 @@ def _stream(s):
 
 # ------------------------------------------------------------------ struct helpers
 def make_grid(nx, ny, n_slices, cell_x, cell_y, dz, kv, f=1, downsample=2, aa_frac=0.5,
-              alpha_max_mrad=20.0, slice_dz=None, precision=PRISM_PRECISION_FP32):
+              alpha_max_mrad=20.0, slice_dz=None, precision=PRISM_PRECISION_FP32, f_y=0):
     g = PrismGrid(nx, ny, n_slices, cell_x, cell_y, dz, None, kv, f, downsample, aa_frac, alpha_max_mrad,
-                  precision)
+                  precision, f_y)
     if slice_dz is not None:
         arr = np.ascontiguousarray(slice_dz, dtype=np.float64)
         g._keep = arr

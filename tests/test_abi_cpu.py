@@ -63,7 +63,7 @@ int main(void) {
   printf("prism_detector %zu\\n", sizeof(prism_detector));
   printf("prism_info %zu\\n", sizeof(prism_info));
   F(prism_grid, cell_x) F(prism_grid, slice_dz) F(prism_grid, kv) F(prism_grid, f) F(prism_grid, aa_frac)
-  F(prism_grid, alpha_max_mrad) F(prism_grid, precision) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
+  F(prism_grid, alpha_max_mrad) F(prism_grid, precision) F(prism_grid, f_y) F(prism_scan, x0) F(prism_scan, y0) F(prism_detector, nbins)
   F(prism_info, wavelength) F(prism_info, device_bytes)
   printf("prism_cell %zu\\n", sizeof(prism_cell));
   printf("prism_batch_info %zu\\n", sizeof(prism_batch_info));
@@ -112,3 +112,7 @@ def test_plan_arguments_rejected_before_any_device_call():
     assert status(precision=P.PRISM_PRECISION_FP16X2, f=4) == P.PRISM_ERR_UNSUPPORTED
     assert status(nx=100) == P.PRISM_ERR_UNSUPPORTED
     assert status(f=0) == P.PRISM_ERR_INVALID
+    assert status(f_y=-1) == P.PRISM_ERR_INVALID
+    assert status(f_y=3) == P.PRISM_ERR_INVALID            # 64 not divisible by 2 * 3
+    assert status(f_y=1, precision=P.PRISM_PRECISION_FP16) == P.PRISM_ERR_UNSUPPORTED  # 16 x 32 window
+    assert status(f=1, f_y=8) == P.PRISM_ERR_UNSUPPORTED  # 32 x 4 window

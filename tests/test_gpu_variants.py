@@ -103,3 +103,54 @@ def test_tilt_out_of_range_rejected():
         sim.scan(P.make_probe(20.0, tilt_x=0.7), [0.0], [0.0], det_c(DET))
     assert e.value.status == P.PRISM_ERR_INVALID
     sim.close()
+
+
+# ------------------------------------------------------------------ separate interpolation factors f_x, f_y
+def rect_grid(n, cell, H, f, fy):
+    g = grid_dict(n, n, cell, cell, H, 2.0, f)
+    g["f_y"] = fy
+    return g, P.make_grid(n, n, H, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0, f_y=fy)
+
+
+@pytest.mark.parametrize("n,cell,H,f,fy,nwx,nwy", [
+    (64, 8.0, 3, 2, 1, 16, 32),
+    (128, 12.8, 2, 4, 2, 16, 32),
+    (128, 12.8, 2, 1, 2, 64, 32),
+    (128, 12.8, 2, 2, 4, 32, 16),
+])
+def test_rectangular_window_scan_matches_oracle(n, cell, H, f, fy, nwx, nwy):
+    g, cg = rect_grid(n, cell, H, f, fy)
+    V = rand_v(H, n, n, 31)
+    sim = PrismSimulation(cg)
+    assert (sim.info.nw_x, sim.info.nw_y) == (nwx, nwy)
+    m, nn = sim.beams()
+    om, on = O.beam_set(n, n, cell, cell, 300.0, f, 20.0, fy)
+    assert np.array_equal(m, om) and np.array_equal(nn, on)
+    sim.build(torch.from_numpy(V).cuda())
+    S, m, nn = O.smatrix_build(V, g)
+    probe = dict(alpha_mrad=20.0, c1=12.0)
+    # scattered, wrapped positions (probe by probe) and a ragged raster (shared union tiles)
+    rng = np.random.Generator(np.random.PCG64(32))
+    x0 = rng.uniform(-cell, 2 * cell, 13)
+    y0 = rng.uniform(-cell, 2 * cell, 13)
+    out = sim.scan(cprobe(probe), x0, y0, det_c(DET)).cpu().numpy()
+    assert_images_close(out, O.prism_scan(S, m, nn, g, probe, DET, x0, y0))
+    X, Y = np.meshgrid(np.arange(7) * 0.35, np.arange(3) * 0.35 + 1.0)
+    out = sim.scan(cprobe(probe), X.ravel(), Y.ravel(), det_c(DET), px=7, py=3).cpu().numpy()
+    assert_images_close(out, O.prism_scan(S, m, nn, g, probe, DET, X.ravel(), Y.ravel()))
+    cb = sim.scan_cbed(cprobe(probe), x0[:4], y0[:4]).cpu().numpy()
+    assert cb.shape == (4, nwy, nwx)
+    ref = O.prism_cbed(S, m, nn, g, probe, x0[:4], y0[:4])
+    assert np.linalg.norm(cb - ref) / np.linalg.norm(ref) < 1e-5
+    sim.close()
+
+
+def test_rectangular_window_limits():
+    # 16-bit storage needs square windows; rectangular windows need sides of 16, 32 or 64
+    with pytest.raises(P.PrismError) as e:
+        PrismSimulation(P.make_grid(64, 64, 1, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0,
+                                    precision=P.PRISM_PRECISION_FP16X2, f_y=1))
+    assert e.value.status == P.PRISM_ERR_UNSUPPORTED
+    with pytest.raises(P.PrismError) as e:
+        PrismSimulation(P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 1, 2, 0.5, 20.0, f_y=2))  # 128 x 64
+    assert e.value.status == P.PRISM_ERR_UNSUPPORTED
