@@ -812,9 +812,21 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
 
 // FP32 mode: the CUDA-core scan kernels; 16-bit mode: the tensor-core kernel (persistent grid, its
 // window scratch grown on demand)
+// FP32: the GEMM scan over 8 x 4 raster blocks when its shared memory fits (grid > 0), else the
+// grouped / per-probe kernels (grid 0); 16-bit: the tensor-core scan
 static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
     *grid = 0;
-    if (P->prec == PRISM_PRECISION_FP32) return PRISM_OK;
+    if (P->prec == PRISM_PRECISION_FP32) {
+        *grid = scan_gemm_grid(P->nw, P->nwy, P->nbeams, a.scan_px, a.scan_py);
+        if (*grid <= 0) {
+            *grid = 0;
+            return PRISM_OK;
+        }
+        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, *grid));
+        if (rc) return rc;
+        a.win = P->win;
+        return PRISM_OK;
+    }
     *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), a.scan_px, a.scan_py);
     if (*grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
     int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid));
@@ -825,7 +837,9 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
 
 static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
     if (P->prec == PRISM_PRECISION_FP32)
-        return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_rect(P->nw, P->nwy, a, P->stream); });
+        return plan_launch(P, PRISM_K_SCAN, [&] {
+            return grid > 0 ? launch_scan_gemm(P->nw, P->nwy, grid, a, P->stream) : launch_scan_rect(P->nw, P->nwy, a, P->stream);
+        });
     return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), grid, a, P->stream); });
 }
 

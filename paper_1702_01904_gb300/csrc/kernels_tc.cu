@@ -283,10 +283,7 @@ struct TcCfg {
     }
     __host__ __device__ static constexpr size_t smem(int kp) { return region0(kp) + MISC; }
 };
-// meta (ints): [0] union tile  [1] tile width  [2] tile height  [3] tile x0  [4] tile y0
-// [5] probes in the group; per slot p < G: [8+p] window x0  [40+p] window y0  [72+p] x offset in
-// the tile  [104+p] y offset in the tile  [136+p] probe index or -1; [168+e] slot of the e-th
-// probe, [200+e] its probe index
+// meta: the layout of raster_group_geometry (scan_common.cuh)
 
 
 template <int NW, int MODE>
@@ -367,45 +364,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
             }
         }
         // group geometry (warp 0, one lane per slot): window origins of Eq. RegionBounds, union tile
-        if (warp == 0) {
-            const int p = lane;
-            const int row = gy * GY + p / GX, col = gx * GX + p % GX;
-            const bool valid = p < G && row < a.scan_py && col < a.scan_px;
-            int sx = 0, sy = 0;
-            if (valid) {
-                const int pr = row * a.scan_px + col;
-                sx = ((int)floor(a.x0[pr] / a.px_s + 0.5) - NW / 2) & (a.nx_s - 1);
-                sy = ((int)floor(a.y0[pr] / a.py_s + 0.5) - NW / 2) & (a.ny_s - 1);
-            }
-            const int sx0 = __shfl_sync(0xffffffffu, sx, 0), sy0 = __shfl_sync(0xffffffffu, sy, 0);
-            const int dx = valid ? ((sx - sx0 + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2 : 0;
-            const int dy = valid ? ((sy - sy0 + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2 : 0;
-            const int dxmin = __reduce_min_sync(0xffffffffu, dx), dxmax = __reduce_max_sync(0xffffffffu, dx);
-            const int dymin = __reduce_min_sync(0xffffffffu, dy), dymax = __reduce_max_sync(0xffffffffu, dy);
-            const unsigned vm = __ballot_sync(0xffffffffu, valid);
-            const int nvalid = __popc(vm);
-            const int tw = dxmax - dxmin + NW, th = dymax - dymin + NW;
-            if (p < G) {
-                meta[8 + p] = sx;
-                meta[40 + p] = sy;
-                meta[72 + p] = dx - dxmin;
-                meta[104 + p] = dy - dymin;
-                meta[136 + p] = valid ? row * a.scan_px + col : -1;
-            }
-            if (valid) {
-                const int e = __popc(vm & ((1u << p) - 1u));
-                meta[168 + e] = p;
-                meta[200 + e] = row * a.scan_px + col;
-            }
-            if (lane == 0) {
-                meta[0] = (long long)tw * th <= (long long)nvalid * NW * NW;
-                meta[1] = tw;
-                meta[2] = th;
-                meta[3] = (sx0 + dxmin) & (a.nx_s - 1);
-                meta[4] = (sy0 + dymin) & (a.ny_s - 1);
-                meta[5] = nvalid;
-            }
-        }
+        if (warp == 0) raster_group_geometry<NW, NW, GX, GY>(a, gx, gy, meta, lane);
         tc::fence_proxy_async();  // Bc was written through the generic proxy; the MMAs read it
         __syncthreads();
         const bool uni = meta[0] != 0;

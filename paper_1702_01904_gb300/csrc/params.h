@@ -131,6 +131,11 @@ cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
 // per side) through the grouped kernel; scan_rect_supported says whether a launch can succeed
 cudaError_t launch_scan_rect(int nwx, int nwy, const ScanArgs &a, cudaStream_t s);
 bool scan_rect_supported(int nwx, int nwy, int n_beams);
+// FP32 GEMM scan over 8 x 4 raster blocks (window sides 16, 32, 64): persistent grid (0 if it does
+// not fit), launch, and the window scratch it needs ([grid][32][nwy][nwx] complex64)
+int scan_gemm_grid(int nwx, int nwy, int n_beams, int scan_px, int scan_py);
+cudaError_t launch_scan_gemm(int nwx, int nwy, int grid, const ScanArgs &a, cudaStream_t s);
+size_t scan_gemm_win_bytes(int nwx, int nwy, int grid);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
 cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);

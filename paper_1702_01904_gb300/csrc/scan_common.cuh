@@ -18,6 +18,11 @@ __device__ __forceinline__ void cp_async16_ca(void *smem_dst, const void *gmem_s
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+// 8-byte copy through L1 (one complex64 pixel)
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -69,6 +74,56 @@ __device__ void group_geometry(const ScanArgs &a, int p0, int gn, int *meta) {
     meta[2] = th;
     meta[3] = tx0 - shift;
     meta[4] = (sy[0] + dymin) & (a.ny_s - 1);
+}
+
+// Geometry of a GX x GY block of the probe raster (group gx, gy), NWX x NWY windows; executed by
+// one warp, lane p = slot j * GX + i for raster row gy*GY + j, column gx*GX + i (GX*GY <= 32).
+// Window origins follow Eq. RegionBounds in FP64; the union tile of the slots' windows is used
+// when it is no larger than their windows together, else each probe runs on its own window.
+// meta (ints): [0] union tile  [1] tile width  [2] tile height  [3] tile x0  [4] tile y0
+// [5] probes in the group; per slot p < 32: [8+p] window x0  [40+p] window y0  [72+p] x offset in
+// the tile  [104+p] y offset in the tile  [136+p] probe index or -1; [168+e] slot of the e-th
+// probe, [200+e] its probe index
+template <int NWX, int NWY, int GX, int GY>
+__device__ void raster_group_geometry(const ScanArgs &a, int gx, int gy, int *meta, int lane) {
+    constexpr int G = GX * GY;
+    const int p = lane;
+    const int row = gy * GY + p / GX, col = gx * GX + p % GX;
+    const bool valid = p < G && row < a.scan_py && col < a.scan_px;
+    int sx = 0, sy = 0;
+    if (valid) {
+        const int pr = row * a.scan_px + col;
+        sx = ((int)floor(a.x0[pr] / a.px_s + 0.5) - NWX / 2) & (a.nx_s - 1);
+        sy = ((int)floor(a.y0[pr] / a.py_s + 0.5) - NWY / 2) & (a.ny_s - 1);
+    }
+    const int sx0 = __shfl_sync(0xffffffffu, sx, 0), sy0 = __shfl_sync(0xffffffffu, sy, 0);
+    const int dx = valid ? ((sx - sx0 + a.nx_s / 2) & (a.nx_s - 1)) - a.nx_s / 2 : 0;
+    const int dy = valid ? ((sy - sy0 + a.ny_s / 2) & (a.ny_s - 1)) - a.ny_s / 2 : 0;
+    const int dxmin = __reduce_min_sync(0xffffffffu, dx), dxmax = __reduce_max_sync(0xffffffffu, dx);
+    const int dymin = __reduce_min_sync(0xffffffffu, dy), dymax = __reduce_max_sync(0xffffffffu, dy);
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    const int nvalid = __popc(vm);
+    const int tw = dxmax - dxmin + NWX, th = dymax - dymin + NWY;
+    if (p < G) {
+        meta[8 + p] = sx;
+        meta[40 + p] = sy;
+        meta[72 + p] = dx - dxmin;
+        meta[104 + p] = dy - dymin;
+        meta[136 + p] = valid ? row * a.scan_px + col : -1;
+    }
+    if (valid) {
+        const int e = __popc(vm & ((1u << p) - 1u));
+        meta[168 + e] = p;
+        meta[200 + e] = row * a.scan_px + col;
+    }
+    if (lane == 0) {
+        meta[0] = (long long)tw * th <= (long long)nvalid * NWX * NWY;
+        meta[1] = tw;
+        meta[2] = th;
+        meta[3] = (sx0 + dxmin) & (a.nx_s - 1);
+        meta[4] = (sy0 + dymin) & (a.ny_s - 1);
+        meta[5] = nvalid;
+    }
 }
 
 // alpha[p][b] = A(q_b - q_t) e^{-i chi} e^{-2 pi i q_b.(r0_p - h tan theta)} for the group's probes
