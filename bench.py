@@ -155,9 +155,14 @@ def oracle_sample(w, V, budget_s=20.0):
     }
 
 
+# sources of the row and column pass kernels (the ones profiles/dram_traffic.json measures)
+PASS_SOURCES = ("fft.cuh", "params.h", "pass_kernels.cuh", "kernels_build.cu", "kernels_tune.cu", "kernels_tune_row.cu",
+                "tune_shapes.cuh")
+
+
 def source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1702_01904_gb300", "csrc"))):
+    for f in PASS_SOURCES:
         with open(os.path.join(ROOT, "paper_1702_01904_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
