@@ -1,13 +1,16 @@
-// kernels_scan.cu -- the PRISM probe scan for sm_103a (PRISM Algorithm section, Fig. 1d-f).
+// kernels_scan.cu -- the FP32 PRISM probe scan for sm_103a (PRISM Algorithm section, Fig. 1d-f).
 //
-// One CTA per probe position r0:
+// Every kernel takes, per probe position r0:
 //   1. coefficients alpha_b(r0) = A(q_b) e^{-i chi(q_b)} e^{-2 pi i q_b.r0}; the phase q_b.r0 is
 //      formed in FP64 and reduced to [-1/2, 1/2) cycles before the FP32 sincos;
 //   2. window origin s = floor(r0 / px' + 1/2) - Nw/2 (mod N') on the stored grid (Eq. RegionBounds);
-//   3. beam sum psi(u) = sum_b alpha_b S_b(s + u) over the Nw x Nw window, wrapped (Eq. PRISMfinal),
-//      each thread accumulating a fixed set of window pixels in registers;
+//   3. beam sum psi(u) = sum_b alpha_b S_b(s + u) over the window, wrapped (Eq. PRISMfinal);
 //   4. 2-D FFT of the window in shared memory (row then column two-level FFTs);
-//   5. |Psi|^2 and the annular bins: one warp per bin, FP64 sums in a fixed order.
+//   5. |Psi|^2 and the annular bins, fixed summation order, FP64 scale.
+// Three kernels: k_scan_gemm (8 x 4 raster blocks, the beam sum as a register-tiled complex GEMM on
+// the union tile of their windows; the default), k_scan_grouped (4 consecutive probes, used when the
+// GEMM's coefficient block does not fit shared memory or for 8-pixel windows) and k_scan (one probe
+// per CTA, for 128-pixel windows and very large beam sets).
 #include <cuda_runtime.h>
 
 #include <algorithm>
