@@ -36,6 +36,24 @@ UNIT = "probes/s"
 DET = dict(start_mrad=0.0, step_mrad=1.0, nbins=100)
 
 
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's time (ms): a barrier-bracketed region timed on every rank, reduced with MAX
+    (dist None: single process)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, ms):
+    """Units per second of the whole job: every rank (a replica of the workload) processed
+    units_per_rank per step for `steps` steps within `ms` (the slowest rank's time)."""
+    return world * units_per_rank * steps / (ms / 1000.0)
+
+
 def workload_config(w, B):
     return {
         "workload": f"amorphous carbon 50x50x100 A (25000 Z=6 atoms, seed 1), {w.nx}x{w.ny} grid, "
@@ -457,10 +475,7 @@ def main():
         sim.set_profiling(False)
         stats = sim.kernel_stats()
         launches = sim.launches()
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, total_ms, "cuda")
 
         # end to end through the C ABI with host buffers (pinned), copies inside the timed region
         V_pin = V_host.pin_memory()
@@ -484,10 +499,7 @@ def main():
         e1.record(stream)
         stream.synchronize()
         e2e_ms = (time.perf_counter() - t_e2e0) * 1000.0
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(dist, e2e_ms, "cuda")
         h2d = V_host.numel() * 4 + P * 16
         d2h = P * DET["nbins"] * 4
 
@@ -549,7 +561,7 @@ def main():
                 s2.close()
         sim.close()
 
-    value = world * P * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, P, args.steps, total_ms)
     ms_probes_s = nms / (ms_ms / 1000.0)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean event time per launch
@@ -637,7 +649,7 @@ def main():
                       "fp16x2": "f16 value + f16 remainder S / f32 accumulate"}[args.precision],
             "data": "synthetic (seeded amorphous-carbon phantom; the paper's Pt/a-C coordinates are not available)",
             "config": {**workload_config(w, Bn), "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "e2e": {"value": world * P * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
+            "e2e": {"value": whole_job_rate(world, P, args.steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "path": "prism_build_smatrix_host + prism_scan_run_host, pinned host buffers, wall clock"},
             "gpu_launches": launches,
