@@ -589,6 +589,14 @@ def main():
         # 16-bit mode: FP32 S of the batch read twice (scale, convert), 16-bit pixel-major S written
         "quantize": 2 * Bn * (px // 4) * 8 + (px // 4) * 2 * ((Bn + 7) // 8 * 8) * 2,
     }
+    # FFT flops per launch: a row pass does an inverse and a forward length-nx transform per row of
+    # every beam plus the t_p multiply (6 flops per element); a column pass the same per kept column
+    # with the propagator multiply
+    fl = lambda n: 5.0 * n * math.log2(n)
+    fft_flops = {
+        "row": Bn * w.ny * (2 * fl(w.nx) + 6.0 * w.nx),
+        "col": Bn * (2 * K + 1) * (2 * fl(w.ny) + 6.0 * w.ny),
+    }
     rows = {}
     for name, (n_l, t_ms) in stats.items():
         if n_l == 0:
@@ -601,6 +609,13 @@ def main():
             gbs = alg[name] / (r["mean_ms"] / 1000.0) / 1e9
             roof_all[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                               "frac": gbs / hbm_peak, "bytes_per_launch": alg[name], **r}
+            if name in fft_flops:
+                # the same launch against the FP32 FFT-flop roofline (5 N log2 N per length-N transform)
+                clk_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+                fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+                tf = fft_flops[name] / (r["mean_ms"] / 1000.0) / 1e12
+                roof_all[name].update({"fft_tflops": tf, "fft_peak_tflops": fp32_peak, "fft_frac": tf / fp32_peak,
+                                       "fft_flops_per_launch": fft_flops[name]})
         elif name == "scan" and args.precision != "fp32":
             # beam sum on the tensor cores: 8 real flops per complex MAC, against the measured dense
             # 16-bit rate (sustained: the scan runs inside a seconds-long loop of steps)
