@@ -328,7 +328,7 @@ static bool grouped_fits(int n_beams) {
 // The beam sum of Eq. PRISMfinal for an 8 x 4 block of the probe raster as a complex GEMM on the
 // union tile of their windows, on the CUDA cores in FP32: psi_p(r) = sum_b S_b(r) alpha_bp for the
 // tile pixels r (M) and the block's 32 probes (N), K = the beams.  The tile is streamed in M tiles
-// of 128 pixels; per M tile the beams pass through a 3-stage cp.async ring (KB beams x 128 pixels
+// of 128 pixels; per M tile the beams pass through a 2-stage cp.async ring (KB beams x 128 pixels
 // per stage, one 8-byte copy per pixel and beam); thread (lane, warp) accumulates pixels lane +
 // 32 i (i < 4) for probes 4 warp + j (j < 4) in registers, so one 8-byte shared-memory load feeds
 // four complex MACs.  Finished M tiles are scattered to the per-CTA window scratch; the window FFT
@@ -338,8 +338,8 @@ template <int NWX, int NWY>
 struct GemmCfg {
     static constexpr int GX = 8, GY = 4, G = GX * GY;
     static constexpr int BLOCK = 256;
-    static constexpr int KB = 16;                    // beams per ring stage
-    static constexpr int STAGES = 3;
+    static constexpr int KB = 32;                    // beams per ring stage
+    static constexpr int STAGES = 2;
     static constexpr int MT = 128;                   // tile pixels per M tile
     static constexpr int RING = STAGES * KB * MT;    // float2
     static constexpr int PW = NWX + 8;
