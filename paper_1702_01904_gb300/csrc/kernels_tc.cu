@@ -246,7 +246,7 @@ cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, 
 //     Bc[2p][2b] = s_b Re a_bp,  Bc[2p][2b+1] = -s_b Im a_bp,  Bc[2p+1][2b] = s_b Im a_bp,
 //     Bc[2p+1][2b+1] = s_b Re a_bp      (a_bp the coefficient of beam b for probe p, s_b its scale)
 // so D[r][2p] + i D[r][2p+1] = psi_p(r).  The tile is streamed in M tiles of 128 pixels and K
-// chunks (a 3-stage cp.async ring), one thread issues tcgen05.mma (M = 128, N = 2 G, K = 16) into
+// chunks (a 2-stage cp.async ring), one thread issues tcgen05.mma (M = 128, N = 2 G, K = 16) into
 // one of two TMEM accumulators, all warps drain a finished accumulator (tcgen05.ld) and scatter
 // each probe's window pixels to a per-CTA global scratch.  When the group is done the windows come
 // back through shared memory for the window FFT, |.|^2 and the bins (the epilogue of the FP32
@@ -260,8 +260,8 @@ struct TcCfg {
     static constexpr int GX = 8, GY = 4, G = GX * GY, N = 2 * G;
     static constexpr int BLOCK = 256;
     static constexpr int PARTS = SPLIT ? 2 : 1;              // hi (and lo) operand parts
-    static constexpr int STAGES = SPLIT ? 2 : 3;
-    static constexpr int KCMAX = SPLIT ? 32 : 64;            // K (16-bit values) per ring stage
+    static constexpr int STAGES = 2;
+    static constexpr int KCMAX = SPLIT ? 32 : 128;           // K (16-bit values) per ring stage
     static constexpr int PART_BYTES = 128 * KCMAX * 2;       // 128 pixels x KCMAX of one part
     static constexpr int STAGE_BYTES = PARTS * PART_BYTES;
     static constexpr int RING = STAGES * STAGE_BYTES;
