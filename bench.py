@@ -322,17 +322,17 @@ def batch_leg(n_cells=64, runs=2, n_branches=4, autotune=True):
             "what": "every cell's transmission + S-matrix build + 16x16-probe scan, FP32, one cudaGraphLaunch per run"}
 
 
-def ncu_case(precision="fp32"):
+def ncu_case(precision="fp32", full_k=False):
     import torch
 
     from paper_1702_01904_gb300 import prism as PR
     from paper_1702_01904_gb300 import specimens
     from paper_1702_01904_gb300.runtime import PrismSimulation
 
-    # FP32: 25 beams (alpha_max 9 mrad), the first 10 scan rows (2000 probes).  16-bit: the full
-    # 129-beam set, so that the tensor-core scan sees the real K, and the first 52 rows (10400
-    # probes, 325 groups of 8 x 4: every resident CTA busy).  Both: 4 slices.
-    half = precision != "fp32"
+    # FP32: 25 beams (alpha_max 9 mrad), the first 10 scan rows (2000 probes).  16-bit, or FP32
+    # with full_k: the full 129-beam set, so that the scan sees the real K, and the first 52 rows
+    # (10400 probes, 325 groups of 8 x 4: every resident CTA busy).  Both: 4 slices.
+    half = precision != "fp32" or full_k
     w = specimens.workload_amorphous_carbon(n_slices=4, alpha_mrad=20.0 if half else 9.0)
     V = torch.from_numpy(w.potential()).cuda()
     x0, y0 = w.scan_positions()
@@ -372,9 +372,11 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the profiling case twice and exit: the same 1024^2 a-C grid, 4 slices, "
                          "alpha_max 9 mrad (25 beams, 200 MB wave stack), 2000 probes")
+    ap.add_argument("--ncu-full-k", action="store_true",
+                    help="with --ncu-case: all 129 beams and 10400 probes in every precision")
     args = ap.parse_args()
     if args.ncu_case:
-        return ncu_case(args.precision)
+        return ncu_case(args.precision, args.ncu_full_k)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

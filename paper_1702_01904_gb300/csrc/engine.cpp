@@ -362,8 +362,10 @@ struct prism_plan {
     void *S16 = nullptr;       // 16-bit mode: [ny_s * nx_s][kp]
     float *scale = nullptr;    // 16-bit mode: [kp / 2] per-beam power-of-two scales
     int kp = 0;
-    float2 *win = nullptr;     // 16-bit mode: scan window scratch
+    float2 *win = nullptr;     // scan window scratch (GEMM and tensor-core scans)
     size_t win_cap = 0;
+    int *win_cnt = nullptr;    // FP32 GEMM scan: completion counters of split groups
+    size_t cnt_cap = 0;
     int *dev_err = nullptr;    // device error word
     int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
     double tune_ms[2][PRISM_TUNE_MAX_SHAPES];
@@ -822,9 +824,15 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
             *grid = 0;
             return PRISM_OK;
         }
-        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, *grid));
+        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, *grid, a.scan_px, a.scan_py));
         if (rc) return rc;
+        // the counters start at zero and every launch leaves them at zero
+        const size_t cb = scan_gemm_cnt_bytes(*grid);
+        const bool fresh = !P->win_cnt || cb > P->cnt_cap;
+        if ((rc = grow(P->arena, (void **)&P->win_cnt, &P->cnt_cap, cb))) return rc;
+        if (fresh) CUDA_TRY(cudaMemsetAsync(P->win_cnt, 0, P->cnt_cap, P->stream));
         a.win = P->win;
+        a.win_cnt = P->win_cnt;
         return PRISM_OK;
     }
     *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), a.scan_px, a.scan_py);

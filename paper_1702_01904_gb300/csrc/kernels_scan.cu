@@ -187,7 +187,7 @@ struct GroupCfg {
     static constexpr int MAXTILE = (NWX + D) * NWY;           // tile pixels
     static constexpr int PIX = (MAXTILE + BLOCK - 1) / BLOCK; // tile pixels per thread
     static constexpr int PAIRS = (MAXTILE / 2 + BLOCK - 1) / BLOCK;  // 16-byte copies per thread
-    static constexpr int PW = NWX + 8;                        // window row pitch (bank spread)
+    static constexpr int PW = NWX + 4;                        // window row pitch (bank spread)
     static constexpr int EX = ExSize<NWX, NWY, BLOCK>::value;
     static constexpr int STAGES = 4;                          // cp.async pipeline depth (beams in flight)
     static constexpr int BIG = (STAGES * MAXTILE > G * NWY * PW) ? STAGES * MAXTILE : G * NWY * PW;
@@ -334,6 +334,14 @@ static bool grouped_fits(int n_beams) {
 // four complex MACs.  Finished M tiles are scattered to the per-CTA window scratch; the window FFT
 // and bins are the shared epilogue.  A block whose union tile is larger than its windows together
 // runs probe by probe (only the warp holding that probe computes).
+// Work units: the blocks of all full rounds of the persistent grid run whole; the blocks of the
+// last, partial round (fewer than the CTAs; all blocks of a scan smaller than the grid) are split
+// into up to MAXP parts of their M tiles (or of their probes, when they run probe by probe) so that
+// that round keeps every CTA busy.  A split block's windows go to a scratch slot of its own; each
+// part counts itself done on an atomic counter, and the part that completes the block runs its
+// epilogue.  Every window pixel is still one accumulation in the same beam order, so the split
+// changes no result.  Scratch slots: [0, tail) the split blocks, then one per CTA when some block
+// runs whole.
 template <int NWX, int NWY>
 struct GemmCfg {
     static constexpr int GX = 8, GY = 4, G = GX * GY;
@@ -342,12 +350,14 @@ struct GemmCfg {
     static constexpr int STAGES = 2;
     static constexpr int MT = 128;                   // tile pixels per M tile
     static constexpr int RING = STAGES * KB * MT;    // float2
-    static constexpr int PW = NWX + 8;
+    static constexpr int PW = NWX + 4;                        // window row pitch (bank spread)
     static constexpr int NWM = NWX > NWY ? NWX : NWY;
     static constexpr int EW = NWM >= 64 ? 2 : NWM == 32 ? 8 : 16;  // windows per epilogue pass
     static constexpr int EX = ExSize<NWX, NWY, BLOCK>::value;
     static constexpr size_t EPI = (size_t)(EW * NWY * PW + EX) * sizeof(float2);
     static constexpr int META = 256;
+    static constexpr int META_LAST = META - 1;       // flag: this CTA completed a split block
+    static constexpr int MAXP = 16;                  // parts per split block at most
     __host__ __device__ static constexpr size_t region0(int n_beams) {
         const size_t r = ((size_t)RING + (size_t)n_beams * G) * sizeof(float2);
         return ((r > EPI ? r : EPI) + 127) & ~(size_t)127;
@@ -377,7 +387,20 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
     const size_t npix_s = (size_t)a.ny_s * a.nx_s;
     const int nkc = (nb + KB - 1) / KB, kcs = (nb + nkc - 1) / nkc;  // balanced beam chunks
 
-    for (int grp = blockIdx.x; grp < ngx * ngy; grp += gridDim.x) {
+    const int n_groups = ngx * ngy;
+    const int tail = n_groups % gridDim.x, full = n_groups - tail;
+    const int parts = tail ? min(C::MAXP, (int)gridDim.x / tail) : 1;
+
+    for (int u = blockIdx.x; u < full + tail * parts; u += gridDim.x) {
+        // unit u: block u whole (scratch slot = this CTA), or part `part` of split block full + tg
+        int grp = u, part = 0, np = 1, slot = tail + blockIdx.x;
+        if (u >= full) {
+            const int tg = (u - full) / parts;
+            grp = full + tg;
+            part = u - full - tg * parts;
+            np = parts;
+            slot = tg;
+        }
         const int gy = grp / ngx, gx = grp - gy * ngx;
         // coefficients alpha[b][p] (zero for slots past the raster)
         for (int i = tid; i < nb * G; i += BLOCK) {
@@ -398,15 +421,17 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
         __syncthreads();
         const bool uni = meta[0] != 0;
         for (int sg = 0; sg < (uni ? 1 : G); ++sg) {
-            if (!uni && meta[136 + sg] < 0) continue;
+            if (!uni && (meta[136 + sg] < 0 || sg % np != part)) continue;
             const int tw = uni ? meta[1] : NWX, th = uni ? meta[2] : NWY;
             const int tx0 = uni ? meta[3] : meta[8 + sg], ty0 = uni ? meta[4] : meta[40 + sg];
-            const int npx = tw * th, nmt = (npx + MT - 1) / MT, nsteps = nmt * nkc;
+            const int npx = tw * th, nmt = (npx + MT - 1) / MT;
+            // ring steps (M tile, beam chunk) of this unit: all, or a split block's share of M tiles
+            const int ls0 = uni ? part * nmt / np * nkc : 0, ls1 = uni ? (part + 1) * nmt / np * nkc : nmt * nkc;
             const bool busy = uni || (sg >> 2) == warp;  // warps whose probes are computed
             // loader: thread -> tile pixel m = tid % MT, beams kk = tid / MT, + 2, ...
             const int lm = tid & (MT - 1), lk = tid >> 7;
             auto load = [&](int ls) {
-                if (ls < nsteps) {
+                if (ls < ls1) {
                     const int mt = ls / nkc, c = ls - mt * nkc;
                     const int b0 = c * kcs, bn = min(kcs, nb - b0);
                     const int idx = mt * MT + lm;
@@ -420,13 +445,13 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                 cp_async_commit();
             };
 #pragma unroll
-            for (int l = 0; l < S - 1; ++l) load(l);
+            for (int l = 0; l < S - 1; ++l) load(ls0 + l);
             float2 acc[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-            for (int ls = 0; ls < nsteps; ++ls) {
+            for (int ls = ls0; ls < ls1; ++ls) {
                 const int mt = ls / nkc, c = ls - mt * nkc;
                 cp_async_wait<S - 2>();
                 __syncthreads();
@@ -464,7 +489,7 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                                 const bool act = uni ? meta[136 + p] >= 0 : p == sg;
                                 const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
                                 if (act && idx < npx && (unsigned)wy < (unsigned)NWY && (unsigned)wx < (unsigned)NWX)
-                                    a.win[((size_t)blockIdx.x * G + p) * (NWX * NWY) + wy * NWX + wx] = acc[i][j];
+                                    __stcs(a.win + ((size_t)slot * G + p) * (NWX * NWY) + wy * NWX + wx, acc[i][j]);
                                 acc[i][j] = make_float2(0.f, 0.f);
                             }
                         }
@@ -474,15 +499,33 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             cp_async_wait<0>();
             __syncthreads();  // ring reads done before the next sub-group or the epilogue reuses it
         }
+        if (np > 1) {
+            // split block: count this part done; the part that completes the block goes on to its
+            // epilogue (release: every thread's scratch stores before the count; acquire: the count
+            // before the scratch loads, which read L2)
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const int last = atomicAdd(a.win_cnt + slot, 1) == np - 1;
+                if (last) a.win_cnt[slot] = 0;  // all parts counted: zero for the next launch
+                __threadfence();
+                meta[C::META_LAST] = last;
+            }
+            __syncthreads();
+            if (!meta[C::META_LAST]) continue;
+        }
         // epilogue: EW windows at a time through shared memory (the window scratch written above is
         // visible to the whole CTA after the barrier)
         const int nvalid = meta[5];
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
             const int ne = min(C::EW, nvalid - e0);
-            for (int i = tid; i < ne * NWX * NWY; i += BLOCK) {
-                const int e = i / (NWX * NWY), u = i - e * (NWX * NWY);
-                win[(e * NWY + u / NWX) * PW + (u % NWX)] = __ldcg(a.win + ((size_t)blockIdx.x * G + meta[168 + e0 + e]) * (NWX * NWY) + u);
+            // the windows in 16-byte pieces (two pixels of a row), every piece in flight at once
+            for (int i = tid; i < ne * (NWX * NWY / 2); i += BLOCK) {
+                const int e = i / (NWX * NWY / 2), u = 2 * (i - e * (NWX * NWY / 2));
+                cp_async16(win + (e * NWY + u / NWX) * PW + (u % NWX), a.win + ((size_t)slot * G + meta[168 + e0 + e]) * (NWX * NWY) + u);
             }
+            cp_async_commit();
+            cp_async_wait<0>();
             __syncthreads();
             window_epilogue<NWX, NWY, BLOCK, C::EW, PW>(a, win, ex, twx, twy, ne, meta + 200 + e0, tid);
             __syncthreads();
@@ -506,7 +549,7 @@ static int gemm_grid(int n_beams, int scan_px, int scan_py) {
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
     const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
-    return (int)std::max<long long>(1, std::min<long long>(groups, (long long)per_sm * sms));
+    return (int)std::max<long long>(1, std::min<long long>(groups * C::MAXP, (long long)per_sm * sms));
 }
 
 template <int NWX, int NWY>
@@ -533,7 +576,7 @@ int scan_gemm_grid(int nwx, int nwy, int n_beams, int scan_px, int scan_py) {
 }
 
 cudaError_t launch_scan_gemm(int nwx, int nwy, int grid, const ScanArgs &a, cudaStream_t s) {
-    if (grid <= 0 || !a.win || a.scan_px <= 0 || a.scan_py <= 0) return cudaErrorInvalidValue;
+    if (grid <= 0 || !a.win || !a.win_cnt || a.scan_px <= 0 || a.scan_py <= 0) return cudaErrorInvalidValue;
 #define PRISM_GEMM_LAUNCH(x, y) \
     if (nwx == x && nwy == y) return gemm_launch<x, y>(grid, a, s);
     PRISM_GEMM_SIDES(PRISM_GEMM_LAUNCH)
@@ -541,7 +584,15 @@ cudaError_t launch_scan_gemm(int nwx, int nwy, int grid, const ScanArgs &a, cuda
     return cudaErrorInvalidValue;
 }
 
-size_t scan_gemm_win_bytes(int nwx, int nwy, int grid) { return (size_t)grid * GemmCfg<16, 16>::G * nwx * nwy * sizeof(float2); }
+size_t scan_gemm_win_bytes(int nwx, int nwy, int grid, int scan_px, int scan_py) {
+    using C = GemmCfg<16, 16>;
+    if (grid <= 0 || scan_px <= 0 || scan_py <= 0) return 0;
+    const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
+    const long long tail = groups % grid, slots = tail + (groups > tail ? grid : 0);  // split blocks, CTAs
+    return (size_t)slots * C::G * nwx * nwy * sizeof(float2);
+}
+
+size_t scan_gemm_cnt_bytes(int grid) { return (size_t)(grid > 0 ? grid : 1) * sizeof(int); }
 
 // rectangular windows (separate interpolation factors f_x != f_y): grouped kernel only
 template <int NWX>

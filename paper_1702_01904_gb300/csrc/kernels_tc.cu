@@ -265,7 +265,7 @@ struct TcCfg {
     static constexpr int PART_BYTES = 128 * KCMAX * 2;       // 128 pixels x KCMAX of one part
     static constexpr int STAGE_BYTES = PARTS * PART_BYTES;
     static constexpr int RING = STAGES * STAGE_BYTES;
-    static constexpr int PW = NW + 8;
+    static constexpr int PW = NW + 4;                         // window row pitch (bank spread)
     static constexpr int EW = NW >= 64 ? 2 : NW == 32 ? 8 : 16;  // windows per epilogue pass
     static constexpr int T = FS::T;
     static constexpr int RSLOTS = BLOCK / T, CW = BLOCK / T;
@@ -468,29 +468,13 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
         const int nvalid = meta[5];
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
             const int ne = min(C::EW, nvalid - e0);
-            // pixel pairs, VEC independent 16-byte loads in flight per thread
-            constexpr int VEC = 8;
-            for (int i0 = 0; i0 < ne * NW * NW / 2; i0 += BLOCK * VEC) {
-                float4 v[VEC];
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) {
-                    const int i = i0 + tid + k * BLOCK;
-                    if (i < ne * NW * NW / 2) {
-                        const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
-                        v[k] = __ldcg(reinterpret_cast<const float4 *>(a.win + ((size_t)blockIdx.x * G + meta[168 + e0 + e]) * (NW * NW) + u));
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) {
-                    const int i = i0 + tid + k * BLOCK;
-                    if (i < ne * NW * NW / 2) {
-                        const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
-                        float2 *d = win + (e * NW + u / NW) * PW + (u & (NW - 1));
-                        d[0] = make_float2(v[k].x, v[k].y);
-                        d[1] = make_float2(v[k].z, v[k].w);
-                    }
-                }
+            // the windows in 16-byte pieces (two pixels of a row), every piece in flight at once
+            for (int i = tid; i < ne * (NW * NW / 2); i += BLOCK) {
+                const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
+                cp_async16(win + (e * NW + u / NW) * PW + (u & (NW - 1)), a.win + ((size_t)blockIdx.x * G + meta[168 + e0 + e]) * (NW * NW) + u);
             }
+            cp_async_commit();
+            cp_async_wait<0>();
             __syncthreads();
             window_epilogue<NW, NW, BLOCK, C::EW, PW>(a, win, ex, twf, twf, ne, meta + 200 + e0, tid);
             __syncthreads();

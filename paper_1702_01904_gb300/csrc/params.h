@@ -89,7 +89,8 @@ struct ScanArgs {
     const void *S16;           // [ny_s * nx_s][kp] 16-bit (re, im) of each beam, zero-padded beams
                                // (split mode: [ny_s * nx_s][2][kp], value row then remainder row)
     const float *beam_scale;   // [B] power of two: S_b = S16_b * beam_scale[b]
-    float2 *win;               // window scratch [grid][probes per group][nw][nw]
+    float2 *win;               // window scratch [slots][probes per group][nw][nw]
+    int *win_cnt;              // FP32 GEMM scan: parts finished per split group (zero between launches)
     int *err;                  // device error word (a bounded wait that ran out sets bit 0)
     int kp;                    // K = 2 * roundup(B, 8)
     int scan_px, scan_py;      // probe raster, probe index = row * scan_px + col
@@ -135,7 +136,10 @@ bool scan_rect_supported(int nwx, int nwy, int n_beams);
 // not fit), launch, and the window scratch it needs ([grid][32][nwy][nwx] complex64)
 int scan_gemm_grid(int nwx, int nwy, int n_beams, int scan_px, int scan_py);
 cudaError_t launch_scan_gemm(int nwx, int nwy, int grid, const ScanArgs &a, cudaStream_t s);
-size_t scan_gemm_win_bytes(int nwx, int nwy, int grid);
+// window scratch of the FP32 GEMM scan: one slot per CTA plus one per split group of the last round
+size_t scan_gemm_win_bytes(int nwx, int nwy, int grid, int scan_px, int scan_py);
+// completion counters of the split groups (int[grid]; zeroed once, each launch leaves them zero)
+size_t scan_gemm_cnt_bytes(int grid);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
 cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);

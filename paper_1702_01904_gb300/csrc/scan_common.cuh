@@ -184,14 +184,17 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
     }
     __syncthreads();
     {
+        // columns like rows: T lanes of one warp per column, warp-local exchange (with the row pitch
+        // PW = 4 mod 16 float2, the T x 32/T lane block of a column access covers every bank pair
+        // twice: two wavefronts, the minimum for 8-byte accesses)
         using FS = FftShape<NWY>;
         using Fwd = FwdFft<NWY>;
-        constexpr int T = FS::T, E = FS::E, CW = BLOCK / T;
-        const int c = tid % CW, t = tid / CW;
-        ColExchange<FS::N1, FS::N2, CW> exc{ex, c};
+        constexpr int T = FS::T, E = FS::E, CSLOTS = BLOCK / T;
+        const int slot = tid / T, t = tid % T;
+        WarpExchange<FS::N1, FS::N2, T> exc{ex + slot * (FS::N1 * (FS::N2 + 1))};
 #pragma unroll 1
-        for (int c0 = 0; c0 < G * NWX; c0 += CW) {
-            const int col = c0 + c;
+        for (int c0 = 0; c0 < G * NWX; c0 += CSLOTS) {
+            const int col = c0 + slot;
             const bool ok = col < nwin * NWX;
             const int cc = ok ? col : col % NWX;
             float2 *w = win + (cc / NWX) * NWY * PW;
@@ -200,7 +203,6 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = w[Fwd::in_elem(r, t) * PW + x];
             Fwd::run(v, t, twy, a.tw, exc);
-            __syncthreads();
             if (ok) {
 #pragma unroll
                 for (int r = 0; r < E; ++r) w[Fwd::out_elem(r, t) * PW + x] = v[r];
