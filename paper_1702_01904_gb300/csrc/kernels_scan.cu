@@ -7,7 +7,7 @@
 //   3. beam sum psi(u) = sum_b alpha_b S_b(s + u) over the window, wrapped (Eq. PRISMfinal);
 //   4. 2-D FFT of the window in shared memory (row then column two-level FFTs);
 //   5. |Psi|^2 and the annular bins, fixed summation order, FP64 scale.
-// Three kernels: k_scan_gemm (8 x 4 raster blocks, the beam sum as a register-tiled complex GEMM on
+// Three kernels: k_scan_gemm (4 x 8 raster blocks, the beam sum as a register-tiled complex GEMM on
 // the union tile of their windows; the default), k_scan_grouped (4 consecutive probes, used when the
 // GEMM's coefficient block does not fit shared memory or for 8-pixel windows) and k_scan (one probe
 // per CTA, for 128-pixel windows and very large beam sets).
@@ -325,13 +325,15 @@ static bool grouped_fits(int n_beams) {
 }
 
 // ------------------------------------------------------------------ FP32 GEMM scan
-// The beam sum of Eq. PRISMfinal for an 8 x 4 block of the probe raster as a complex GEMM on the
+// The beam sum of Eq. PRISMfinal for a 4 x 8 block of the probe raster as a complex GEMM on the
 // union tile of their windows, on the CUDA cores in FP32: psi_p(r) = sum_b S_b(r) alpha_bp for the
 // tile pixels r (M) and the block's 32 probes (N), K = the beams.  The tile is streamed in M tiles
 // of 128 pixels; per M tile the beams pass through a 2-stage cp.async ring (KB beams x 128 pixels
 // per stage, one 8-byte copy per pixel and beam); thread (lane, warp) accumulates pixels lane +
-// 32 i (i < 4) for probes 4 warp + j (j < 4) in registers, so one 8-byte shared-memory load feeds
-// four complex MACs.  Finished M tiles are scattered to the per-CTA window scratch; the window FFT
+// 32 i (i < 4) for probes 4 warp + j (j < 4) -- raster row `warp` of the block -- in registers, so
+// one 8-byte shared-memory load feeds four complex MACs.  A warp skips the M tiles that lie wholly
+// above or below its row's windows (the union tile is NWY + 7 probe steps high, a row's windows
+// NWY).  Finished M tiles are scattered to the per-CTA window scratch; the window FFT
 // and bins are the shared epilogue.  A block whose union tile is larger than its windows together
 // runs probe by probe (only the warp holding that probe computes).
 // Work units: the blocks of all full rounds of the persistent grid run whole; the blocks of the
@@ -344,7 +346,7 @@ static bool grouped_fits(int n_beams) {
 // runs whole.
 template <int NWX, int NWY>
 struct GemmCfg {
-    static constexpr int GX = 8, GY = 4, G = GX * GY;
+    static constexpr int GX = 4, GY = 8, G = GX * GY;  // a warp's four probes: one raster row
     static constexpr int BLOCK = 256;
     static constexpr int KB = 32;                    // beams per ring stage
     static constexpr int STAGES = 2;
@@ -428,6 +430,22 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             // ring steps (M tile, beam chunk) of this unit: all, or a split block's share of M tiles
             const int ls0 = uni ? part * nmt / np * nkc : 0, ls1 = uni ? (part + 1) * nmt / np * nkc : nmt * nkc;
             const bool busy = uni || (sg >> 2) == warp;  // warps whose probes are computed
+            // union-tile rows the windows of this warp's probes cover (a warp's four probes share a
+            // raster row): M tiles wholly outside them hold none of its window pixels, so the warp
+            // skips their products
+            int wy0 = 0, wy1 = th - 1;
+            if (uni) {
+                wy0 = th;
+                wy1 = -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int p = 4 * warp + j;
+                    if (meta[136 + p] >= 0) {
+                        wy0 = min(wy0, meta[104 + p]);
+                        wy1 = max(wy1, meta[104 + p] + NWY - 1);
+                    }
+                }
+            }
             // loader: thread -> tile pixel m = tid % MT, beams kk = tid / MT, + 2, ...
             const int lm = tid & (MT - 1), lk = tid >> 7;
             auto load = [&](int ls) {
@@ -456,11 +474,12 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                 cp_async_wait<S - 2>();
                 __syncthreads();
                 load(ls + S - 1);  // its slot was last read in step ls - 1, which every thread has left
-                if (busy) {
+                const bool need = busy && (mt * MT + MT - 1) / tw >= wy0 && (mt * MT) / tw <= wy1;
+                if (need) {
                     const float2 *cur = ring + (ls % S) * (KB * MT);
                     const int b0 = c * kcs, bn = min(kcs, nb - b0);
                     const float4 *al = reinterpret_cast<const float4 *>(alpha + (size_t)b0 * G + 4 * warp);
-#pragma unroll 2
+#pragma unroll 4
                     for (int kk = 0; kk < bn; ++kk) {
                         const float4 a01 = al[(size_t)kk * (G / 2)], a23 = al[(size_t)kk * (G / 2) + 1];
                         const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                 }
                 if (c == nkc - 1) {
                     // M tile done: scatter tile pixel (ty, tx) to pixel (ty - oy_p, tx - ox_p) of probe p
-                    if (busy) {
+                    if (need) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int idx = mt * MT + lane + 32 * i;
