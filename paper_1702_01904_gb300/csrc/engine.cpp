@@ -385,6 +385,11 @@ struct prism_plan {
     size_t out_cap = 0;
     float *v_stage = nullptr;
     size_t v_cap = 0;
+    // host-buffer builds: potential chunks copied on their own stream, each chunk's transmission
+    // launched once its copy is done (the copy of later chunks overlaps the first slices' passes)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copy_start = nullptr;
+    std::vector<cudaEvent_t> copy_done;
     Tw64 tw64;
     // cached detector map
     double det_key[2] = {0, 0};
@@ -602,6 +607,12 @@ extern "C" void prism_plan_destroy(prism_plan *P) {
         cudaEventDestroy(pe.b);
     }
     for (auto e : P->ev_pool) cudaEventDestroy(e);
+    if (P->copy) {
+        cudaStreamSynchronize(P->copy);
+        cudaStreamDestroy(P->copy);
+    }
+    if (P->copy_start) cudaEventDestroy(P->copy_start);
+    for (auto e : P->copy_done) cudaEventDestroy(e);
     P->arena.release();
     cudaStreamSynchronize(P->stream);
     delete P;
@@ -654,7 +665,7 @@ static ColArgs col_args(const GridTables &T, float2 *wave, const float2 *prop_x,
     return a;
 }
 
-static int build_launches(prism_plan *P, const float *V_dev);
+static int build_launches(prism_plan *P, const float *V_dev, int per = 0);
 
 extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
@@ -664,18 +675,28 @@ extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
 }
 
 // transmission, every slice's row and column passes, ROW_OUT (and the 16-bit quantiser) of every
-// beam batch: kernel launches only (also captured into batch graphs)
-static int build_launches(prism_plan *P, const float *V_dev) {
+// beam batch: kernel launches only (also captured into batch graphs).  per > 0: the transmission
+// functions are made `per` slices at a time, each chunk after P->copy_done[chunk] (host-buffer
+// builds); otherwise all slices in one launch.
+static int build_launches(prism_plan *P, const float *V_dev, int per) {
     int rc;
     const prism_grid &g = P->g;
     const size_t px = (size_t)g.nx * g.ny;
-    // transmission functions t_p = exp(i sigma V_p) for all slices
     const double sigma_cycles = P->T.sigma / (2.0 * PI);
-    rc = plan_launch(P, PRISM_K_TRANSMIT, [&] { return launch_transmission(V_dev, P->t, (size_t)g.n_slices * px, sigma_cycles, P->stream); });
-    if (rc) return rc;
+    const bool chunked = per > 0;
+    if (!chunked) per = g.n_slices;
     for (int b0 = 0; b0 < P->nbeams; b0 += P->batch) {
         const int nb = std::min(P->batch, P->nbeams - b0);
         for (int p = 0; p < g.n_slices; ++p) {
+            if (b0 == 0 && p % per == 0) {
+                // transmission functions t_p = exp(i sigma V_p) of slices p ... p + per - 1
+                if (chunked) CUDA_TRY(cudaStreamWaitEvent(P->stream, P->copy_done[p / per], 0));
+                const int ns = std::min(per, g.n_slices - p);
+                rc = plan_launch(P, PRISM_K_TRANSMIT, [&] {
+                    return launch_transmission(V_dev + (size_t)p * px, P->t + (size_t)p * px, (size_t)ns * px, sigma_cycles, P->stream);
+                });
+                if (rc) return rc;
+            }
             RowArgs ra = row_args(P);
             ra.trans = P->t + (size_t)p * px;
             ra.n_rows = nb * g.ny;
@@ -726,8 +747,27 @@ extern "C" int prism_build_smatrix_host(prism_plan *P, const float *V_host) {
     const size_t bytes = (size_t)P->g.n_slices * P->g.nx * P->g.ny * sizeof(float);
     int rc = grow(P->arena, (void **)&P->v_stage, &P->v_cap, bytes);
     if (rc) return rc;
-    CUDA_TRY(cudaMemcpyAsync(P->v_stage, V_host, bytes, cudaMemcpyHostToDevice, P->stream));
-    return prism_build_smatrix(P, P->v_stage);
+    // the potential in up to 8 chunks of slices on the copy stream, after every earlier use of the
+    // staging buffer on the plan's stream
+    const int H = P->g.n_slices, per = (H + 7) / 8, nch = (H + per - 1) / per;
+    const size_t slice = (size_t)P->g.nx * P->g.ny;
+    if (!P->copy) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&P->copy, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&P->copy_start, cudaEventDisableTiming));
+    }
+    while ((int)P->copy_done.size() < nch) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        P->copy_done.push_back(e);
+    }
+    CUDA_TRY(cudaEventRecord(P->copy_start, P->stream));
+    CUDA_TRY(cudaStreamWaitEvent(P->copy, P->copy_start, 0));
+    for (int c = 0; c < nch; ++c) {
+        const size_t off = (size_t)c * per * slice, n = (size_t)std::min(per, H - c * per) * slice;
+        CUDA_TRY(cudaMemcpyAsync(P->v_stage + off, V_host + off, n * sizeof(float), cudaMemcpyHostToDevice, P->copy));
+        CUDA_TRY(cudaEventRecord(P->copy_done[c], P->copy));
+    }
+    return build_launches(P, P->v_stage, per);
 }
 
 // ------------------------------------------------------------------ scan

@@ -294,6 +294,31 @@ def test_deterministic_and_host_variants_identical():
     assert np.array_equal(a, b) and np.array_equal(a, host.numpy())
 
 
+def test_host_build_chunks_and_rebuild_identical():
+    # host-buffer builds copy the potential in chunks of slices (here 9 slices: chunks of 2, the
+    # last ragged) on their own stream; two builds back to back reuse the staging buffer, and a
+    # small HBM budget splits the beams into batches: every result equals the device-buffer build
+    g = grid_dict(64, 64, 8.0, 8.0, 9, 2.0, 2)
+    V1 = rand_v(9, 64, 64, 21)
+    V2 = rand_v(9, 64, 64, 22)
+    x0 = np.linspace(0.5, 7.5, 12)
+    y0 = np.linspace(1.0, 6.0, 12)
+    probe = P.make_probe(20.0)
+    full, ref = run_prism(g, V2, probe, x0, y0, DET)
+    # plan memory: t_p of every slice + the FP32 S + 1 MiB, then one wave per beam of a batch
+    small = 9 * 64 * 64 * 8 + full.info.n_beams * 32 * 32 * 8 + (1 << 20) + 5 * 64 * 64 * 8
+    for budget, batch in ((0, full.info.n_beams), (small, 5)):
+        sim = PrismSimulation(c_grid(g), budget)
+        assert sim.info.beam_batch == batch
+        sim.build_host(torch.from_numpy(V1).pin_memory())
+        sim.build_host(torch.from_numpy(V2).pin_memory())
+        host = torch.empty((12, DET["nbins"]), dtype=torch.float32).pin_memory()
+        sim.scan_host(probe, x0, y0, det_c(DET), host)
+        sim.sync()
+        assert np.array_equal(ref, host.numpy())
+        sim.close()
+
+
 def test_empty_scan_and_single_bin():
     g = grid_dict(64, 64, 8.0, 8.0, 1, 2.0, 2)
     V = rand_v(1, 64, 64, 11)
