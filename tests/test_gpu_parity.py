@@ -319,6 +319,31 @@ def test_host_build_chunks_and_rebuild_identical():
         sim.close()
 
 
+def test_scan_partition_invariant():
+    # a probe's result does not depend on which raster block or part of a split block computed it:
+    # a 160 x 64 raster (320 blocks of 4 x 8: 304 whole on the persistent grid, the last 16 split)
+    # equals the same raster scanned as 8 bands of 8 rows (40 blocks each, all split) and as 64
+    # single rows, bitwise; sampled probes match the oracle
+    g = grid_dict(64, 64, 8.0, 8.0, 3, 2.0, 2)
+    V = rand_v(3, 64, 64, 31)
+    xs, ys = np.meshgrid(np.arange(160) * 0.05, 0.5 + np.arange(64) * 0.11)
+    x0, y0 = xs.ravel(), ys.ravel()
+    probe = P.make_probe(20.0)
+    sim = PrismSimulation(c_grid(g))
+    sim.build(torch.from_numpy(V).cuda())
+    whole = sim.scan(probe, x0, y0, det_c(DET), px=160, py=64).cpu().numpy()
+    bands = np.concatenate([sim.scan(probe, x0[r * 1280:(r + 1) * 1280], y0[r * 1280:(r + 1) * 1280], det_c(DET),
+                                     px=160, py=8).cpu().numpy() for r in range(8)])
+    rows = np.concatenate([sim.scan(probe, x0[r * 160:(r + 1) * 160], y0[r * 160:(r + 1) * 160], det_c(DET),
+                                    px=160, py=1).cpu().numpy() for r in range(64)])
+    assert np.array_equal(whole, bands) and np.array_equal(whole, rows)
+    S, m, nn = O.smatrix_build(V, g)
+    sel = np.array([0, 159, 5000, 10079, 10239])
+    ref = O.prism_scan(S, m, nn, g, dict(alpha_mrad=20.0), DET, x0[sel], y0[sel])
+    assert_images_close(whole[sel], ref)
+    sim.close()
+
+
 def test_empty_scan_and_single_bin():
     g = grid_dict(64, 64, 8.0, 8.0, 1, 2.0, 2)
     V = rand_v(1, 64, 64, 11)
