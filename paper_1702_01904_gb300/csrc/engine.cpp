@@ -626,6 +626,8 @@ extern "C" int prism_sync(prism_plan *P) {
     CUDA_TRY(cudaMemcpy(&err, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         CUDA_TRY(cudaMemset(P->dev_err, 0, sizeof(int)));
+        // a scan whose wait ran out may have left split-block counters mid-count
+        if (P->win_cnt) CUDA_TRY(cudaMemset(P->win_cnt, 0, P->cnt_cap));
         return fail(PRISM_ERR_DEVICE, "a kernel's bounded wait ran out (device error word " + std::to_string(err) + ")");
     }
     return PRISM_OK;
@@ -852,6 +854,19 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     return PRISM_OK;
 }
 
+// completion counters of the blocks a scan splits over idle CTAs: int[grid], zeroed when allocated;
+// every launch leaves them at zero
+static int split_counters(prism_plan *P, ScanArgs &a, int grid) {
+    const size_t cb = scan_gemm_cnt_bytes(grid);
+    const bool fresh = !P->win_cnt || cb > P->cnt_cap;
+    int rc = grow(P->arena, (void **)&P->win_cnt, &P->cnt_cap, cb);
+    if (rc) return rc;
+    if (fresh) CUDA_TRY(cudaMemsetAsync(P->win_cnt, 0, P->cnt_cap, P->stream));
+    a.win = P->win;
+    a.win_cnt = P->win_cnt;
+    return PRISM_OK;
+}
+
 // FP32 mode: the CUDA-core scan kernels; 16-bit mode: the tensor-core kernel (persistent grid, its
 // window scratch grown on demand)
 // FP32: the GEMM scan over 8 x 4 raster blocks when its shared memory fits (grid > 0), else the
@@ -866,21 +881,13 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
         }
         int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, *grid, a.scan_px, a.scan_py));
         if (rc) return rc;
-        // the counters start at zero and every launch leaves them at zero
-        const size_t cb = scan_gemm_cnt_bytes(*grid);
-        const bool fresh = !P->win_cnt || cb > P->cnt_cap;
-        if ((rc = grow(P->arena, (void **)&P->win_cnt, &P->cnt_cap, cb))) return rc;
-        if (fresh) CUDA_TRY(cudaMemsetAsync(P->win_cnt, 0, P->cnt_cap, P->stream));
-        a.win = P->win;
-        a.win_cnt = P->win_cnt;
-        return PRISM_OK;
+        return split_counters(P, a, *grid);
     }
     *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), a.scan_px, a.scan_py);
     if (*grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
-    int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid));
+    int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid, a.scan_px, a.scan_py));
     if (rc) return rc;
-    a.win = P->win;
-    return PRISM_OK;
+    return split_counters(P, a, *grid);
 }
 
 static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {

@@ -274,6 +274,8 @@ struct TcCfg {
     static constexpr int EX = EXR > EXC ? EXR : EXC;
     static constexpr size_t EPI = (size_t)(EW * NW * PW + EX) * sizeof(float2);
     static constexpr int META = 256;                        // ints
+    static constexpr int META_LAST = META - 1;              // flag: this CTA completed a split block
+    static constexpr int MAXP = 16;                         // parts per split block at most
     static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16;
     static constexpr uint32_t TMEM_COLS = 2 * N;            // two accumulators
     __host__ __device__ static constexpr size_t bmat_bytes(int kp) { return (size_t)PARTS * kp * N * 2; }
@@ -331,7 +333,20 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
         if (a.err) atomicOr(a.err, 1);
     };
 
-    for (int grp = blockIdx.x; grp < ngroups && !dead; grp += gridDim.x) {
+    // work units as in the FP32 GEMM scan: the blocks of all full rounds whole, the blocks of the
+    // last, partial round split into up to MAXP parts of their M tiles (or probes) over the idle
+    // CTAs; a split block's windows in a scratch slot of its own ([0, tail)), the CTA slots after
+    const int tail = ngroups % gridDim.x, full = ngroups - tail;
+    const int parts = tail ? min(C::MAXP, (int)gridDim.x / tail) : 1;
+    for (int u = blockIdx.x; u < full + tail * parts && !dead; u += gridDim.x) {
+        int grp = u, part = 0, np = 1, slot = tail + blockIdx.x;
+        if (u >= full) {
+            const int tg = (u - full) / parts;
+            grp = full + tg;
+            part = u - full - tg * parts;
+            np = parts;
+            slot = tg;
+        }
         const int gy = grp / ngx, gx = grp - gy * ngx;
         // coefficient operand Bc, K-major core matrices: core (k/8, n/8) at ((k/8)(N/8) + n/8) * 128 B
         for (int i = tid; i < G * bp; i += BLOCK) {
@@ -371,17 +386,21 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
         const int nkc = (kp + C::KCMAX - 1) / C::KCMAX;
         const int kcs = ((kp + nkc - 1) / nkc + 15) & ~15;
         for (int sg = 0; sg < (uni ? 1 : G) && !dead; ++sg) {
-            if (!uni && meta[136 + sg] < 0) continue;
+            if (!uni && (meta[136 + sg] < 0 || sg % np != part)) continue;
             const int tw = uni ? meta[1] : NW, th = uni ? meta[2] : NW;
             const int tx0 = uni ? meta[3] : meta[8 + sg], ty0 = uni ? meta[4] : meta[40 + sg];
-            const int npx = tw * th, nmt = (npx + 127) / 128, nsteps = nmt * nkc;
+            const int npx = tw * th, nmt = (npx + 127) / 128;
+            // M tiles [m0, m1) of this unit: all, or a split block's share
+            const int m0 = uni ? part * nmt / np : 0, m1 = uni ? (part + 1) * nmt / np : nmt;
+            const int nsteps = (m1 - m0) * nkc;
+            if (nsteps == 0) continue;
             const uint32_t st0 = st;
             // A chunk of local step ls: thread -> pixel m = 16 warp + lane/2 of the M tile, K cores
             // kc = lane%2, lane%2 + 2, ...  (a lane pair reads one 32-byte sector of a pixel; a warp
             // writes 2 x 256 contiguous shared-memory bytes)
             auto load = [&](int ls) {
                 if (ls < nsteps) {
-                    const int mt = ls / nkc, c = ls - mt * nkc;
+                    const int mt = m0 + ls / nkc, c = ls % nkc;
                     const int k0 = c * kcs, kn = min(kcs, kp - k0);
                     const int m = warp * 16 + (lane >> 1);
                     const int idx = mt * 128 + m;
@@ -415,7 +434,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                             const bool act = uni ? meta[136 + p] >= 0 : p == sg;
                             const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
                             if (act && (unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
-                                a.win[((size_t)blockIdx.x * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
+                                a.win[((size_t)slot * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
                         }
                     }
                 }
@@ -431,7 +450,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                     dead = true;
                     break;
                 }
-                const int mt = ls / nkc, c = ls - mt * nkc;
+                const int mt = m0 + ls / nkc, c = ls % nkc;
                 if (tid == 0) {
                     tc::fence_after_sync();
                     const int k0 = c * kcs, kn = min(kcs, kp - k0);
@@ -453,17 +472,30 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 // ring slot (s + S - 1) % S was read by step s - 1: wait for its MMAs before refilling it
                 if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
                 load(ls + S - 1);
-                if (c == 0 && mt >= 1) drain(mt - 1);
+                if (c == 0 && mt > m0) drain(mt - 1);  // the previous tile of this unit
             }
             st = st0 + nsteps;
             if (dead) break;
             if (!tc::mbar_wait_bounded(&mbar[(st - 1) % S], ((st - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
-            drain(nmt - 1);
+            drain(m1 - 1);
             if (__syncthreads_or(my_fail)) dead = true;
         }
         cp_async_wait<0>();
         __syncthreads();  // window scratch written by this CTA is visible to all its threads
         if (dead) break;
+        if (np > 1) {
+            // split block: count this part done; the part that completes the block runs its epilogue
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const int last = atomicAdd(a.win_cnt + slot, 1) == np - 1;
+                if (last) a.win_cnt[slot] = 0;  // all parts counted: zero for the next launch
+                __threadfence();
+                meta[C::META_LAST] = last;
+            }
+            __syncthreads();
+            if (!meta[C::META_LAST]) continue;
+        }
         // epilogue: EW windows at a time through shared memory
         const int nvalid = meta[5];
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
@@ -471,7 +503,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
             // the windows in 16-byte pieces (two pixels of a row), every piece in flight at once
             for (int i = tid; i < ne * (NW * NW / 2); i += BLOCK) {
                 const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
-                cp_async16(win + (e * NW + u / NW) * PW + (u & (NW - 1)), a.win + ((size_t)blockIdx.x * G + meta[168 + e0 + e]) * (NW * NW) + u);
+                cp_async16(win + (e * NW + u / NW) * PW + (u & (NW - 1)), a.win + ((size_t)slot * G + meta[168 + e0 + e]) * (NW * NW) + u);
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -518,7 +550,7 @@ static int tc_grid(int kp, int scan_px, int scan_py) {
     const int per_sm = std::min(std::min(by_regs, by_smem), std::min(by_tmem, 2048 / C::BLOCK));
     if (per_sm < 1) return 0;
     const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
-    return (int)std::max<long long>(1, std::min<long long>(groups, (long long)per_sm * sms));
+    return (int)std::max<long long>(1, std::min<long long>(groups * C::MAXP, (long long)per_sm * sms));
 }
 
 template <int NW>
@@ -540,7 +572,13 @@ int scan_tc_grid(int nw, int kp, int mode, int scan_px, int scan_py) {
     }
 }
 
-size_t scan_tc_win_bytes(int nw, int grid) { return (size_t)grid * TcCfg<16>::G * nw * nw * sizeof(float2); }
+size_t scan_tc_win_bytes(int nw, int grid, int scan_px, int scan_py) {
+    using C = TcCfg<16>;
+    if (grid <= 0 || scan_px <= 0 || scan_py <= 0) return 0;
+    const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
+    const long long tail = groups % grid, slots = tail + (groups > tail ? grid : 0);  // split blocks, CTAs
+    return (size_t)slots * C::G * nw * nw * sizeof(float2);
+}
 static_assert(TcCfg<16>::G == TcCfg<32>::G && TcCfg<16>::G == TcCfg<64, true>::G, "one group size for every window");
 
 template <int NW, int MODE>
@@ -566,7 +604,7 @@ static cudaError_t tc_launch_mode(int mode, int grid, const ScanArgs &a, cudaStr
 }
 
 cudaError_t launch_scan_tc(int nw, int mode, int grid, const ScanArgs &a, cudaStream_t s) {
-    if (grid <= 0 || a.kp % 16 || a.kp < 2 * a.n_beams || !a.S16 || !a.beam_scale || !a.win) return cudaErrorInvalidValue;
+    if (grid <= 0 || a.kp % 16 || a.kp < 2 * a.n_beams || !a.S16 || !a.beam_scale || !a.win || !a.win_cnt) return cudaErrorInvalidValue;
     switch (nw) {
         case 16: return tc_launch_mode<16>(mode, grid, a, s);
         case 32: return tc_launch_mode<32>(mode, grid, a, s);

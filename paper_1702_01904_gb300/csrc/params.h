@@ -90,7 +90,7 @@ struct ScanArgs {
                                // (split mode: [ny_s * nx_s][2][kp], value row then remainder row)
     const float *beam_scale;   // [B] power of two: S_b = S16_b * beam_scale[b]
     float2 *win;               // window scratch [slots][probes per group][nw][nw]
-    int *win_cnt;              // FP32 GEMM scan: parts finished per split group (zero between launches)
+    int *win_cnt;              // parts finished per split block (zero between launches)
     int *err;                  // device error word (a bounded wait that ran out sets bit 0)
     int kp;                    // K = 2 * roundup(B, 8)
     int scan_px, scan_py;      // probe raster, probe index = row * scan_px + col
@@ -152,7 +152,8 @@ bool scan_tc_supported(int nw);
 // persistent grid of the tensor-core scan (resident CTAs, at most the probe groups), 0 if it does
 // not fit; window scratch bytes for that grid
 int scan_tc_grid(int nw, int kp, int mode, int scan_px, int scan_py);
-size_t scan_tc_win_bytes(int nw, int grid);
+// window scratch of the tensor-core scan: one slot per CTA plus one per split block of the last round
+size_t scan_tc_win_bytes(int nw, int grid, int scan_px, int scan_py);
 // autotuner launch shapes of ROW_STD (kind 0) and COL_STD (kind 1), N = 256 ... 2048 (kernels_tune.cu)
 int tune_shapes(int kind);
 const char *tune_shape_name(int kind, int v);

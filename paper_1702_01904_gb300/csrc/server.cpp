@@ -118,8 +118,24 @@ static size_t plan_bytes_estimate(const prism_grid &g) {
            s16 + ((size_t)2 << 20) + (size_t)g.n_slices * px * 4;
 }
 
+// window scratch a scan of this job can grow its plan's to: 32 complex windows per probe block, one
+// slot per resident CTA (at most 2 per SM) plus one per block split over idle CTAs
+static size_t scan_scratch_estimate(const Job &j) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 160;
+    }
+    const int ds = j.grid.downsample > 0 ? j.grid.downsample : 1;
+    const int fx = j.grid.f > 0 ? j.grid.f : 1, fy = j.grid.f_y > 0 ? j.grid.f_y : fx;
+    const size_t win = (size_t)(j.grid.nx / ds / fx) * (size_t)(j.grid.ny / ds / fy) * 8;
+    const size_t blocks = ((size_t)j.px + 3) / 4 * (((size_t)j.py + 3) / 4);  // bounds 4 x 8 and 8 x 4 blocks
+    const size_t cap = (size_t)2 * sms;
+    return (std::min(blocks, cap) + std::min(blocks, cap)) * 32 * win + cap * sizeof(int);
+}
+
 size_t prism_server::footprint(const Job &j, bool need_plan) const {
-    size_t b = j.out_bytes + (size_t)j.x0.size() * 16 + 4096;
+    size_t b = j.out_bytes + (size_t)j.x0.size() * 16 + 4096 + scan_scratch_estimate(j);
     if (need_plan) b += plan_bytes_estimate(j.grid);
     return b;
 }
