@@ -379,8 +379,9 @@ struct prism_plan {
     double *pos = nullptr;
     size_t pos_cap = 0;
     float2 *base = nullptr;
-    int *bin_buf = nullptr;
+    int *bin_buf = nullptr;    // window detector: CSR offsets, CSR indices, indices by rank
     size_t bin_cap = 0;
+    size_t bin_t_off = 0;      // element offset of the by-rank table in bin_buf
     float *out_stage = nullptr;
     size_t out_cap = 0;
     float *v_stage = nullptr;
@@ -813,8 +814,17 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     if (det && (P->det_nbins != det->nbins || P->det_key[0] != det->start_mrad || P->det_key[1] != det->step_mrad)) {
         std::vector<int> off, idx;
         detector_csr(P->nw, P->nwy, P->g.cell_x, P->g.cell_y, P->g.f, P->fy, lam, det, off, idx);
+        // the lists again by rank within the bin, so that threads summing consecutive bins read
+        // consecutive words
+        int maxlen = 0;
+        for (int k = 0; k < det->nbins; ++k) maxlen = std::max(maxlen, off[k + 1] - off[k]);
+        std::vector<int> idx_t((size_t)maxlen * det->nbins, 0);
+        for (int k = 0; k < det->nbins; ++k)
+            for (int i = 0; i < off[k + 1] - off[k]; ++i) idx_t[(size_t)i * det->nbins + k] = idx[off[k] + i];
+        P->bin_t_off = off.size() + idx.size();
         std::vector<int> all(off);
         all.insert(all.end(), idx.begin(), idx.end());
+        all.insert(all.end(), idx_t.begin(), idx_t.end());
         if ((rc = grow(P->arena, (void **)&P->bin_buf, &P->bin_cap, all.size() * sizeof(int)))) return rc;
         CUDA_TRY(cudaMemcpyAsync(P->bin_buf, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
         P->det_nbins = det->nbins;
@@ -832,6 +842,7 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     a.tw_fwd_y = P->tww_fy;
     a.bin_off = det ? P->bin_buf : nullptr;
     a.bin_idx = det ? P->bin_buf + det->nbins + 1 : nullptr;
+    a.bin_idx_t = det ? P->bin_buf + P->bin_t_off : nullptr;
     a.px_s = pxs;
     a.py_s = pys;
     a.shift_x = tl.sx;

@@ -73,6 +73,8 @@ struct ScanArgs {
     const float2 *tw_inv;      // (unused by the forward-only window FFT; kept for symmetry)
     const int *bin_off;        // [nbins+1] CSR offsets into bin_idx
     const int *bin_idx;        // window pixel indices (ky*nw + kx) grouped by bin
+    const int *bin_idx_t;      // the same lists by rank: entry i of bin k at [i * nbins + k] (rows of
+                               // the longest bin; bin k's list ends at bin_off[k+1] - bin_off[k])
     float *out;                // [P][nbins] annular bins, or NULL
     float *cbed;               // [P][nw][nw] full window diffraction patterns (FFT order), or NULL
     float acc_w;               // accumulate: out += acc_w * I (else out = I)

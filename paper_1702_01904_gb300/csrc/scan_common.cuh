@@ -221,17 +221,21 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
         }
     }
     // annular bins: one thread per (window, bin) walks the bin's pixel list with four interleaved
-    // FP32 partial sums (fixed order; relative error <= (n/4 + 2) 2^-24 for n pixels), FP64 scale
+    // FP32 partial sums (fixed order; relative error <= (n/4 + 2) 2^-24 for n pixels), FP64 scale.
+    // The lists are read by rank (entry i of bin k at bin_idx_t[i * nbins + k]), so the threads of
+    // consecutive bins read consecutive words.
     if (a.out) {
-        for (int j = tid; j < nwin * a.nbins; j += BLOCK) {
-            const int p = j / a.nbins, k = j - p * a.nbins;
+        const int nb = a.nbins;
+        for (int j = tid; j < nwin * nb; j += BLOCK) {
+            const int p = j / nb, k = j - p * nb;
             const float2 *w = win + p * NWY * PW;
-            const int e = __ldg(a.bin_off + k + 1);
+            const int e = __ldg(a.bin_off + k + 1) - __ldg(a.bin_off + k);
+            const int *ix = a.bin_idx_t + k;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int i = __ldg(a.bin_off + k);
+            int i = 0;
             for (; i + 4 <= e; i += 4) {
-                const int u0 = __ldg(a.bin_idx + i), u1 = __ldg(a.bin_idx + i + 1);
-                const int u2 = __ldg(a.bin_idx + i + 2), u3 = __ldg(a.bin_idx + i + 3);
+                const int u0 = __ldg(ix + i * nb), u1 = __ldg(ix + (i + 1) * nb);
+                const int u2 = __ldg(ix + (i + 2) * nb), u3 = __ldg(ix + (i + 3) * nb);
                 const float2 z0 = w[(u0 >> LNW) * PW + (u0 & (NWX - 1))], z1 = w[(u1 >> LNW) * PW + (u1 & (NWX - 1))];
                 const float2 z2 = w[(u2 >> LNW) * PW + (u2 & (NWX - 1))], z3 = w[(u3 >> LNW) * PW + (u3 & (NWX - 1))];
                 s0 = fmaf(z0.x, z0.x, fmaf(z0.y, z0.y, s0));
@@ -240,7 +244,7 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
                 s3 = fmaf(z3.x, z3.x, fmaf(z3.y, z3.y, s3));
             }
             for (; i < e; ++i) {
-                const int u = __ldg(a.bin_idx + i);
+                const int u = __ldg(ix + i * nb);
                 const float2 z = w[(u >> LNW) * PW + (u & (NWX - 1))];
                 s0 = fmaf(z.x, z.x, fmaf(z.y, z.y, s0));
             }
