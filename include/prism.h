@@ -307,6 +307,12 @@ typedef struct prism_tune_entry {
 int prism_plan_autotune(prism_plan *plan);
 int prism_plan_tune_result(const prism_plan *plan, int kind, prism_tune_entry *out);
 const char *prism_tune_shape_name(int kind, int shape);
+/* Pin the launch shape of one pass for the plan's later builds without timing: `shape` indexes the
+ * pass's list (prism_tune_shape_name), -1 restores the default launcher.  PRISM_ERR_INVALID for a
+ * NULL plan or a kind outside {PRISM_TUNE_ROW, PRISM_TUNE_COL}; PRISM_ERR_UNSUPPORTED for a shape
+ * not compiled for the plan's N, or one that stages through TMA when the plan holds no tensor map
+ * of its wave scratch.  Every shape computes bitwise the same result. */
+int prism_plan_set_tune_shape(prism_plan *plan, int kind, int shape);
 
 /* ---- batches of uneven cells: one captured CUDA graph ------------------------------
  *

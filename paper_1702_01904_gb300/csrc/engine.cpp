@@ -7,7 +7,9 @@
 // definition, so the integer outcome does not depend on the compiler fusing multiply-adds.
 #include "prism.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
 #include <algorithm>
 #include <cmath>
@@ -366,6 +368,8 @@ struct prism_plan {
     size_t win_cap = 0;
     int *win_cnt = nullptr;    // FP32 GEMM scan: completion counters of split groups
     size_t cnt_cap = 0;
+    CUtensorMap wave_map;      // the wave stack for the TMA-staged column pass
+    bool wave_map_ok = false;
     int *dev_err = nullptr;    // device error word
     int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
     double tune_ms[2][PRISM_TUNE_MAX_SHAPES];
@@ -444,6 +448,30 @@ static int grow(DevArena &A, void **p, size_t *cap, size_t need) {
 static int tc_mode(int prec) { return prec == PRISM_PRECISION_BF16 ? 1 : prec == PRISM_PRECISION_FP16X2 ? 2 : 0; }
 // 16-bit rows stored per pixel
 static int tc_parts(int prec) { return prec == PRISM_PRECISION_FP16X2 ? 2 : 1; }
+
+// Tensor map of a wave stack [batch][ny][nx] complex64 for the TMA-staged column pass: FP32 view
+// [batch][ny][2 nx], boxes of 16 floats (8 columns) x min(ny, 256) rows x 1.  The encoder comes from
+// the driver through the runtime's entry-point query; false (shape not used) if it is unavailable
+// or the stack breaks a rule of the map (16-byte aligned base, strides multiples of 16 bytes).
+static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    std::memset(&map, 0, sizeof(map));
+    if (!encode || !wave || ((uintptr_t)wave & 15) || nx < 8 || nx % 8 || ny < 1 || batch < 1) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * sizeof(float), (cuuint64_t)2 * nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {16, (cuuint32_t)std::min(ny, 256), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(wave), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes, void *cuda_stream, prism_plan **out) {
     if (!out) return fail(PRISM_ERR_INVALID, "out is NULL");
@@ -578,6 +606,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.alloc((void **)&P->dev_err, sizeof(int)))) return bail(rc);
     CUDA_TRY(cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->stream));
     if ((rc = A.alloc((void **)&P->wave, (size_t)batch * w_bytes))) return bail(rc);
+    P->wave_map_ok = encode_wave_map(P->wave_map, P->wave, g.nx, g.ny, batch);
     if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
     if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
     if ((rc = A.upload(&P->aa_kmax, P->T.aa_kmax))) return bail(rc);
@@ -670,6 +699,23 @@ static ColArgs col_args(const GridTables &T, float2 *wave, const float2 *prop_x,
 
 static int build_launches(prism_plan *P, const float *V_dev, int per = 0);
 
+// the column pass's launch shape when none is tuned or pinned: the TMA-staged shape at N = 1024
+// (the fastest there: 0.295 against 0.320 ms per launch for cp.async staging on the 1024^2 carbon
+// workload), when the plan holds the tensor map of its wave; otherwise the default launcher (-1)
+static int col_default_shape(const prism_plan *P) {
+    if (P->g.ny != 1024 || !P->wave_map_ok) return -1;
+    for (int v = 0; v < tune_shapes(PRISM_TUNE_COL); ++v)
+        if (tune_shape_needs_map(PRISM_TUNE_COL, v) && tune_shape_valid(PRISM_TUNE_COL, 1024, v)) return v;
+    return -1;
+}
+
+// the plan's wave stack in the column arguments of its build and autotuner launches
+static void col_wave_map(const prism_plan *P, ColArgs &ca) {
+    ca.wave_map = P->wave_map;
+    ca.wave_map_ok = P->wave_map_ok ? 1 : 0;
+    ca.err = P->dev_err;
+}
+
 extern "C" int prism_build_smatrix(prism_plan *P, const float *V_dev) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
     int rc;
@@ -715,9 +761,10 @@ static int build_launches(prism_plan *P, const float *V_dev, int per) {
             ca.batch = nb;
             ca.kx_half = P->T.kx_half;
             ca.band4 = P->T.band4;
+            col_wave_map(P, ca);
+            const int cs = P->tune_shape[1] >= 0 ? P->tune_shape[1] : col_default_shape(P);
             rc = plan_launch(P, PRISM_K_COL, [&] {
-                return P->tune_shape[1] >= 0 ? launch_col_shape(g.ny, P->tune_shape[1], ca, P->stream)
-                                             : launch_col(g.ny, COL_STD, ca, P->stream);
+                return cs >= 0 ? launch_col_shape(g.ny, cs, ca, P->stream) : launch_col(g.ny, COL_STD, ca, P->stream);
             });
             if (rc) return rc;
         }
@@ -1325,6 +1372,20 @@ struct TuneVal {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
+extern "C" int prism_plan_set_tune_shape(prism_plan *P, int kind, int shape) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "kind must be PRISM_TUNE_ROW or PRISM_TUNE_COL");
+    if (shape >= 0) {
+        const int n = kind == PRISM_TUNE_ROW ? P->g.nx : P->g.ny;
+        if (shape >= tune_shapes(kind) || !tune_shape_valid(kind, n, shape))
+            return fail(PRISM_ERR_UNSUPPORTED, std::string("launch shape ") + std::to_string(shape) + " is not compiled for N = " + std::to_string(n));
+        if (tune_shape_needs_map(kind, shape) && !P->wave_map_ok)
+            return fail(PRISM_ERR_UNSUPPORTED, "the plan holds no tensor map of its wave scratch (TMA-staged shape)");
+    }
+    P->tune_shape[kind] = shape < 0 ? -1 : shape;
+    return PRISM_OK;
+}
+
 extern "C" int prism_plan_autotune(prism_plan *P) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
     const prism_grid &g = P->g;
@@ -1349,7 +1410,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
         int best = -1;
         double best_ms = 0;
         for (int v = 0; v < tune_shapes(kind) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
-            if (!tune_shape_valid(kind, n, v)) continue;
+            if (!tune_shape_valid(kind, n, v) || (tune_shape_needs_map(kind, v) && !P->wave_map_ok)) continue;
             RowArgs ra = row_args(P);
             ra.trans = P->t;
             ra.n_rows = P->batch * g.ny;
@@ -1357,6 +1418,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
             ca.batch = P->batch;
             ca.kx_half = P->T.kx_half;
             ca.band4 = P->T.band4;
+            col_wave_map(P, ca);
             auto once = [&]() {
                 return kind == 0 ? launch_row_shape(g.nx, v, ra, P->stream) : launch_col_shape(g.ny, v, ca, P->stream);
             };
@@ -1397,7 +1459,8 @@ extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_
     const int n = kind == 0 ? P->g.nx : P->g.ny;
     out->n_shapes = std::min(tune_shapes(kind), PRISM_TUNE_MAX_SHAPES);
     out->chosen = P->tune_shape[kind];
-    out->default_shape = tune_shape_valid(kind, n, tune_default_shape(kind, n)) ? tune_default_shape(kind, n) : -1;
+    const int dc = kind == PRISM_TUNE_COL ? col_default_shape(P) : -1;
+    out->default_shape = dc >= 0 ? dc : tune_shape_valid(kind, n, tune_default_shape(kind, n)) ? tune_default_shape(kind, n) : -1;
     for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) out->ms[v] = P->tuned[kind] ? P->tune_ms[kind][v] : -1.0;
     return PRISM_OK;
 }

@@ -1,8 +1,9 @@
 // kernels_tune.cu -- the alternative launch shapes of the two multislice passes that the autotuner
 // times (ROW_STD and COL_STD, N = 256 ... 2048): the column shapes and the shape tables here, the
-// row shapes in kernels_tune_row.cu (a separate unit so that both compile in parallel).  A shape changes only how rows or columns are
-// spread over threads and whether the next row/tile is staged through shared memory with
-// cp.async; every shape computes bitwise the same transform.
+// row shapes in kernels_tune_row.cu (a separate unit so that both compile in parallel).  A shape
+// changes only how rows or columns are spread over threads and whether the next row/tile is staged
+// through shared memory (with cp.async, or for "W8, TMA" with tiled TMA loads completing on an
+// mbarrier); every shape computes bitwise the same transform.
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -19,18 +20,19 @@ using tune::N_COL;
 using tune::N_ROW;
 using tune::ROW_SHAPES;
 const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged"};
-const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W16", "W8, 2/SM", "W4, staged, 3/SM"};
+const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W8, TMA", "W8, 2/SM", "W4, staged, 3/SM"};
 
 template <int N, int I>
 constexpr bool col_ok() {
-    using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>;
-    return C::SMEM <= 227 * 1024 && C::THREADS <= 1024 && (size_t)C::MINB * (C::SMEM + 1024) <= 228 * 1024;
+    using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb, COL_SHAPES[I].tma>;
+    return C::SMEM <= 227 * 1024 && C::THREADS <= 1024 && (size_t)C::MINB * (C::SMEM + 1024) <= 228 * 1024 &&
+           (!C::TMA || (2 * C::W * 4 == 64 && N % C::BOXR == 0));
 }
 
 template <int N, int I>
 cudaError_t col_shape(const ColArgs &a, cudaStream_t s) {
     if (a.batch <= 0) return cudaSuccess;
-    return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb>(a, s);
+    return col_go<N, COL_STD, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb, COL_SHAPES[I].tma>(a, s);
 }
 
 template <int N>
@@ -72,10 +74,12 @@ int tune_default_shape(int kind, int n) {
     } else if (kind == 1) {
         const int w = n >= 2048 ? 4 : n >= 1024 ? 8 : 16;  // col_default_w, staged
         for (int v = 0; v < N_COL; ++v)
-            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg && COL_SHAPES[v].mb == 0) return v;
+            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg && COL_SHAPES[v].mb == 0 && !COL_SHAPES[v].tma) return v;
     }
     return -1;
 }
+
+bool tune_shape_needs_map(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].tma; }
 
 bool tune_shape_valid(int kind, int n, int v) {
     if (kind == 0) {

@@ -3,6 +3,7 @@
 // kernel parameter space (__grid_constant__), which keeps the 64 register-DFT twiddles in the
 // constant bank.
 #pragma once
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -39,6 +40,8 @@ struct RowArgs {
 
 // Column pass over columns of length ny.
 struct ColArgs {
+    CUtensorMap wave_map;      // TMA staging (STD): `wave` as FP32 [batch][ny][2 nx], boxes of 16 floats
+                               // (8 columns) x min(ny, 256) rows x 1; valid when wave_map_ok
     float2 *wave;              // [batch][ny][nx]
     float *inten;              // DETECT: [batch][ny][nx] |Psi|^2 (scaled later)
     const float2 *prop_x;      // [nx]  exp(-i pi lambda dz qx^2)
@@ -57,6 +60,8 @@ struct ColArgs {
     int band4;                 // 1: the aperture keeps |ky| < ny/4 on every column (aa_kmax < ny/4), so
                                // the column transforms may drop that band's complement at compile
                                // time (STD, DETECT)
+    int wave_map_ok;           // 1: wave_map describes `wave` (the TMA-staged shape may run)
+    int *err;                  // device error word: a TMA wait that ran out sets bit 1
     Tw64 tw;
 };
 
@@ -161,6 +166,7 @@ int tune_shapes(int kind);
 const char *tune_shape_name(int kind, int v);
 int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
+bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
 cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s);
 // smallest scan-window / FFT sizes the kernels are instantiated for

@@ -13,6 +13,7 @@
 
 #include "fft.cuh"
 #include "params.h"
+#include "tc.cuh"  // mbarrier and TMA helpers
 
 namespace prism {
 
@@ -284,13 +285,16 @@ template <int NY>
 constexpr int col_default_w() { return NY >= 2048 ? 4 : NY >= 1024 ? 8 : 16; }
 
 // WC interleaved columns per CTA, STG: cp.async staging of the next tile, MB: CTAs per SM the
-// register allocation must allow (0: the default rule) -- launch shape only
-template <int NY, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
+// register allocation must allow (0: the default rule), TM: the next tile staged by TMA instead
+// (NY / BOXR boxes of W columns x BOXR rows, one thread issues them) -- launch shape only
+template <int NY, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false>
 struct ColCfg {
     using FS = FftShape<NY>;
     static constexpr int W = WC;           // interleaved columns per CTA
     static constexpr int THREADS = FS::T * W;
-    static constexpr bool STAGE = STG;     // cp.async staging of the next tile
+    static constexpr bool TMA = TM;
+    static constexpr bool STAGE = STG || TM;  // staging of the next tile (cp.async or TMA)
+    static constexpr int BOXR = NY < 256 ? NY : 256;  // rows per TMA box
     static constexpr bool SMEM_TW = false; // stage twiddles in shared memory (else L1 broadcast loads)
     static constexpr bool PERSIST = true;  // grid = resident CTAs, each looping over tiles
     static constexpr int MINB = MB > 0 ? MB : (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
@@ -298,15 +302,28 @@ struct ColCfg {
     static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
+// TMA staging gives up after this many SM cycles (about a second) and reports it in the error word
+constexpr long long COL_TMA_WAIT_CYCLES = 2000000000LL;
+
 // BL: every column keeps at most |ky| < NY/4 (band4), known at compile time
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool BL = false>
-__global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, WC, STG, MB>::MINB) k_col(const __grid_constant__ ColArgs a) {
-    using C = ColCfg<NY, WC, STG, MB>;
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool BL = false, bool TM = false>
+__global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<NY, WC, STG, MB, TM>::MINB) k_col(const __grid_constant__ ColArgs a) {
+    using C = ColCfg<NY, WC, STG, MB, TM>;
     using FS = FftShape<NY>;
     using Fwd = FwdFft<NY>;
     using Inv = InvFft<NY>;
     constexpr int W = C::W, E = FS::E, THREADS = C::THREADS;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(128) float2 smem_c[];
+    float2 *smem = smem_c;
+    __shared__ __align__(8) uint64_t tbar;  // TMA staging: the tile's boxes have landed
+    uint32_t tphase = 0;
+    if constexpr (C::TMA) {
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&tbar, 1);
+            tc::fence_mbar_init();
+        }
+        __syncthreads();
+    }
     // FFT stage twiddles (forward, inverse), staging tile [NY][W], exchange
     const float2 *twf = a.tw_fwd, *twi = a.tw_inv;
     if constexpr (C::SMEM_TW) {
@@ -348,6 +365,15 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, W
     auto stage = [&](int tile) {
         int b, kx0;
         locate(tile, b, kx0);
+        if constexpr (C::TMA) {
+            // NY / BOXR boxes of the tile's rows; x = 2 kx0 floats, kx0 a multiple of W (16-byte rule)
+            if (threadIdx.x == 0) {
+                tc::fence_proxy_async();  // the buffer's generic reads (previous tile) before the async writes
+                tc::mbar_arrive_expect_tx(&tbar, (uint32_t)(NY * W * sizeof(float2)));
+                for (int y0 = 0; y0 < NY; y0 += C::BOXR) tc::tma_load_3d(stg + y0 * W, &a.wave_map, 2 * kx0, y0, b, &tbar);
+            }
+            return;
+        }
         const float2 *base = a.wave + (size_t)b * NY * a.nx + kx0;
         constexpr int PIECES = NY * W / 2;  // 16-byte pieces of the tile
 #pragma unroll
@@ -359,6 +385,13 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, W
         cp_async_commit();
     };
 
+    if constexpr (C::TMA) {
+        // TMA writes 128-byte aligned boxes: a misplaced buffer is reported, never copied into
+        if (tc::smem_u32(stg) & 127) {
+            if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
+            return;
+        }
+    }
     if constexpr (MODE != COL_PROBE && C::STAGE) stage(blockIdx.x);
     // without persistence every CTA owns exactly one tile and there is no loop (a loop would let
     // the compiler hoist the loop-invariant twiddle loads and hold them in registers)
@@ -383,8 +416,20 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB>::THREADS, ColCfg<NY, W
             }
         } else {
             if constexpr (C::STAGE) {
-                cp_async_wait_all();
-                __syncthreads();
+                if constexpr (C::TMA) {
+                    const uint32_t ph = tphase;
+                    tphase ^= 1;
+                    const bool ok = tc::mbar_wait_bounded(&tbar, ph, COL_TMA_WAIT_CYCLES);
+                    if (__syncthreads_or(!ok)) {
+                        // report, give the boxes in flight one more bounded wait, leave (every thread)
+                        if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
+                        tc::mbar_wait_bounded(&tbar, ph, COL_TMA_WAIT_CYCLES);
+                        return;
+                    }
+                } else {
+                    cp_async_wait_all();
+                    __syncthreads();
+                }
 #pragma unroll
                 for (int r = 0; r < E; ++r) v[r] = stg[Fwd::in_elem(r, t) * W + c];
                 __syncthreads();  // the staging buffer is refilled next
@@ -442,27 +487,29 @@ static inline long long col_tiles(int nx, int w, int kx_half, int batch) {
     return (long long)(lo + (nx / w - hs)) * batch;
 }
 
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0>
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false>
 static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
-    using C = ColCfg<NY, WC, STG, MB>;
-    if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024) {
+    using C = ColCfg<NY, WC, STG, MB, TM>;
+    if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024 || (TM && (MODE != COL_STD || 2 * WC * 4 != 64 || NY % C::BOXR))) {
         return cudaErrorInvalidConfiguration;
     } else {
         if (a.nx % C::W) return cudaErrorInvalidValue;
+        // the map must describe this wave stack with boxes of W columns x BOXR rows
+        if (TM && !a.wave_map_ok) return cudaErrorInvalidValue;
         int grid = 0;
         const long long work = col_tiles(a.nx, C::W, a.kx_half, a.batch);
         cudaError_t e;
         if constexpr (NY >= 64 && MODE != COL_PROBE) {
             if (a.band4) {
-                e = persistent_grid(k_col<NY, MODE, WC, STG, MB, true>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
+                e = persistent_grid(k_col<NY, MODE, WC, STG, MB, true, TM>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
                 if (e != cudaSuccess) return e;
-                k_col<NY, MODE, WC, STG, MB, true><<<grid, C::THREADS, C::SMEM, s>>>(a);
+                k_col<NY, MODE, WC, STG, MB, true, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
                 return cudaGetLastError();
             }
         }
-        e = persistent_grid(k_col<NY, MODE, WC, STG, MB, false>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
+        e = persistent_grid(k_col<NY, MODE, WC, STG, MB, false, TM>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
         if (e != cudaSuccess) return e;
-        k_col<NY, MODE, WC, STG, MB, false><<<grid, C::THREADS, C::SMEM, s>>>(a);
+        k_col<NY, MODE, WC, STG, MB, false, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
         return cudaGetLastError();
     }
 }

@@ -121,6 +121,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// arrive on the barrier and add `bytes` to the transaction count its phase waits for (the
+// asynchronous copies that complete_tx on it supply those bytes)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// --- TMA: one box of a 3-D tiled tensor map into shared memory, completing on `mbar`.  The
+// innermost coordinate c0 times the element size must be a multiple of 16 bytes, and `dst` 128-byte
+// aligned; the map lives in kernel parameter space (a __grid_constant__ argument).
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int c0, int c1, int c2, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
+        : "memory");
+}
 // bounded wait: false if the phase did not complete within `limit_cycles` SM clock cycles
 // (try_wait itself suspends the thread for a short hardware-defined time between checks)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit_cycles) {

@@ -6,13 +6,14 @@ namespace prism {
 namespace tune {
 
 struct Shape {
-    int a;     // row pass: threads per CTA; column pass: interleaved columns per CTA
-    bool stg;  // cp.async staging of the next row / tile
-    int mb;    // column pass: CTAs per SM the registers must allow (0: default rule)
+    int a;      // row pass: threads per CTA; column pass: interleaved columns per CTA
+    bool stg;   // cp.async staging of the next row / tile
+    int mb;     // column pass: CTAs per SM the registers must allow (0: default rule)
+    bool tma;   // column pass: the next tile staged by TMA (needs the plan's tensor map of the wave)
 };
-constexpr Shape ROW_SHAPES[] = {{128, false, 0}, {256, false, 0}, {128, true, 0}, {256, true, 0}};
-constexpr Shape COL_SHAPES[] = {{4, true, 0}, {8, true, 0}, {16, true, 0}, {4, false, 0}, {8, false, 0}, {16, false, 0},
-                                {8, false, 2}, {4, true, 3}};
+constexpr Shape ROW_SHAPES[] = {{128, false, 0, false}, {256, false, 0, false}, {128, true, 0, false}, {256, true, 0, false}};
+constexpr Shape COL_SHAPES[] = {{4, true, 0, false},  {8, true, 0, false},  {16, true, 0, false}, {4, false, 0, false},
+                                {8, false, 0, false}, {8, false, 0, true},  {8, false, 2, false}, {4, true, 3, false}};
 constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
 constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
 

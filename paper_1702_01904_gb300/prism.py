@@ -48,7 +48,7 @@ EXPORTED = [
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
     "prism_selftest_tcgen05",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
-    "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name",
+    "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
 ]
 
 
@@ -150,6 +150,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_autotune": (c_int, [P]),
         "prism_plan_tune_result": (c_int, [P, c_int, POINTER(PrismTuneEntry)]),
         "prism_tune_shape_name": (c_char_p, [c_int, c_int]),
+        "prism_plan_set_tune_shape": (c_int, [P, c_int, c_int]),
         "prism_batch_run": (c_int, [P]),
         "prism_batch_sync": (c_int, [P]),
         "prism_batch_info_get": (c_int, [P, POINTER(PrismBatchInfo)]),
@@ -445,3 +446,7 @@ def prism_plan_tune_result(plan, kind):
 
 def prism_tune_shape_name(kind, shape):
     return load().prism_tune_shape_name(kind, shape).decode()
+
+
+def prism_plan_set_tune_shape(plan, kind, shape):
+    _check(load().prism_plan_set_tune_shape(plan, kind, shape))

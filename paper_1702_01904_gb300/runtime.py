@@ -100,6 +100,10 @@ class PrismSimulation:
         P.prism_plan_autotune(self.plan)
         return self.tune_result()
 
+    def set_shape(self, kind, shape):
+        """Pin one pass's launch shape by index (prism_plan_set_tune_shape); -1 restores the default."""
+        P.prism_plan_set_tune_shape(self.plan, kind, shape)
+
     def tune_result(self):
         out = {}
         for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col")):

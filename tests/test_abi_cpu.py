@@ -116,3 +116,12 @@ def test_plan_arguments_rejected_before_any_device_call():
     assert status(f_y=3) == P.PRISM_ERR_INVALID            # 64 not divisible by 2 * 3
     assert status(f_y=1, precision=P.PRISM_PRECISION_FP16) == P.PRISM_ERR_UNSUPPORTED  # 16 x 32 window
     assert status(f=1, f_y=8) == P.PRISM_ERR_UNSUPPORTED  # 32 x 4 window
+
+
+def test_tune_shape_arguments_rejected_without_a_device():
+    """prism_plan_set_tune_shape checks its plan and pass on the host."""
+    with pytest.raises(P.PrismError) as e:
+        P.prism_plan_set_tune_shape(None, P.PRISM_TUNE_COL, 0)
+    assert e.value.status == P.PRISM_ERR_INVALID
+    names = [P.prism_tune_shape_name(P.PRISM_TUNE_COL, v) for v in range(P.PRISM_TUNE_MAX_SHAPES)]
+    assert "W8, TMA" in names and "W8, staged" in names

@@ -58,6 +58,33 @@ def test_autotuned_plan_is_bitwise_identical(n, cell, f, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("n,cell,f", [(1024, 50.0, 8), (512, 32.0, 8)])
+def test_every_column_shape_is_bitwise_identical(n, cell, f):
+    # each compiled column-pass shape pinned in turn -- cp.async-staged, unstaged and TMA-staged
+    # tiles, 4 to 16 columns per CTA -- builds the same S-matrix, bit for bit
+    grid = P.make_grid(n, n, 2, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0)
+    V = rand_v(2, n, 12)
+    ref = PrismSimulation(grid)
+    ref.build(V)
+    S0 = ref.smatrix().cpu().numpy()
+    ref.close()
+    ran = []
+    for v in range(P.PRISM_TUNE_MAX_SHAPES):
+        sim = PrismSimulation(grid)
+        try:
+            sim.set_shape(P.PRISM_TUNE_COL, v)
+        except P.PrismError as e:
+            assert e.status == P.PRISM_ERR_UNSUPPORTED
+            sim.close()
+            continue
+        sim.build(V)
+        sim.sync()
+        assert np.array_equal(S0, sim.smatrix().cpu().numpy()), P.prism_tune_shape_name(P.PRISM_TUNE_COL, v)
+        ran.append(P.prism_tune_shape_name(P.PRISM_TUNE_COL, v))
+        sim.close()
+    assert "W8, TMA" in ran and "W8, staged" in ran
+
+
 def test_small_grid_has_only_the_default_shape():
     grid = P.make_grid(64, 64, 2, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0)
     sim = PrismSimulation(grid)
