@@ -677,6 +677,7 @@ static RowArgs row_args(prism_plan *P) {
     a.f_y = P->fy;
     a.downsample = P->g.downsample;
     a.kx_half = P->T.kx_half;
+    a.err = P->dev_err;
     a.tw = P->tw64;
     return a;
 }

@@ -19,7 +19,7 @@ using tune::COL_SHAPES;
 using tune::N_COL;
 using tune::N_ROW;
 using tune::ROW_SHAPES;
-const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged"};
+const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged", "128 thr, TMA"};
 const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W8, TMA", "W8, 2/SM", "W4, staged, 3/SM"};
 
 template <int N, int I>
@@ -70,7 +70,7 @@ int tune_default_shape(int kind, int n) {
     if (kind == 0) {
         const int thr = n >= 512 ? 128 : 256;  // row_default_threads, unstaged
         for (int v = 0; v < N_ROW; ++v)
-            if (ROW_SHAPES[v].a == thr && !ROW_SHAPES[v].stg) return v;
+            if (ROW_SHAPES[v].a == thr && !ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma) return v;
     } else if (kind == 1) {
         const int w = n >= 2048 ? 4 : n >= 1024 ? 8 : 16;  // col_default_w, staged
         for (int v = 0; v < N_COL; ++v)

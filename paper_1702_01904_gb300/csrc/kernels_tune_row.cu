@@ -15,14 +15,14 @@ using tune::ROW_SHAPES;
 
 template <int N, int I>
 constexpr bool row_ok() {
-    using C = RowCfg<N, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>;
-    return C::SMEM <= 227 * 1024 && ROW_SHAPES[I].a % C::T == 0 && ROW_SHAPES[I].a <= 1024;
+    using C = RowCfg<N, ROW_SHAPES[I].a, ROW_SHAPES[I].stg, ROW_SHAPES[I].tma>;
+    return C::SMEM <= 227 * 1024 && ROW_SHAPES[I].a % C::T == 0 && ROW_SHAPES[I].a <= 1024 && (!C::TMA || C::T == 32);
 }
 
 template <int N, int I>
 cudaError_t row_shape(const RowArgs &a, cudaStream_t s) {
     if (a.n_rows <= 0) return cudaSuccess;
-    return row_go<N, ROW_STD, ROW_SHAPES[I].a, ROW_SHAPES[I].stg>(a, s);
+    return row_go<N, ROW_STD, ROW_SHAPES[I].a, ROW_SHAPES[I].stg, ROW_SHAPES[I].tma>(a, s);
 }
 
 template <int N>
@@ -32,12 +32,13 @@ cudaError_t row_n(int v, const RowArgs &a, cudaStream_t s) {
         case 1: return row_shape<N, 1>(a, s);
         case 2: return row_shape<N, 2>(a, s);
         case 3: return row_shape<N, 3>(a, s);
+        case 4: return row_shape<N, 4>(a, s);
     }
     return cudaErrorInvalidValue;
 }
 template <int N>
 bool row_valid_n(int v) {
-    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>()};
+    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>(), row_ok<N, 4>()};
     return v >= 0 && v < N_ROW && ok[v];
 }
 }  // namespace

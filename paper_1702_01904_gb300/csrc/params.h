@@ -35,6 +35,7 @@ struct RowArgs {
                                // non-zero (the propagator's anti-aliasing aperture zeroes the rest):
                                // loads there are replaced by exact zeros and stores are skipped
                                // (STD, PLANE, OUT); 0: every kx
+    int *err;                  // device error word: a TMA wait that ran out sets bit 2
     Tw64 tw;
 };
 

@@ -68,14 +68,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int NX>
 constexpr int row_default_threads() { return NX >= 512 ? 128 : 256; }
 
-// THR threads per CTA, STG: cp.async staging of the next row (launch shape only: every variant
-// computes bitwise the same rows)
-template <int NX, int THR = row_default_threads<NX>(), bool STG = false>
+// THR threads per CTA, STG: cp.async staging of the next row, TM: bulk-copy (TMA) staging of the
+// next row's two kept quarters (launch shape only: every variant computes bitwise the same rows)
+template <int NX, int THR = row_default_threads<NX>(), bool STG = false, bool TM = false>
 struct RowCfg {
     using FS = FftShape<NX>;
     static constexpr int T = FS::T;
     static constexpr int E = FS::E;
     static constexpr bool STAGE = STG;        // cp.async staging of the next row
+    static constexpr bool TMA = TM;           // bulk staging of [0, NX/4) and [3NX/4, NX) (one slot = one warp)
     static constexpr bool PERSIST = true;     // grid = resident CTAs, each looping over rows
     static constexpr bool T_EARLY = E <= 32;  // E extra complex registers for t_p
     static constexpr int THREADS = THR;
@@ -83,19 +84,30 @@ struct RowCfg {
     static constexpr int EXF = FS::N1 * (FS::N2 + 1);
     static constexpr int EXI = FS::N2 * (FS::N1 + 1);
     static constexpr int EX = EXF > EXI ? EXF : EXI;
-    static constexpr int SLOT_F2 = (STAGE ? NX : 0) + EX;  // staging row + exchange, float2
+    static constexpr int SLOT_F2 = (TMA ? NX / 2 : STAGE ? NX : 0) + EX;  // staging row + exchange, float2
     static constexpr size_t SMEM = (size_t)(2 * NX + SLOTS * SLOT_F2) * sizeof(float2);
 };
 
+// bulk-staged rows give up after this many SM cycles (about a second) and report it
+constexpr long long ROW_TMA_WAIT_CYCLES = 2000000000LL;
+
 // BL: the kept columns are exactly |kx| < NX/4 (kx_half == NX/4), known at compile time
-template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool BL = false>
+template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool BL = false, bool TM = false>
 __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) {
-    using C = RowCfg<NX, THR, STG>;
+    using C = RowCfg<NX, THR, STG, TM>;
     using FS = FftShape<NX>;
     using Fwd = FwdFft<NX>;
     using Inv = InvFft<NX>;
     constexpr int T = C::T, E = FS::E;
+    static_assert(!TM || (BL && T == 32 && MODE != ROW_PLANE), "bulk staging: compile-time band, one slot per warp");
     extern __shared__ float2 smem[];
+    __shared__ __align__(8) uint64_t rbar[C::SLOTS];  // TM: a slot's next row has landed
+    uint32_t rphase = 0;
+    const int slot = threadIdx.x / T, t = threadIdx.x % T;
+    if constexpr (C::TMA) {
+        if (t == 0) tc::mbar_init(&rbar[slot], 1);
+        tc::fence_mbar_init();
+    }
     // FFT stage twiddles (forward, inverse) in shared memory, then one region per slot
     float2 *twf = smem, *twi = smem + NX;
     for (int i = threadIdx.x; i < NX; i += C::THREADS) {
@@ -103,9 +115,8 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
         twi[i] = a.tw_inv[i];
     }
     __syncthreads();
-    const int slot = threadIdx.x / T, t = threadIdx.x % T;
     float2 *stg = smem + 2 * NX + slot * C::SLOT_F2;
-    float2 *exbuf = stg + (C::STAGE ? NX : 0);
+    float2 *exbuf = stg + (C::TMA ? NX / 2 : C::STAGE ? NX : 0);
     WarpExchange<FS::N1, FS::N2, T> exF{exbuf};
     WarpExchange<FS::N2, FS::N1, T> exI{exbuf};
     const int stride = gridDim.x * C::SLOTS;
@@ -144,6 +155,20 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
         cp_async_commit();
     };
 
+    // bulk (TMA) staging of a row's two kept quarters, [0, NX/4) then [3NX/4, NX), into the slot's
+    // buffer: lane 0 arms the slot's barrier with the byte count and issues both copies
+    auto bulk = [&](int row) {
+        if (t == 0) {
+            int b, y;
+            locate(row, b, y);
+            const float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
+            tc::fence_proxy_async();  // the buffer's generic reads (previous row) before the async writes
+            tc::mbar_arrive_expect_tx(&rbar[slot], (uint32_t)(NX / 2 * sizeof(float2)));
+            tc::bulk_load(stg, w, (uint32_t)(NX / 4 * sizeof(float2)), &rbar[slot]);
+            tc::bulk_load(stg + NX / 4, w + 3 * NX / 4, (uint32_t)(NX / 4 * sizeof(float2)), &rbar[slot]);
+        }
+    };
+    if constexpr (C::TMA) bulk(row0);
     if constexpr (MODE != ROW_PLANE && C::STAGE) stage(row0);
     for (int it = 0; it < iters; ++it) {
         const int row = row0 + it * stride;
@@ -173,7 +198,29 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                 v[r] = cmul(make_float2(c, s), __ldcg(tp + x));
             }
         } else {
-            if constexpr (C::STAGE) {
+            if constexpr (C::TMA) {
+                const uint32_t ph = rphase;
+                rphase ^= 1;
+                const bool ok = tc::mbar_wait_bounded(&rbar[slot], ph, ROW_TMA_WAIT_CYCLES);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    // report, give the copies in flight one more bounded wait, leave (the whole warp)
+                    if (t == 0 && a.err) atomicOr(a.err, 4);
+                    tc::mbar_wait_bounded(&rbar[slot], ph, ROW_TMA_WAIT_CYCLES);
+                    return;
+                }
+                static_for<E>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    constexpr int cls = BandClass<Inv, NX>::of(r, true);
+                    // a register's elements lie in one 32-aligned block, so one quarter holds them all
+                    constexpr int off = Inv::in_elem(r, 0) < NX / 4 ? 0 : NX / 2;
+                    const int e = Inv::in_elem(r, t);
+                    if constexpr (cls == BAND_OUT) v[r] = make_float2(0.f, 0.f);
+                    else if constexpr (cls == BAND_IN) v[r] = stg[e - off];
+                    else v[r] = keep(e) ? stg[e - off] : make_float2(0.f, 0.f);
+                });
+                __syncwarp();  // the buffer is refilled next
+                if (it + 1 < iters) bulk(row + stride);
+            } else if constexpr (C::STAGE) {
                 cp_async_wait_all();
                 __syncwarp();
                 static_for<E>([&](auto rc) {
@@ -252,26 +299,31 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
     }
 }
 
-template <int NX, int MODE, int THR, bool STG, bool BL>
+template <int NX, int MODE, int THR, bool STG, bool BL, bool TM = false>
 static cudaError_t row_go_bl(const RowArgs &a, cudaStream_t s) {
-    using C = RowCfg<NX, THR, STG>;
+    using C = RowCfg<NX, THR, STG, TM>;
     int grid = 0;
-    cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG, BL>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
+    cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG, BL, TM>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
                                     &grid, C::PERSIST);
     if (e != cudaSuccess) return e;
-    k_row<NX, MODE, THR, STG, BL><<<grid, C::THREADS, C::SMEM, s>>>(a);
+    k_row<NX, MODE, THR, STG, BL, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false>
+// TM: bulk staging where it applies (the compile-time band, one slot per warp, rows read from the
+// wave); elsewhere the same shape without it, which computes the same rows
+template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool TM = false>
 static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
-    using C = RowCfg<NX, THR, STG>;
+    using C = RowCfg<NX, THR, STG, TM>;
     if constexpr (C::SMEM > 227 * 1024 || THR % C::T != 0 || THR > 1024) {
         return cudaErrorInvalidConfiguration;
     } else {
         // the compile-time band for the default aperture (aa_frac 1/2 on a square grid: |kx| < NX/4)
         if constexpr (NX >= 64) {
-            if (a.kx_half * 4 == NX) return row_go_bl<NX, MODE, THR, STG, true>(a, s);
+            if (a.kx_half * 4 == NX) {
+                if constexpr (TM && C::T == 32 && MODE != ROW_PLANE) return row_go_bl<NX, MODE, THR, STG, true, true>(a, s);
+                else return row_go_bl<NX, MODE, THR, STG, true>(a, s);
+            }
         }
         return row_go_bl<NX, MODE, THR, STG, false>(a, s);
     }

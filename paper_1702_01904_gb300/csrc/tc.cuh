@@ -136,6 +136,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int c0, 
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
         : "memory");
 }
+// --- bulk copy (TMA, no tensor map): `bytes` (a multiple of 16) from global to shared memory, both
+// 16-byte aligned, completing on `mbar`
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
 // bounded wait: false if the phase did not complete within `limit_cycles` SM clock cycles
 // (try_wait itself suspends the thread for a short hardware-defined time between checks)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit_cycles) {

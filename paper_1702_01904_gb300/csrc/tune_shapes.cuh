@@ -9,9 +9,11 @@ struct Shape {
     int a;      // row pass: threads per CTA; column pass: interleaved columns per CTA
     bool stg;   // cp.async staging of the next row / tile
     int mb;     // column pass: CTAs per SM the registers must allow (0: default rule)
-    bool tma;   // column pass: the next tile staged by TMA (needs the plan's tensor map of the wave)
+    bool tma;   // the next tile (column pass, needs the plan's tensor map of the wave) or row (row
+                // pass, bulk copies of its kept quarters) staged by TMA
 };
-constexpr Shape ROW_SHAPES[] = {{128, false, 0, false}, {256, false, 0, false}, {128, true, 0, false}, {256, true, 0, false}};
+constexpr Shape ROW_SHAPES[] = {{128, false, 0, false}, {256, false, 0, false}, {128, true, 0, false}, {256, true, 0, false},
+                                {128, false, 0, true}};
 constexpr Shape COL_SHAPES[] = {{4, true, 0, false},  {8, true, 0, false},  {16, true, 0, false}, {4, false, 0, false},
                                 {8, false, 0, false}, {8, false, 0, true},  {8, false, 2, false}, {4, true, 3, false}};
 constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);

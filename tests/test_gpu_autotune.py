@@ -59,30 +59,41 @@ def test_autotuned_plan_is_bitwise_identical(n, cell, f, prec):
 
 
 @pytest.mark.parametrize("n,cell,f", [(1024, 50.0, 8), (512, 32.0, 8)])
-def test_every_column_shape_is_bitwise_identical(n, cell, f):
-    # each compiled column-pass shape pinned in turn -- cp.async-staged, unstaged and TMA-staged
-    # tiles, 4 to 16 columns per CTA -- builds the same S-matrix, bit for bit
+@pytest.mark.parametrize("kind", [P.PRISM_TUNE_ROW, P.PRISM_TUNE_COL])
+def test_every_shape_is_bitwise_identical(n, cell, f, kind):
+    # each compiled shape of a pass pinned in turn -- threads or columns per CTA, unstaged,
+    # cp.async-staged and TMA-staged rows or tiles, register caps -- builds the same S-matrix and
+    # detector stack, bit for bit
     grid = P.make_grid(n, n, 2, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0)
     V = rand_v(2, n, 12)
+    x0 = np.linspace(0.0, cell, 9, endpoint=False)
+    y0 = np.linspace(1.0, 3.0, 9)
+    probe = P.make_probe(20.0)
     ref = PrismSimulation(grid)
     ref.build(V)
     S0 = ref.smatrix().cpu().numpy()
+    o0 = ref.scan(probe, x0, y0, DET).cpu().numpy()
     ref.close()
     ran = []
     for v in range(P.PRISM_TUNE_MAX_SHAPES):
         sim = PrismSimulation(grid)
         try:
-            sim.set_shape(P.PRISM_TUNE_COL, v)
+            sim.set_shape(kind, v)
         except P.PrismError as e:
             assert e.status == P.PRISM_ERR_UNSUPPORTED
             sim.close()
             continue
         sim.build(V)
+        out = sim.scan(probe, x0, y0, DET).cpu().numpy()
         sim.sync()
-        assert np.array_equal(S0, sim.smatrix().cpu().numpy()), P.prism_tune_shape_name(P.PRISM_TUNE_COL, v)
-        ran.append(P.prism_tune_shape_name(P.PRISM_TUNE_COL, v))
+        name = P.prism_tune_shape_name(kind, v)
+        assert np.array_equal(S0, sim.smatrix().cpu().numpy()) and np.array_equal(o0, out), name
+        ran.append(name)
         sim.close()
-    assert "W8, TMA" in ran and "W8, staged" in ran
+    if kind == P.PRISM_TUNE_COL:
+        assert "W8, TMA" in ran and "W8, staged" in ran
+    else:
+        assert "128 thr" in ran and ("128 thr, TMA" in ran) == (n >= 1024)
 
 
 def test_small_grid_has_only_the_default_shape():
