@@ -288,7 +288,8 @@ void prism_server_destroy(prism_server *server);
  *
  * The build is two streaming passes per slice (Calculation Time section: its cost grows with
  * beams x slices x N^2); their fastest launch shape (threads or interleaved columns per CTA,
- * cp.async staging or not) depends on N and the beam batch.  prism_plan_autotune times every
+ * staging of the next row or tile through shared memory by cp.async or by TMA, or none) depends on
+ * N and the beam batch.  At N = 1024 the untuned column pass already uses the TMA-staged shape.  prism_plan_autotune times every
  * compiled shape of the row pass (PRISM_TUNE_ROW) and the column pass (PRISM_TUNE_COL) on the
  * plan's own wave scratch (5 launches each after 2 warm-ups, CUDA events on the plan's stream)
  * and keeps the fastest for the plan's later builds.  Shapes exist for N = 256 ... 2048; smaller
