@@ -585,7 +585,10 @@ def main():
     alg = {
         "row": 2 * Bn * px * 8 * fk + px * 8,
         "col": 2 * Bn * px * 8 * fk,
-        "row_plane": Bn * px * 8 * fk + px * 8,
+        # first slice: the row transform of t_0 (read t_0, write every column), then the shifted
+        # gather that writes the kept part of every beam's rows (reading the transform once)
+        "row_plane": 2 * px * 8,
+        "plane": Bn * px * 8 * fk + px * 8,
         "row_out": Bn * (px // 2) * 8 * fk + Bn * (px // 4) * 8,
         "transmission": w.n_slices * px * (4 + 8),
         # 16-bit mode: FP32 S of the batch read twice (scale, convert), 16-bit pixel-major S written

@@ -398,13 +398,15 @@ double prism_interaction_constant(double kv);
 
 /* Kernel classes timed by the plan when profiling is on. */
 #define PRISM_K_TRANSMIT   0  /* t_p = exp(i sigma V_p)                                    */
-#define PRISM_K_ROW_PLANE  1  /* first slice: plane wave x t_0, row FFT                     */
+#define PRISM_K_ROW_PLANE  1  /* first slice: row FFT of t_0 (once per build)                */
 #define PRISM_K_ROW        2  /* row IFFT, x t_p, row FFT                                   */
 #define PRISM_K_COL        3  /* column FFT, x propagator (AA-masked), column IFFT          */
 #define PRISM_K_ROW_OUT    4  /* last row IFFT, store S                                     */
 #define PRISM_K_SCAN       5  /* coefficients + window gather + beam sum + window FFT + bins */
 #define PRISM_K_QUANT      6  /* FP16/BF16 mode: per-beam scales, S to pixel-major 16-bit     */
-#define PRISM_K_COUNT      7
+#define PRISM_K_PLANE      7  /* first slice of every beam: the row FFT of t_0 shifted by the
+                                 beam's m f columns, times its y phase (shift theorem)        */
+#define PRISM_K_COUNT      8
 
 /* profiling on: every launch of the plan is bracketed by CUDA events on the plan's stream. */
 int prism_plan_set_profiling(prism_plan *plan, int enable);

@@ -360,6 +360,8 @@ struct prism_plan {
     DevArena arena;
     // device tables / buffers
     float2 *t = nullptr, *wave = nullptr, *S = nullptr;  // S: all beams (FP32 mode) or one beam batch (16-bit)
+    float2 *t0f = nullptr;     // FFT_x(t_0) [ny][nx]: the first slice of every beam by the shift theorem
+    int *zero_mn = nullptr;    // the (0, 0) beam that makes it
     int prec = PRISM_PRECISION_FP32;
     void *S16 = nullptr;       // 16-bit mode: [ny_s * nx_s][kp]
     float *scale = nullptr;    // 16-bit mode: [kp / 2] per-beam power-of-two scales
@@ -567,7 +569,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     const size_t s16_bytes = half ? (size_t)nxs * nys * P->kp * 2 * tc_parts(g.precision) + (size_t)P->kp / 2 * sizeof(float) : 0;
     const size_t w_bytes = px * 8;
     const size_t per_beam = w_bytes + (half ? sbeam : 0);
-    const size_t fixed = t_bytes + (half ? s16_bytes : (size_t)P->nbeams * sbeam) + (1 << 20);
+    const size_t fixed = t_bytes + px * 8 + (half ? s16_bytes : (size_t)P->nbeams * sbeam) + (1 << 20);
     int batch = P->nbeams;
     if (hbm_budget_bytes) {
         if (fixed + per_beam > hbm_budget_bytes) {
@@ -606,6 +608,9 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.alloc((void **)&P->dev_err, sizeof(int)))) return bail(rc);
     CUDA_TRY(cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->stream));
     if ((rc = A.alloc((void **)&P->wave, (size_t)batch * w_bytes))) return bail(rc);
+    if ((rc = A.alloc((void **)&P->t0f, px * 8))) return bail(rc);
+    if ((rc = A.alloc((void **)&P->zero_mn, 2 * sizeof(int)))) return bail(rc);
+    CUDA_TRY(cudaMemsetAsync(P->zero_mn, 0, 2 * sizeof(int), P->stream));
     P->wave_map_ok = encode_wave_map(P->wave_map, P->wave, g.nx, g.ny, batch);
     if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
     if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
@@ -747,14 +752,34 @@ static int build_launches(prism_plan *P, const float *V_dev, int per) {
                 });
                 if (rc) return rc;
             }
-            RowArgs ra = row_args(P);
-            ra.trans = P->t + (size_t)p * px;
-            ra.n_rows = nb * g.ny;
-            ra.beam0 = b0;
-            rc = plan_launch(P, p == 0 ? PRISM_K_ROW_PLANE : PRISM_K_ROW, [&] {
-                return p > 0 && P->tune_shape[0] >= 0 ? launch_row_shape(g.nx, P->tune_shape[0], ra, P->stream)
-                                                      : launch_row(g.nx, p == 0 ? ROW_PLANE : ROW_STD, ra, P->stream);
-            });
+            if (p == 0) {
+                // first slice (shift theorem): T0 = FFT_x(t_0) once per build, every column -- the
+                // first row pass of the (0, 0) beam -- then every beam's rows as T0 shifted by m f
+                // columns times the y phase exp(2 pi i n f_y y / ny)
+                if (b0 == 0) {
+                    RowArgs r0 = row_args(P);
+                    r0.wave = P->t0f;
+                    r0.trans = P->t;
+                    r0.n_rows = g.ny;
+                    r0.beam_mn = P->zero_mn;
+                    r0.beam0 = 0;
+                    r0.kx_half = 0;
+                    rc = plan_launch(P, PRISM_K_ROW_PLANE, [&] { return launch_row(g.nx, ROW_PLANE, r0, P->stream); });
+                    if (rc) return rc;
+                }
+                rc = plan_launch(P, PRISM_K_PLANE, [&] {
+                    return launch_plane(P->t0f, P->wave, P->beam_mn, b0, nb, g.nx, g.ny, g.f, P->fy, P->T.kx_half, P->stream);
+                });
+            } else {
+                RowArgs ra = row_args(P);
+                ra.trans = P->t + (size_t)p * px;
+                ra.n_rows = nb * g.ny;
+                ra.beam0 = b0;
+                rc = plan_launch(P, PRISM_K_ROW, [&] {
+                    return P->tune_shape[0] >= 0 ? launch_row_shape(g.nx, P->tune_shape[0], ra, P->stream)
+                                                 : launch_row(g.nx, ROW_STD, ra, P->stream);
+                });
+            }
             if (rc) return rc;
             const int pi = P->T.slice_prop[p];
             ColArgs ca = col_args(P->T, P->wave, P->prop_x + (size_t)pi * g.nx, P->prop_y + (size_t)pi * g.ny,
@@ -1248,7 +1273,7 @@ extern "C" int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cud
 }
 
 // ------------------------------------------------------------------ timing
-static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan", "quantize"};
+static const char *k_names[PRISM_K_COUNT] = {"transmission", "row_plane", "row", "col", "row_out", "scan", "quantize", "plane"};
 
 extern "C" const char *prism_kernel_name(int kind) {
     if (kind < 0 || kind >= PRISM_K_COUNT) return "?";

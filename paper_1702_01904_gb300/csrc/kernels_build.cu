@@ -30,6 +30,44 @@ __global__ void __launch_bounds__(256) k_transmission(const float4 *__restrict__
     }
 }
 
+// ------------------------------------------------------------------ first slice by the shift theorem
+// The first row pass of beam (m, n) transforms psi_b t_0 with psi_b = exp(2 pi i (m f x / nx +
+// n f_y y / ny)): row by row that is FFT_x(t_0)[kx - m f] exp(2 pi i n f_y y / ny).  So the row
+// transform T0 = FFT_x(t_0) is made once per build (a ROW_PLANE pass of the (0, 0) beam that keeps
+// every column) and each beam's first-slice rows are T0 shifted by m f columns times the row's y
+// phase -- a gather instead of a transform per row.  One CTA per row at a time, threads over its
+// kept columns; nx and ny are powers of two, so the index reductions are masks and ky / ny is exact
+// in FP32.
+__global__ void __launch_bounds__(256) k_plane(const float2 *__restrict__ T0, float2 *__restrict__ wave,
+                                               const int *__restrict__ beam_mn, int beam0, int nb, int nx, int ny,
+                                               int f, int f_y, int kx_half) {
+    const int kept = kx_half > 0 ? 2 * kx_half - 1 : nx;  // kx = 0 .. kh-1 and nx-kh+1 .. nx-1
+    for (int row = blockIdx.x; row < nb * ny; row += gridDim.x) {
+        const int b = row / ny, y = row - b * ny;
+        const int m = __ldg(beam_mn + 2 * (beam0 + b)), n = __ldg(beam_mn + 2 * (beam0 + b) + 1);
+        const int ky = (int)(((long long)n * f_y * y) & (ny - 1));
+        float sn, cs;
+        sincospif(2.0f * ((float)ky / (float)ny), &sn, &cs);
+        const float2 e = make_float2(cs, sn);
+        const float2 *t0 = T0 + (size_t)y * nx;
+        float2 *w = wave + (size_t)row * nx;
+        const int shift = m * f;
+        for (int j = threadIdx.x; j < kept; j += blockDim.x) {
+            const int kx = kx_half > 0 && j >= kx_half ? nx - 2 * kx_half + 1 + j : j;
+            w[kx] = cmul(__ldg(t0 + ((kx - shift) & (nx - 1))), e);
+        }
+    }
+}
+
+cudaError_t launch_plane(const float2 *T0, float2 *wave, const int *beam_mn, int beam0, int nb, int nx, int ny, int f, int f_y,
+                         int kx_half, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    if ((nx & (nx - 1)) || (ny & (ny - 1))) return cudaErrorInvalidValue;  // the masks need powers of two
+    const int rows = nb * ny;
+    k_plane<<<rows < 152 * 8 ? rows : 152 * 8, 256, 0, s>>>(T0, wave, beam_mn, beam0, nb, nx, ny, f, f_y, kx_half);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigma_cycles, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const size_t n4 = n / 4;  // n = H * nx * ny is a multiple of 256

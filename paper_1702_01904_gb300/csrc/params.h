@@ -133,6 +133,9 @@ struct BinArgs {
 
 // launchers (kernels_build.cu, kernels_scan.cu); return cudaSuccess or the launch error
 cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigma_cycles, cudaStream_t s);
+// first-slice rows of beams beam0 .. beam0+nb-1 from T0 = FFT_x(t_0) [ny][nx] (kept columns only)
+cudaError_t launch_plane(const float2 *T0, float2 *wave, const int *beam_mn, int beam0, int nb, int nx, int ny, int f, int f_y,
+                         int kx_half, cudaStream_t s);
 cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s);
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);

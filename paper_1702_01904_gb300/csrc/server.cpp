@@ -105,7 +105,8 @@ struct prism_server {
 };
 
 static size_t plan_bytes_estimate(const prism_grid &g) {
-    // transmission + wave stack of all beams + S-matrix + tables, matching prism_plan_create
+    // transmission + row transform of t_0 + wave stack of all beams + S-matrix + tables, matching
+    // prism_plan_create
     const double lam = prism_wavelength(g.kv);
     const double a = g.alpha_max_mrad * 1e-3;
     const double rx = a / (lam * g.f / g.cell_x), ry = a / (lam * (g.f_y > 0 ? g.f_y : g.f) / g.cell_y);
@@ -114,7 +115,7 @@ static size_t plan_bytes_estimate(const prism_grid &g) {
     const size_t s16 = g.precision != PRISM_PRECISION_FP32
                            ? (size_t)((beams + 8) * 4 * px / (g.downsample * g.downsample)) * (g.precision == PRISM_PRECISION_FP16X2 ? 2 : 1)
                            : 0;
-    return (size_t)g.n_slices * px * 8 + (size_t)(beams * px * 8) + (size_t)(beams * px / (g.downsample * g.downsample) * 8) +
+    return (size_t)(g.n_slices + 1) * px * 8 + (size_t)(beams * px * 8) + (size_t)(beams * px / (g.downsample * g.downsample) * 8) +
            s16 + ((size_t)2 << 20) + (size_t)g.n_slices * px * 4;
 }
 

@@ -23,8 +23,8 @@ PRISM_ERR_CUDA = -3
 PRISM_ERR_DEVICE = -4
 PRISM_ERR_UNSUPPORTED = -5
 
-PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN, PRISM_K_QUANT = range(7)
-PRISM_K_COUNT = 7
+PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN, PRISM_K_QUANT, PRISM_K_PLANE = range(8)
+PRISM_K_COUNT = 8
 
 PRISM_PRECISION_FP32 = 0
 PRISM_PRECISION_FP16 = 1

@@ -271,7 +271,8 @@ def test_batched_build_is_bitwise_identical():
     y0 = np.linspace(1, 7, 9)
     probe = P.make_probe(20.0)
     full, a = run_prism(g, V, probe, x0, y0, DET)
-    need = 3 * 64 * 64 * 8 + full.info.n_beams * 32 * 32 * 8 + (1 << 20)
+    # plan memory: t_p of the 3 slices, the row transform of t_0, the FP32 S, 1 MiB; then one wave per beam
+    need = 3 * 64 * 64 * 8 + 64 * 64 * 8 + full.info.n_beams * 32 * 32 * 8 + (1 << 20)
     small, b = run_prism(g, V, probe, x0, y0, DET, budget=need + 5 * 64 * 64 * 8)
     assert small.info.beam_batch == 5 < full.info.n_beams
     assert np.array_equal(a, b)
@@ -305,8 +306,9 @@ def test_host_build_chunks_and_rebuild_identical():
     y0 = np.linspace(1.0, 6.0, 12)
     probe = P.make_probe(20.0)
     full, ref = run_prism(g, V2, probe, x0, y0, DET)
-    # plan memory: t_p of every slice + the FP32 S + 1 MiB, then one wave per beam of a batch
-    small = 9 * 64 * 64 * 8 + full.info.n_beams * 32 * 32 * 8 + (1 << 20) + 5 * 64 * 64 * 8
+    # plan memory: t_p of every slice, the row transform of t_0, the FP32 S, 1 MiB; then one wave per
+    # beam of a batch
+    small = 9 * 64 * 64 * 8 + 64 * 64 * 8 + full.info.n_beams * 32 * 32 * 8 + (1 << 20) + 5 * 64 * 64 * 8
     for budget, batch in ((0, full.info.n_beams), (small, 5)):
         sim = PrismSimulation(c_grid(g), budget)
         assert sim.info.beam_batch == batch
