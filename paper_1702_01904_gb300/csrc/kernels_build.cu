@@ -10,19 +10,24 @@
 namespace prism {
 
 // ------------------------------------------------------------------ transmission (t = e^{i sigma V})
-// The phase sigma*V is formed in FP64 and reduced to [-1/2, 1/2) cycles before the FP32 sincos.
+// The phase sigma*V in cycles is reduced to [-1/2, 1/2) before the FP32 sincos, in float-float
+// arithmetic (FP64 runs at a small fraction of the FP32 rate on this GPU): sigma = hi + lo (two
+// floats, split on the host), p = V hi rounded and its exact error e = fma(V, hi, -p), so that
+// (p - rint(p)) + (e + V lo) is the fractional part to about 2^-24 of a cycle (p - rint(p) is
+// exact while |p| < 2^23).
 __global__ void __launch_bounds__(256) k_transmission(const float4 *__restrict__ V, float4 *__restrict__ t,
-                                                      size_t n4, double sigma_cycles) {
+                                                      size_t n4, float sig_hi, float sig_lo) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
         const float4 v = V[i];
         float vv[4] = {v.x, v.y, v.z, v.w};
         float2 o[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double c = sigma_cycles * (double)vv[k];
-            c -= rint(c);
+            const float p = vv[k] * sig_hi;
+            const float e = fmaf(vv[k], sig_hi, -p);
+            const float c = (p - rintf(p)) + fmaf(vv[k], sig_lo, e);
             float s, co;
-            sincospif(2.0f * (float)c, &s, &co);
+            sincospif(2.0f * c, &s, &co);
             o[k] = make_float2(co, s);
         }
         t[2 * i] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
@@ -73,8 +78,9 @@ cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigm
     const size_t n4 = n / 4;  // n = H * nx * ny is a multiple of 256
     size_t blocks = (n4 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    const float hi = (float)sigma_cycles, lo = (float)(sigma_cycles - (double)hi);
     k_transmission<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float4 *>(V),
-                                                     reinterpret_cast<float4 *>(t), n4, sigma_cycles);
+                                                     reinterpret_cast<float4 *>(t), n4, hi, lo);
     return cudaGetLastError();
 }
 
