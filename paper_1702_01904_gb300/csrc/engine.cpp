@@ -370,7 +370,8 @@ struct prism_plan {
     size_t win_cap = 0;
     int *win_cnt = nullptr;    // FP32 GEMM scan: completion counters of split groups
     size_t cnt_cap = 0;
-    CUtensorMap wave_map;      // the wave stack for the TMA-staged column pass
+    CUtensorMap wave_map, wave_map4;  // the wave stack for the TMA-staged column pass (8 / 4 columns per box)
+    bool shared_sms = false;   // a batch runs this plan's kernels beside other cells' (see col_default_shape)
     bool wave_map_ok = false;
     int *dev_err = nullptr;    // device error word
     int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
@@ -452,10 +453,10 @@ static int tc_mode(int prec) { return prec == PRISM_PRECISION_BF16 ? 1 : prec ==
 static int tc_parts(int prec) { return prec == PRISM_PRECISION_FP16X2 ? 2 : 1; }
 
 // Tensor map of a wave stack [batch][ny][nx] complex64 for the TMA-staged column pass: FP32 view
-// [batch][ny][2 nx], boxes of 16 floats (8 columns) x min(ny, 256) rows x 1.  The encoder comes from
+// [batch][ny][2 nx], boxes of 2 w floats (w = 4 or 8 columns) x min(ny, 256) rows x 1.  The encoder comes from
 // the driver through the runtime's entry-point query; false (shape not used) if it is unavailable
 // or the stack breaks a rule of the map (16-byte aligned base, strides multiples of 16 bytes).
-static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch) {
+static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch, int w) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -468,7 +469,7 @@ static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny
     if (!encode || !wave || ((uintptr_t)wave & 15) || nx < 8 || nx % 8 || ny < 1 || batch < 1) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)batch};
     const cuuint64_t strides[2] = {(cuuint64_t)2 * nx * sizeof(float), (cuuint64_t)2 * nx * ny * sizeof(float)};
-    const cuuint32_t box[3] = {16, (cuuint32_t)std::min(ny, 256), 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * w), (cuuint32_t)std::min(ny, 256), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(wave), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -611,7 +612,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.alloc((void **)&P->t0f, px * 8))) return bail(rc);
     if ((rc = A.alloc((void **)&P->zero_mn, 2 * sizeof(int)))) return bail(rc);
     CUDA_TRY(cudaMemsetAsync(P->zero_mn, 0, 2 * sizeof(int), P->stream));
-    P->wave_map_ok = encode_wave_map(P->wave_map, P->wave, g.nx, g.ny, batch);
+    P->wave_map_ok = encode_wave_map(P->wave_map, P->wave, g.nx, g.ny, batch, 8) && encode_wave_map(P->wave_map4, P->wave, g.nx, g.ny, batch, 4);
     if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
     if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
     if ((rc = A.upload(&P->aa_kmax, P->T.aa_kmax))) return bail(rc);
@@ -705,19 +706,25 @@ static ColArgs col_args(const GridTables &T, float2 *wave, const float2 *prop_x,
 
 static int build_launches(prism_plan *P, const float *V_dev, int per = 0);
 
-// the column pass's launch shape when none is tuned or pinned: the TMA-staged shape at N = 1024
-// (the fastest there: 0.295 against 0.320 ms per launch for cp.async staging on the 1024^2 carbon
-// workload), when the plan holds the tensor map of its wave; otherwise the default launcher (-1)
+// the column pass's launch shape when none is tuned or pinned: at N = 1024 the TMA-staged shape of
+// 4 columns per CTA, 3 CTAs per SM (the fastest there: 0.275 ms per launch on the 1024^2 carbon
+// workload, against 0.293 with 8 columns and 0.320 for cp.async staging), when the plan holds the
+// tensor maps of its wave; otherwise the default launcher (-1)
+// In a batch graph with parallel branches the passes of different cells share the SMs, and a shape
+// that fills an SM by itself (3 CTAs of 66 KB and 168 x 128 registers) leaves no room for the
+// other branches' kernels: there the 8-column TMA shape (one 131 KB CTA per SM) is the default, and
+// the autotuner skips the SM-filling shapes (64 uneven cells, 4 branches: 2.78 s per run with them,
+// 2.25 s without).
 static int col_default_shape(const prism_plan *P) {
     if (P->g.ny != 1024 || !P->wave_map_ok) return -1;
-    for (int v = 0; v < tune_shapes(PRISM_TUNE_COL); ++v)
-        if (tune_shape_needs_map(PRISM_TUNE_COL, v) && tune_shape_valid(PRISM_TUNE_COL, 1024, v)) return v;
-    return -1;
+    const int v = tune_col_tma_shape(P->shared_sms ? 8 : 4);
+    return v >= 0 && tune_shape_valid(PRISM_TUNE_COL, 1024, v) ? v : -1;
 }
 
 // the plan's wave stack in the column arguments of its build and autotuner launches
 static void col_wave_map(const prism_plan *P, ColArgs &ca) {
     ca.wave_map = P->wave_map;
+    ca.wave_map4 = P->wave_map4;
     ca.wave_map_ok = P->wave_map_ok ? 1 : 0;
     ca.err = P->dev_err;
 }
@@ -1387,8 +1394,9 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
 // ------------------------------------------------------------------ autotuner
 struct TuneKey {
     int kind, n, batch;
+    bool shared;  // tuned for a batch whose branches share the SMs
     bool operator<(const TuneKey &o) const {
-        return kind != o.kind ? kind < o.kind : n != o.n ? n < o.n : batch < o.batch;
+        return kind != o.kind ? kind < o.kind : n != o.n ? n < o.n : batch != o.batch ? batch < o.batch : shared < o.shared;
     }
 };
 struct TuneVal {
@@ -1421,7 +1429,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
     int rc = PRISM_OK;
     for (int kind = 0; kind < 2 && !rc; ++kind) {
         const int n = kind == 0 ? g.nx : g.ny;
-        const TuneKey key{kind, n, P->batch};
+        const TuneKey key{kind, n, P->batch, P->shared_sms};
         for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->tune_ms[kind][v] = -1.0;
         P->tuned[kind] = true;
         {
@@ -1436,7 +1444,9 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
         int best = -1;
         double best_ms = 0;
         for (int v = 0; v < tune_shapes(kind) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
-            if (!tune_shape_valid(kind, n, v) || (tune_shape_needs_map(kind, v) && !P->wave_map_ok)) continue;
+            if (!tune_shape_valid(kind, n, v) || (tune_shape_needs_map(kind, v) && !P->wave_map_ok) ||
+                (P->shared_sms && tune_shape_fills_sm(kind, v)))
+                continue;
             RowArgs ra = row_args(P);
             ra.trans = P->t;
             ra.n_rows = P->batch * g.ny;
@@ -1561,6 +1571,7 @@ extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t h
         prism_plan *P = nullptr;
         if ((rc = prism_plan_create(&c.grid, 0, B->origin, &P))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
         B->plans.push_back(P);
+        P->shared_sms = nb > 1;
         if ((flags & PRISM_BATCH_AUTOTUNE) && (rc = prism_plan_autotune(P))) return bail(rc);
         ScanArgs a;
         if ((rc = scan_prepare(P, &c.probe, &c.scan, &c.det, a, false))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);

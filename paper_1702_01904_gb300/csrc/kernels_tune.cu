@@ -20,13 +20,13 @@ using tune::N_COL;
 using tune::N_ROW;
 using tune::ROW_SHAPES;
 const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged", "128 thr, TMA"};
-const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4", "W8", "W8, TMA", "W8, 2/SM", "W4, staged, 3/SM"};
+const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4, TMA, 3/SM", "W8", "W8, TMA", "W8, 2/SM", "W4, staged, 3/SM"};
 
 template <int N, int I>
 constexpr bool col_ok() {
     using C = ColCfg<N, COL_SHAPES[I].a, COL_SHAPES[I].stg, COL_SHAPES[I].mb, COL_SHAPES[I].tma>;
     return C::SMEM <= 227 * 1024 && C::THREADS <= 1024 && (size_t)C::MINB * (C::SMEM + 1024) <= 228 * 1024 &&
-           (!C::TMA || (2 * C::W * 4 == 64 && N % C::BOXR == 0));
+           (!C::TMA || ((C::W == 4 || C::W == 8) && N % C::BOXR == 0));
 }
 
 template <int N, int I>
@@ -80,6 +80,14 @@ int tune_default_shape(int kind, int n) {
 }
 
 bool tune_shape_needs_map(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].tma; }
+
+bool tune_shape_fills_sm(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].mb >= 3; }
+
+int tune_col_tma_shape(int w) {
+    for (int v = 0; v < N_COL; ++v)
+        if (COL_SHAPES[v].tma && COL_SHAPES[v].a == w) return v;
+    return -1;
+}
 
 bool tune_shape_valid(int kind, int n, int v) {
     if (kind == 0) {

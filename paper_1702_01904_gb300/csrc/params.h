@@ -43,6 +43,7 @@ struct RowArgs {
 struct ColArgs {
     CUtensorMap wave_map;      // TMA staging (STD): `wave` as FP32 [batch][ny][2 nx], boxes of 16 floats
                                // (8 columns) x min(ny, 256) rows x 1; valid when wave_map_ok
+    CUtensorMap wave_map4;     // the same with boxes of 8 floats (4 columns)
     float2 *wave;              // [batch][ny][nx]
     float *inten;              // DETECT: [batch][ny][nx] |Psi|^2 (scaled later)
     const float2 *prop_x;      // [nx]  exp(-i pi lambda dz qx^2)
@@ -61,7 +62,7 @@ struct ColArgs {
     int band4;                 // 1: the aperture keeps |ky| < ny/4 on every column (aa_kmax < ny/4), so
                                // the column transforms may drop that band's complement at compile
                                // time (STD, DETECT)
-    int wave_map_ok;           // 1: wave_map describes `wave` (the TMA-staged shape may run)
+    int wave_map_ok;           // 1: wave_map and wave_map4 describe `wave` (the TMA-staged shapes may run)
     int *err;                  // device error word: a TMA wait that ran out sets bit 1
     Tw64 tw;
 };
@@ -171,6 +172,8 @@ const char *tune_shape_name(int kind, int v);
 int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
 bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
+int tune_col_tma_shape(int w);                // the TMA-staged column shape of w columns per CTA, or -1
+bool tune_shape_fills_sm(int kind, int v);    // 3 or more CTAs per SM, each with a third of its resources
 cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s);
 // smallest scan-window / FFT sizes the kernels are instantiated for

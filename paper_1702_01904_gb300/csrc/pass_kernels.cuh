@@ -338,7 +338,7 @@ constexpr int col_default_w() { return NY >= 2048 ? 4 : NY >= 1024 ? 8 : 16; }
 
 // WC interleaved columns per CTA, STG: cp.async staging of the next tile, MB: CTAs per SM the
 // register allocation must allow (0: the default rule), TM: the next tile staged by TMA instead
-// (NY / BOXR boxes of W columns x BOXR rows, one thread issues them) -- launch shape only
+// (NY / BOXR boxes of W = 4 or 8 columns x BOXR rows, one thread issues them) -- launch shape only
 template <int NY, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false>
 struct ColCfg {
     using FS = FftShape<NY>;
@@ -422,7 +422,8 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
             if (threadIdx.x == 0) {
                 tc::fence_proxy_async();  // the buffer's generic reads (previous tile) before the async writes
                 tc::mbar_arrive_expect_tx(&tbar, (uint32_t)(NY * W * sizeof(float2)));
-                for (int y0 = 0; y0 < NY; y0 += C::BOXR) tc::tma_load_3d(stg + y0 * W, &a.wave_map, 2 * kx0, y0, b, &tbar);
+                const CUtensorMap *map = W == 8 ? &a.wave_map : &a.wave_map4;  // boxes of W columns
+                for (int y0 = 0; y0 < NY; y0 += C::BOXR) tc::tma_load_3d(stg + y0 * W, map, 2 * kx0, y0, b, &tbar);
             }
             return;
         }
@@ -542,11 +543,11 @@ static inline long long col_tiles(int nx, int w, int kx_half, int batch) {
 template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false>
 static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
     using C = ColCfg<NY, WC, STG, MB, TM>;
-    if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024 || (TM && (MODE != COL_STD || 2 * WC * 4 != 64 || NY % C::BOXR))) {
+    if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024 || (TM && (MODE != COL_STD || (WC != 4 && WC != 8) || NY % C::BOXR))) {
         return cudaErrorInvalidConfiguration;
     } else {
         if (a.nx % C::W) return cudaErrorInvalidValue;
-        // the map must describe this wave stack with boxes of W columns x BOXR rows
+        // the maps must describe this wave stack with boxes of W columns x BOXR rows
         if (TM && !a.wave_map_ok) return cudaErrorInvalidValue;
         int grid = 0;
         const long long work = col_tiles(a.nx, C::W, a.kx_half, a.batch);
