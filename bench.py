@@ -173,16 +173,23 @@ def oracle_sample(w, V, budget_s=20.0):
     }
 
 
-# sources of the row and column pass kernels (the ones profiles/dram_traffic.json measures)
-PASS_SOURCES = ("fft.cuh", "params.h", "pass_kernels.cuh", "kernels_build.cu", "kernels_tune.cu", "kernels_tune_row.cu",
-                "tune_shapes.cuh")
+# device code of the row and column pass kernels (the ones profiles/dram_traffic.json measures):
+# the kernel templates and their helpers, the compiled launch shapes, and the parameter blocks the
+# kernels read (host-only declarations in params.h do not enter the hash)
+PASS_SOURCES = ("fft.cuh", "pass_kernels.cuh", "tc.cuh", "kernels_build.cu", "tune_shapes.cuh")
+PASS_STRUCTS = ("struct Tw64", "struct RowArgs", "struct ColArgs")
 
 
 def source_hash():
     h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1702_01904_gb300", "csrc")
     for f in PASS_SOURCES:
-        with open(os.path.join(ROOT, "paper_1702_01904_gb300", "csrc", f), "rb") as fh:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    params = open(os.path.join(csrc, "params.h")).read()
+    for name in PASS_STRUCTS:
+        i = params.index(name)
+        h.update(params[i:params.index("};", i) + 2].encode())
     return h.hexdigest()[:16]
 
 
