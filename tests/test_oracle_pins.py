@@ -582,3 +582,33 @@ def test_rectangular_window_empty_sample_one_pixel_per_beam_and_linearity():
     for x0, y0 in [(0.0, 0.0), (6.3, 2.9)]:
         a = O.prism_scan(S, m, n, g, PROBE, DET, np.array([x0]), np.array([y0]))[0]
         assert np.max(np.abs(a - O.prism_probe_direct(v, g, PROBE, DET, x0, y0))) < 1e-12
+
+
+# ------------------------------------------------------------------ identities the CUDA path relies on
+def test_first_slice_shift_theorem():
+    # the first row transform of a plane wave times t_0 is the row transform of t_0 shifted by the
+    # plane wave's column index, times its y phase (the build makes the first slice this way)
+    rng = np.random.Generator(np.random.PCG64(3))
+    nx, ny, m, n, f, fy = 32, 16, -3, 2, 2, 1
+    t0 = np.exp(1j * rng.random((ny, nx)) * 2.0)
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    psi = np.exp(2j * np.pi * (m * f * x / nx + n * fy * y / ny))
+    direct = np.fft.fft(psi * t0, axis=1)
+    T0 = np.fft.fft(t0, axis=1)
+    kx = np.arange(nx)
+    shifted = T0[:, (kx - m * f) % nx] * np.exp(2j * np.pi * (n * fy * np.arange(ny) / ny))[:, None]
+    assert np.max(np.abs(direct - shifted)) < 1e-12 * nx
+
+
+def test_half_resolution_storage_is_every_second_sample():
+    # a wave band-limited to |k| < N/4 (what the anti-aliasing aperture leaves) has its inner-square
+    # Fourier crop, inverse-transformed at N/2 and divided by 4, equal to its even real-space samples
+    rng = np.random.Generator(np.random.PCG64(4))
+    n = 32
+    k = np.fft.fftfreq(n, 1.0 / n)
+    band = (np.abs(k)[:, None] < n // 4) & (np.abs(k)[None, :] < n // 4)
+    spec = (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) * band
+    wave = np.fft.ifft2(spec)
+    crop = O.fourier_crop_half(wave)
+    assert np.max(np.abs(crop - wave[::2, ::2])) < 1e-13
