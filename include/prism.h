@@ -384,6 +384,15 @@ int prism_plan_transmission(const prism_plan *plan, const void **dev_ptr);
  * INVALID before the S-matrix is built. */
 int prism_plan_smatrix_copy(prism_plan *plan, float *out_dev);
 
+/* Load an S-matrix instead of building it (checkpoint / resume: the build is the expensive part of
+ * the method, Calculation Time section, and the same S serves every later probe configuration,
+ * Varying Probe Size section).  S_dev is complex64 [B][ny_s][nx_s] as written by
+ * prism_plan_smatrix_copy of a plan with the same grid, in caller-owned device memory that must stay
+ * valid until the plan's stream has passed this call (prism_sync).  FP32 plans copy it; 16-bit plans
+ * quantise it beam batch by beam batch as their build does.  The plan is then built.  INVALID for a
+ * NULL plan or a misaligned S_dev. */
+int prism_plan_load_smatrix(prism_plan *plan, const float *S_dev);
+
 /* Diagnostic of the tensor-core path (no counterpart in the paper): one tcgen05 MMA
  * D[128][16] = A[128][16] B[16][16]^T on small-integer FP16 operands, A[m][k] = (m + 3k) % 7 - 3,
  * B[n][k] = (5n + k) % 5 - 2, written to out_dev float32 [128][16]; status_dev[0] is set to 1 if the

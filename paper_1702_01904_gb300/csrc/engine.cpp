@@ -1264,6 +1264,35 @@ extern "C" int prism_plan_smatrix_copy(prism_plan *P, float *out_dev) {
     return PRISM_OK;
 }
 
+extern "C" int prism_plan_load_smatrix(prism_plan *P, const float *S_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    int rc;
+    if ((rc = check_dev_ptr(S_dev, 8, "S_dev"))) return rc;
+    const size_t sbeam = (size_t)P->nxs * P->nys * sizeof(float2);
+    if (P->prec == PRISM_PRECISION_FP32) {
+        CUDA_TRY(cudaMemcpyAsync(P->S, S_dev, (size_t)P->nbeams * sbeam, cudaMemcpyDeviceToDevice, P->stream));
+    } else {
+        // the FP32 beam-batch buffer takes each batch in turn; the quantiser writes its 16-bit rows
+        for (int b0 = 0; b0 < P->nbeams; b0 += P->batch) {
+            const int nb = std::min(P->batch, P->nbeams - b0);
+            CUDA_TRY(cudaMemcpyAsync(P->S, reinterpret_cast<const char *>(S_dev) + (size_t)b0 * sbeam, (size_t)nb * sbeam,
+                                     cudaMemcpyDeviceToDevice, P->stream));
+            QuantArgs q;
+            q.S = P->S;
+            q.S16 = P->S16;
+            q.scale = P->scale;
+            q.beam0 = b0;
+            q.nb = nb;
+            q.npix = P->nxs * P->nys;
+            q.kp = P->kp;
+            q.mode = tc_mode(P->prec);
+            if ((rc = plan_launch(P, PRISM_K_QUANT, [&] { return launch_quantize(q, P->stream); }))) return rc;
+        }
+    }
+    P->built = true;
+    return PRISM_OK;
+}
+
 extern "C" int prism_plan_transmission(const prism_plan *P, const void **dev_ptr) {
     if (!P || !dev_ptr) return fail(PRISM_ERR_INVALID, "NULL argument");
     *dev_ptr = P->t;

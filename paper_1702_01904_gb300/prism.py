@@ -49,6 +49,7 @@ EXPORTED = [
     "prism_selftest_tcgen05",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
     "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
+    "prism_plan_load_smatrix",
 ]
 
 
@@ -151,6 +152,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_tune_result": (c_int, [P, c_int, POINTER(PrismTuneEntry)]),
         "prism_tune_shape_name": (c_char_p, [c_int, c_int]),
         "prism_plan_set_tune_shape": (c_int, [P, c_int, c_int]),
+        "prism_plan_load_smatrix": (c_int, [P, P]),
         "prism_batch_run": (c_int, [P]),
         "prism_batch_sync": (c_int, [P]),
         "prism_batch_info_get": (c_int, [P, POINTER(PrismBatchInfo)]),
@@ -450,3 +452,7 @@ def prism_tune_shape_name(kind, shape):
 
 def prism_plan_set_tune_shape(plan, kind, shape):
     _check(load().prism_plan_set_tune_shape(plan, kind, shape))
+
+
+def prism_plan_load_smatrix(plan, S_dev):
+    _check(load().prism_plan_load_smatrix(plan, _ptr(S_dev)))

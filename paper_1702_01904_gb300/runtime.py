@@ -127,6 +127,16 @@ class PrismSimulation:
         self.sync()
         return torch.view_as_complex(out)
 
+    def load_smatrix(self, S: torch.Tensor):
+        """Use an S-matrix (complex64 [B][ny_s][nx_s] on the GPU, e.g. from smatrix() of a plan with the
+        same grid, or loaded from a file) instead of building one (prism_plan_load_smatrix)."""
+        i = self.info
+        S = torch.view_as_real(S.to(torch.complex64).contiguous()) if S.is_complex() else S.contiguous()
+        assert S.is_cuda and S.numel() == i.n_beams * i.ny_s * i.nx_s * 2, "S-matrix shape of this plan"
+        torch.cuda.current_stream().synchronize()
+        P.prism_plan_load_smatrix(self.plan, S)
+        self.sync()
+
     def transmission(self) -> torch.Tensor:
         """Copy of the transmission functions complex64 [H][ny][nx] (waits for the plan's stream)."""
         self.sync()

@@ -346,6 +346,33 @@ def test_scan_partition_invariant():
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [P.PRISM_PRECISION_FP32, P.PRISM_PRECISION_FP16, P.PRISM_PRECISION_FP16X2])
+def test_smatrix_checkpoint_resume(prec, tmp_path):
+    # an S-matrix saved to a file and loaded into a fresh plan scans like the plan that built it:
+    # bitwise in FP32 and FP16 (a power-of-two scale and its 16-bit values survive the round trip);
+    # in FP16X2 the stored value + remainder pairs may split differently where a remainder sits on a
+    # rounding tie (same sum, other pair), which moves the products by about 2^-22 of a term
+    g = grid_dict(64, 64, 8.0, 8.0, 2, 2.0, 2)
+    V = rand_v(2, 64, 64, 41)
+    x0 = np.linspace(0.5, 7.5, 8)
+    y0 = np.linspace(1.0, 2.0, 8)
+    probe = P.make_probe(20.0, c1=5.0)
+    grid = P.make_grid(64, 64, 2, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0, precision=prec)
+    a = PrismSimulation(grid)
+    a.build(torch.from_numpy(V).cuda())
+    ref = a.scan(probe, x0, y0, det_c(DET), px=8, py=1).cpu().numpy()
+    np.save(tmp_path / "s.npy", a.smatrix().cpu().numpy())
+    a.close()
+    b = PrismSimulation(grid)
+    b.load_smatrix(torch.from_numpy(np.load(tmp_path / "s.npy")).cuda())
+    got = b.scan(probe, x0, y0, det_c(DET), px=8, py=1).cpu().numpy()
+    b.close()
+    if prec == P.PRISM_PRECISION_FP16X2:
+        assert_images_close(got, ref, rel=1e-5)
+    else:
+        assert np.array_equal(ref, got)
+
+
 def test_empty_scan_and_single_bin():
     g = grid_dict(64, 64, 8.0, 8.0, 1, 2.0, 2)
     V = rand_v(1, 64, 64, 11)
