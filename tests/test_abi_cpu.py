@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1702_01904_gb300 import build as B
@@ -125,3 +126,18 @@ def test_tune_shape_arguments_rejected_without_a_device():
     assert e.value.status == P.PRISM_ERR_INVALID
     names = [P.prism_tune_shape_name(P.PRISM_TUNE_COL, v) for v in range(P.PRISM_TUNE_MAX_SHAPES)]
     assert "W8, TMA" in names and "W8, staged" in names
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """The torch-facing layer refuses to run without a CUDA device instead of falling back to a
+    host path (there is none)."""
+    import torch
+    from paper_1702_01904_gb300 import runtime
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g = P.make_grid(64, 64, 1, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0)
+    with pytest.raises(RuntimeError):
+        runtime.PrismSimulation(g)
+    with pytest.raises(RuntimeError):
+        runtime.multislice(g, torch.zeros(1, 64, 64), P.make_probe(20.0), np.zeros(1), np.zeros(1),
+                           P.make_detector(0.0, 1.0, 10))
