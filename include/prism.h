@@ -399,6 +399,15 @@ int prism_plan_load_smatrix(prism_plan *plan, const float *S_dev);
  * MMA did not complete within its poll limit (caller zeroes it).  Asynchronous on cuda_stream. */
 int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cuda_stream);
 
+/* Diagnostic of failure detection (no counterpart in the paper): the library's in-kernel waits
+ * (tensor-core scan, TMA staging) are mbarrier waits that give up after a clock budget and report
+ * through an error word instead of hanging.  This launches one CTA whose threads wait at most
+ * limit_cycles SM cycles (0 ... 4e9) for a barrier's first phase; with arrive = 0 nothing completes
+ * it and status_dev[0] is set to 1 (the wait ran out, the context stays usable), with arrive != 0
+ * one arrival completes it and status_dev[0] is left alone (caller zeroes it).  Asynchronous on
+ * cuda_stream.  INVALID for a NULL status_dev or a limit outside that range. */
+int prism_selftest_bounded_wait(int *status_dev, long long limit_cycles, int arrive, void *cuda_stream);
+
 /* Relativistic wavelength (Angstrom) and interaction constant (rad/(V*Angstrom)), CODATA 2018. */
 double prism_wavelength(double kv);
 double prism_interaction_constant(double kv);

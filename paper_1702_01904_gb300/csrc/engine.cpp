@@ -1299,6 +1299,15 @@ extern "C" int prism_plan_transmission(const prism_plan *P, const void **dev_ptr
     return PRISM_OK;
 }
 
+extern "C" int prism_selftest_bounded_wait(int *status_dev, long long limit_cycles, int arrive, void *cuda_stream) {
+    int rc;
+    if ((rc = check_dev_ptr(status_dev, 4, "status_dev"))) return rc;
+    if (limit_cycles < 0 || limit_cycles > 4000000000LL) return fail(PRISM_ERR_INVALID, "limit_cycles must be in [0, 4e9]");
+    cudaError_t e = launch_wait_selftest(status_dev, limit_cycles, arrive, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(PRISM_ERR_CUDA, std::string("bounded-wait self-test launch: ") + cudaGetErrorString(e));
+    return PRISM_OK;
+}
+
 extern "C" int prism_selftest_tcgen05(float *out_dev, int *status_dev, void *cuda_stream) {
     int rc;
     if ((rc = check_dev_ptr(out_dev, 16, "out_dev"))) return rc;

@@ -88,6 +88,30 @@ cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ bounded-wait diagnostic
+// The waits of the tensor-core scan and of the TMA-staged passes are mbarrier waits that give up
+// after a clock budget.  This kernel makes one run out on purpose without any fault: one CTA
+// initialises a barrier expecting one arrival, thread 0 arrives or not (`arrive`), and every thread
+// waits for the barrier's first phase for at most `limit_cycles`.  status[0] = 1 if the wait ran
+// out (no arrival: the expected outcome), 0 if the phase completed.
+__global__ void __launch_bounds__(128) k_wait_selftest(int *status, long long limit_cycles, int arrive) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) tc::mbar_arrive(&bar);
+    const bool done = tc::mbar_wait_bounded(&bar, 0, limit_cycles);
+    if (__syncthreads_or(!done) && threadIdx.x == 0) status[0] = 1;
+}
+
+cudaError_t launch_wait_selftest(int *status, long long limit_cycles, int arrive, cudaStream_t s) {
+    if (limit_cycles < 0 || limit_cycles > 4000000000LL) return cudaErrorInvalidValue;
+    k_wait_selftest<<<1, 128, 0, s>>>(status, limit_cycles, arrive);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ 16-bit S-matrix
 // Storage reduction of the S-matrix (PRISM Algorithm section): after the build, each beam's
 // real-space exit wave is divided by a power-of-two scale (the smallest power of two above its

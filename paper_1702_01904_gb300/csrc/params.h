@@ -155,6 +155,7 @@ size_t scan_gemm_cnt_bytes(int grid);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);
 cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s);
+cudaError_t launch_wait_selftest(int *status, long long limit_cycles, int arrive, cudaStream_t s);
 // 16-bit mode (kernels_tc.cu)
 cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s);
 cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp,

@@ -46,7 +46,7 @@ EXPORTED = [
     "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
-    "prism_selftest_tcgen05",
+    "prism_selftest_tcgen05", "prism_selftest_bounded_wait",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
     "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
     "prism_plan_load_smatrix",
@@ -171,6 +171,7 @@ def load(path: str = LIB_PATH):
         "prism_server_stats": (c_int, [P, POINTER(PrismServerInfo)]),
         "prism_server_destroy": (None, [P]),
         "prism_selftest_tcgen05": (c_int, [P, P, P]),
+        "prism_selftest_bounded_wait": (c_int, [P, ctypes.c_longlong, c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -400,6 +401,10 @@ def prism_server_destroy(server):
 
 def prism_selftest_tcgen05(out_dev, status_dev, cuda_stream=None):
     return _check(load().prism_selftest_tcgen05(_ptr(out_dev), _ptr(status_dev), _stream(cuda_stream)))
+
+
+def prism_selftest_bounded_wait(status_dev, limit_cycles, arrive, cuda_stream=None):
+    return _check(load().prism_selftest_bounded_wait(_ptr(status_dev), int(limit_cycles), int(arrive), _stream(cuda_stream)))
 
 
 # ------------------------------------------------------------------ batches of cells

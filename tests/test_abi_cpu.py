@@ -119,6 +119,12 @@ def test_plan_arguments_rejected_before_any_device_call():
     assert status(f=1, f_y=8) == P.PRISM_ERR_UNSUPPORTED  # 32 x 4 window
 
 
+def test_bounded_wait_selftest_rejects_a_null_status():
+    with pytest.raises(P.PrismError) as e:
+        P.prism_selftest_bounded_wait(None, 1000, 0)
+    assert e.value.status == P.PRISM_ERR_INVALID
+
+
 def test_tune_shape_arguments_rejected_without_a_device():
     """prism_plan_set_tune_shape checks its plan and pass on the host."""
     with pytest.raises(P.PrismError) as e:
