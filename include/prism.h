@@ -43,7 +43,8 @@ extern "C" {
 #define PRISM_ERR_INVALID     -1  /* bad argument: NULL pointer, N % (2f) != 0, nbins <= 0, ... */
 #define PRISM_ERR_BUDGET      -2  /* the plan does not fit the HBM budget given at creation     */
 #define PRISM_ERR_CUDA        -3  /* a CUDA runtime call failed (message has the CUDA error)     */
-#define PRISM_ERR_DEVICE      -4  /* a kernel raised the device error flag                      */
+#define PRISM_ERR_DEVICE      -4  /* a kernel raised the device error flag: one of its bounded
+                                     waits ran out (tensor-core scan, TMA-staged tiles or rows)    */
 #define PRISM_ERR_UNSUPPORTED -5  /* valid but not implemented here (e.g. non power-of-two N)   */
 
 /* Simulation grid and PRISM build parameters.
