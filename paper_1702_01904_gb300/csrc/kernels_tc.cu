@@ -94,6 +94,10 @@ cudaError_t launch_tc_selftest(float *out, int *status, cudaStream_t s) {
 // initialises a barrier expecting one arrival, thread 0 arrives or not (`arrive`), and every thread
 // waits for the barrier's first phase for at most `limit_cycles`.  status[0] = 1 if the wait ran
 // out (no arrival: the expected outcome), 0 if the phase completed.
+__device__ __forceinline__ void mbar_arrive_once(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+
 __global__ void __launch_bounds__(128) k_wait_selftest(int *status, long long limit_cycles, int arrive) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(128) k_wait_selftest(int *status, long long li
         tc::fence_mbar_init();
     }
     __syncthreads();
-    if (arrive && threadIdx.x == 0) tc::mbar_arrive(&bar);
+    if (arrive && threadIdx.x == 0) mbar_arrive_once(&bar);
     const bool done = tc::mbar_wait_bounded(&bar, 0, limit_cycles);
     if (__syncthreads_or(!done) && threadIdx.x == 0) status[0] = 1;
 }

@@ -121,10 +121,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// one arrival on the barrier
-__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
-}
 // arrive on the barrier and add `bytes` to the transaction count its phase waits for (the
 // asynchronous copies that complete_tx on it supply those bytes)
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
