@@ -133,6 +133,42 @@ def test_transmit_then_propagate_order_tilt_walkoff():
     assert np.max(np.abs(out - ref)) < 1e-10
 
 
+@pytest.mark.parametrize("axis", [1, 0])
+def test_weak_phase_grating_contrast_sign(axis):
+    # Weak phase object V = eps cos(2 pi g x) under a plane wave, one slice, then free flight z.
+    # To first order in sigma eps, t = 1 + i sigma eps cos(2 pi g x); the two diffracted beams at
+    # +-g each pick up exp(-i pi lambda z g^2), so the exit intensity is
+    #   I(x) = 1 + 2 sigma eps sin(pi lambda z g^2) cos(2 pi g x) + O((sigma eps)^2).
+    # The sign of the contrast term is the sign of the transmission phase (the propagator's sign is
+    # fixed by the Gaussian-beam pin): exp(-i sigma V) would flip it.  The exit wave comes from the
+    # oracle's own S-matrix path (the q = 0 beam at full resolution), so the whole composition of
+    # transmission, propagator and slice step is what is checked.
+    n, cell, kg, z = 64, 16.0, 4, 200.0
+    lam = O.wavelength(300.0)
+    sig = O.interaction_constant(300.0)
+    g = kg / cell
+    x = np.arange(n) * (cell / n)
+    phase_q = math.pi * lam * z * g * g
+    assert math.sin(phase_q) > 0.5  # a clearly positive contrast transfer at this z
+    grid = dict(nx=n, ny=n, cell_x=cell, cell_y=cell, n_slices=1, dz=z, kv=300.0, f=1,
+                downsample=1, aa_frac=0.5, alpha_mrad=20.0)
+    residuals = []
+    for eps in (30.0, 15.0):  # sigma * eps = 0.0196 and 0.0098
+        line = eps * np.cos(2 * math.pi * g * x)
+        v = np.broadcast_to(line[None, :] if axis == 1 else line[:, None], (n, n))[None].copy()
+        S, _, _ = O.smatrix_build(v, grid, beams=(np.array([0]), np.array([0])))
+        inten = np.abs(S[0]) ** 2
+        model = 1.0 + 2.0 * sig * eps * math.sin(phase_q) * np.cos(2 * math.pi * g * x)
+        model = np.broadcast_to(model[None, :] if axis == 1 else model[:, None], (n, n))
+        res = float(np.max(np.abs(inten - model)))
+        assert res <= 2.0 * (sig * eps) ** 2, (eps, res)
+        # the bright fringe sits on the potential's maximum (x = 0) for a positive potential
+        assert inten[0, 0] > 1.0 + sig * eps * math.sin(phase_q)
+        residuals.append(res)
+    # the residual is second order: halving eps quarters it
+    assert 3.0 < residuals[0] / residuals[1] < 5.0
+
+
 # ------------------------------------------------------------------ beam set
 def gauss_circle_count(r2):
     r = int(math.isqrt(int(math.floor(r2)))) + 1
