@@ -224,7 +224,9 @@ int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_
  * nx*ny*(8*n_slices + 24) bytes plus 16 bytes per probe position (e.g. 256^2 with up to ~28
  * slices); larger requests return PRISM_ERR_BUDGET with the required size in prism_last_error().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  All calls share the array and
+ * device current) and keeps it for the life of the process; make that first call before any stream
+ * capture, and do not call this entry point again after a cudaDeviceReset of that device (the kept
+ * address would be stale).  All calls share the array and
  * every call overwrites what it uses, so calls that overlap on the GPU (different streams, or
  * different host threads on one device) race: serialise them on one stream.  Asynchronous like
  * multislice_scan_run: synchronise `cuda_stream` before reading out_dev. */

@@ -1053,6 +1053,18 @@ extern "C" int prism_scan_run_accumulate(prism_plan *P, const prism_probe *probe
 }
 
 // ------------------------------------------------------------------ multislice baseline
+// The row passes may skip the columns the anti-aliasing aperture zeroes (|kx| >= kx_half) only if
+// the initial probe is zero there too: a probe aperture wider than the anti-aliasing aperture keeps
+// every column (returns 0).
+static int probe_kx_half(int kx_half, const std::vector<float2> &pbase, int nx, int ny) {
+    for (int ky = 0; ky < ny && kx_half; ++ky)
+        for (int kx = kx_half; kx <= nx - kx_half; ++kx) {
+            const float2 v = pbase[(size_t)ky * nx + kx];
+            if (v.x != 0.f || v.y != 0.f) return 0;
+        }
+    return kx_half;
+}
+
 extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
                                    const prism_scan *sc, const prism_detector *det, float *out_dev,
                                    void *cuda_stream, size_t scratch_bytes) {
@@ -1089,17 +1101,7 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             }
         }
     }
-    // the row passes may skip the columns the aperture zeroes only if the initial probe is zero
-    // there too (a probe aperture wider than the anti-aliasing aperture keeps every column)
-    int kx_half = T.kx_half;
-    for (int ky = 0; ky < ny && kx_half; ++ky)
-        for (int kx = kx_half; kx <= nx - kx_half; ++kx) {
-            const float2 v = pbase[(size_t)ky * nx + kx];
-            if (v.x != 0.f || v.y != 0.f) {
-                kx_half = 0;
-                break;
-            }
-        }
+    const int kx_half = probe_kx_half(T.kx_half, pbase, nx, ny);
     std::vector<int> off, idx;
     detector_csr(nx, ny, g.cell_x, g.cell_y, 1, 1, T.lam, det, off, idx);
     if (scratch_bytes == 0) scratch_bytes = (size_t)1 << 30;
@@ -1416,6 +1418,8 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
             }
         }
     }
+    M.kx_half = probe_kx_half(T.kx_half, M.pbase, g.nx, g.ny);
+    M.band4 = T.band4;
     detector_csr(g.nx, g.ny, g.cell_x, g.cell_y, 1, 1, T.lam, det, M.bin_off, M.bin_idx);
     const long long Pn = (long long)sc->px * sc->py;
     M.pos.resize((size_t)Pn * 2);

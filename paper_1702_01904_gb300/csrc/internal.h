@@ -17,6 +17,8 @@ struct MsHostTables {
     std::vector<float2> prop_x, prop_y, twr_f, twr_i, twc_f, twc_i, pbase;
     std::vector<int> aa_kmax, bin_off, bin_idx;
     std::vector<double> pos;  // x0[P] then y0[P]
+    int kx_half = 0;          // row/column passes: kept columns |kx| < kx_half (0: all), as multislice_scan_run
+    int band4 = 0;            // column passes: the aperture keeps |ky| < ny/4 on every column
     Tw64 tw;
 };
 

@@ -172,6 +172,7 @@ extern "C" int multislice_scan_run_noalloc(const prism_grid *grid, const float *
             ra.tw_inv = twr_i;
             ra.ny = ny;
             ra.n_rows = nb * ny;
+            ra.kx_half = M.kx_half;
             ra.tw = M.tw;
             if ((rc = check(launch_row(nx, ROW_STD, ra, st), "row pass"))) return rc;
             const int pi = M.slice_prop[p];
@@ -180,6 +181,9 @@ extern "C" int multislice_scan_run_noalloc(const prism_grid *grid, const float *
             ca.prop_y = prop_y + (size_t)pi * ny;
             ca.inten = inten;
             ca.probe_base = nullptr;
+            // the detecting pass reads and writes every column, as in multislice_scan_run
+            ca.kx_half = p + 1 == H ? 0 : M.kx_half;
+            ca.band4 = M.band4;
             if ((rc = check(launch_col(ny, p + 1 == H ? COL_DETECT : COL_STD, ca, st), "column pass"))) return rc;
         }
         BinArgs ba;
