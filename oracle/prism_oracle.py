@@ -328,6 +328,19 @@ def frozen_phonon_scan(v_configs, grid, probe, det, x0s, y0s):
     return acc / len(v_configs)
 
 
+def periodic_probe_wave(a, m, n, nx, ny, f, fy):
+    """sum_b a_b exp(2 pi i q_b.r) on the grid, q_b = (m_b f / cx, n_b f_y / cy).
+
+    At the pixel centres r = (ix cx/nx, iy cy/ny) each plane wave is exp(2 pi i (m_b f ix / nx +
+    n_b f_y iy / ny)), the inverse-DFT basis function of the integer frequency (m_b f, n_b f_y).  So
+    the sum is the inverse 2-D DFT of a spectrum holding nx ny a_b at that frequency's FFT bin
+    (distinct beams occupy distinct bins).
+    """
+    spec = np.zeros((ny, nx), dtype=np.complex128)
+    spec[(n * fy) % ny, (m * f) % nx] = np.asarray(a) * (nx * ny)
+    return ifft2(spec)
+
+
 def prism_probe_direct(v_slices, grid, probe, det, x0, y0):
     """One PRISM probe by linearity of Eq. PRISMfinal, without the S-matrix.
 
@@ -339,9 +352,7 @@ def prism_probe_direct(v_slices, grid, probe, det, x0, y0):
     f, fy = interpolation_factors(grid)
     m, n = beam_set(nx, ny, cx, cy, grid["kv"], f, grid["alpha_mrad"], fy)
     a = probe_coefficients(m, n, grid, probe, x0, y0)
-    psi = np.zeros((ny, nx), dtype=np.complex128)
-    for b in range(len(m)):
-        psi += a[b] * plane_wave(nx, ny, cx, cy, float(m[b] * f) / cx, float(n[b] * fy) / cy)
+    psi = periodic_probe_wave(a, m, n, nx, ny, f, fy)
     psi = multislice(psi, transmission(v_slices, grid["kv"]), slice_propagators(grid))
     if grid.get("downsample", 2) == 2:
         psi = fourier_crop_half(psi)

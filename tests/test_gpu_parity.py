@@ -225,42 +225,7 @@ def test_small_workload_multislice(small_workload):
     assert_images_close(out, ref)
 
 
-# ------------------------------------------------------------------ the amorphous-carbon workload at full size, sampled
-@pytest.fixture(scope="module")
-def carbon_workload():
-    w = specimens.workload_amorphous_carbon()
-    V = w.potential()
-    g = grid_dict(w.nx, w.ny, w.cell_x, w.cell_y, w.n_slices, w.dz, w.f, ds=w.downsample, alpha=w.alpha_mrad)
-    return w, V, g
-
-
-def test_carbon_workload_sampled(carbon_workload):
-    w, V, g = carbon_workload
-    x0, y0 = w.scan_positions()
-    probe = P.make_probe(w.alpha_mrad)
-    sim = PrismSimulation(c_grid(g))
-    assert sim.info.n_beams == 129 and sim.info.nw_x == 64
-    sim.build(torch.from_numpy(V).cuda())
-    out = sim.scan(probe, x0, y0, det_c(DET), px=w.scan_px, py=w.scan_py).cpu().numpy()
-    S = sim.smatrix()
-    m, nn = sim.beams()
-    # two sampled beams of the S-matrix, each one oracle multislice of its plane wave
-    trans = O.transmission(V, g["kv"])
-    prop = O.slice_propagators(g)
-    for b in (0, 64):
-        pw = O.plane_wave(w.nx, w.ny, w.cell_x, w.cell_y, m[b] * w.f / w.cell_x, nn[b] * w.f / w.cell_y)
-        ref = O.fourier_crop_half(O.multislice(pw, trans, prop))
-        assert rel_l2(S[b].cpu().numpy(), ref) < 5e-5
-    # three sampled probes, each one oracle multislice of its periodic probe (linearity of Eq. PRISMfinal)
-    sel = [0, 20101, 39999]
-    ref = np.array([O.prism_probe_direct(V, g, dict(alpha_mrad=w.alpha_mrad), DET, x0[i], y0[i]) for i in sel])
-    assert_images_close(out[sel], ref)
-    # the binned intensity of every probe is the incident one up to the crop approximation of PRISM
-    # (the d/f window is not norm-preserving for the exit wave; the oracle shows the same excess)
-    tot = out.sum(1)
-    assert np.all(tot > 0.98) and np.all(tot < 1.01)
-    assert np.max(np.abs(tot[sel] - ref.sum(1))) < 1e-5
-    sim.close()
+# The amorphous-carbon workload at full size (sampled against the oracle) is in test_gpu_fullsize.py.
 
 
 # ------------------------------------------------------------------ properties, edge cases, errors

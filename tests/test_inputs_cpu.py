@@ -72,3 +72,35 @@ def test_projected_potential_slices_partition_the_atoms():
     v = S.project_potential(spec, 64, 64, 4, 2.0)
     assert np.count_nonzero(v.reshape(4, -1).max(1) > 0) == 1 and v[1].max() > 0
     assert abs(v.max() - S.V0_VA * 29 ** 0.7) / (S.V0_VA * 29 ** 0.7) < 1e-3
+
+
+def test_chunked_packing_spacing_density_and_seed():
+    a = S.random_packing_chunked((30.0, 30.0, 24.0), 2160, 1.4, seed=8, chunk=256)
+    assert a.xyz.shape == (2160, 3)
+    assert np.all(a.xyz >= 0) and np.all(a.xyz < (30.0, 30.0, 24.0))
+    assert min_spacing(a) >= 1.4
+    assert np.array_equal(S.random_packing_chunked((30.0, 30.0, 24.0), 2160, 1.4, seed=8, chunk=256).xyz, a.xyz)
+    # positions are uniform: each half of the cell along every axis holds about half the atoms
+    for ax, c in enumerate((30.0, 30.0, 24.0)):
+        assert abs(np.mean(a.xyz[:, ax] < c / 2) - 0.5) < 0.05
+
+
+def test_large_serving_cell_recipe():
+    # a thin version of the 2048^2 cell: the Au sphere on the entrance side, carbon below it
+    w = S.workload_nanoparticle_on_carbon(n_slices=8, particle_diameter=10.0)
+    s = w.specimen
+    assert (w.nx, w.ny, w.cell_x, w.f, w.n_slices, w.dz) == (2048, 2048, 102.4, 8, 8, 2.0)
+    au, c = s.xyz[s.z_number == 79], s.xyz[s.z_number == 6]
+    assert len(au) > 20 and np.all(au[:, 2] < 10.0 + 1e-9)
+    assert np.all(np.abs(au[:, :2] - 51.2).max(1) <= 5.0 + 1e-9)
+    assert abs(len(c) - 0.1 * 102.4 * 102.4 * 6.0) < 1 and np.all(c[:, 2] >= 10.0) and np.all(c[:, 2] < 16.0)
+    assert min_spacing(S.Specimen(c, s.z_number[s.z_number == 6], (102.4, 102.4, 16.0))) >= 1.4
+    # the full-thickness recipe: 40 A sphere over 160 A of carbon (about 168 000 carbon atoms)
+    assert round(0.1 * 102.4 * 102.4 * (200.0 - 40.0)) == 167772
+
+
+def test_vectorised_projection_equals_the_per_atom_one():
+    spec = S.nanoparticle_on_carbon(16.0, 8.0, 4.0, seed=9)
+    ref = S.project_potential(spec, 128, 128, 4, 2.0)
+    got = S.project_potential_vectorised(spec, 128, 128, 4, 2.0, chunk=37)
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(ref)

@@ -620,6 +620,22 @@ def test_rectangular_window_empty_sample_one_pixel_per_beam_and_linearity():
         assert np.max(np.abs(a - O.prism_probe_direct(v, g, PROBE, DET, x0, y0))) < 1e-12
 
 
+def test_periodic_probe_wave_is_the_plane_wave_sum():
+    # the spectrum form of sum_b a_b exp(2 pi i q_b.r) against the plane waves evaluated one by one,
+    # on a rectangular grid with f_x != f_y (a transposed or mis-scaled bin would fail)
+    rng = np.random.Generator(np.random.PCG64(12))
+    nx, ny, cx, cy, f, fy = 48, 32, 6.0, 4.0, 3, 2
+    m, n = O.beam_set(nx, ny, cx, cy, 300.0, f, 40.0, fy)
+    assert len(m) > 6 and len(set(zip(m, n))) == len(m)
+    a = rng.normal(size=len(m)) + 1j * rng.normal(size=len(m))
+    x = np.arange(nx) * (cx / nx)
+    y = np.arange(ny) * (cy / ny)
+    brute = np.zeros((ny, nx), dtype=complex)
+    for b in range(len(m)):
+        brute += a[b] * np.exp(2j * math.pi * (m[b] * f / cx * x[None, :] + n[b] * fy / cy * y[:, None]))
+    assert np.max(np.abs(O.periodic_probe_wave(a, m, n, nx, ny, f, fy) - brute)) < 1e-12 * len(m)
+
+
 # ------------------------------------------------------------------ identities the CUDA path relies on
 def test_first_slice_shift_theorem():
     # the first row transform of a plane wave times t_0 is the row transform of t_0 shifted by the
