@@ -415,6 +415,16 @@ int prism_selftest_bounded_wait(int *status_dev, long long limit_cycles, int arr
 double prism_wavelength(double kv);
 double prism_interaction_constant(double kv);
 
+/* Beam-set radius for a probe (PRISM Algorithm section: the maximum incident semi-angle should be
+ * the largest desired probe semi-angle plus f times the Fourier pixel size).  Writes to
+ * *alpha_max_mrad = probe->alpha_mrad + 1000 |tilt| + 1000 lambda max(f / cell_x, f_y / cell_y)
+ * (mrad; |tilt| = hypot(tilt_x, tilt_y) in rad, the tilted aperture's centre offset; f_y = 0 means
+ * f), the value to put in prism_grid.alpha_max_mrad so that the plan's plane-wave set holds every
+ * beam of the (tilted) probe with one lattice step of margin.  Reads grid->kv, f, f_y, cell_x and
+ * cell_y only.  Host-only, synchronous.  INVALID for NULL pointers, kv <= 0, f < 1, f_y < 0,
+ * cells <= 0 or a negative probe semi-angle. */
+int prism_recommended_alpha_max(const prism_grid *grid, const prism_probe *probe, double *alpha_max_mrad);
+
 /* ---- per-kernel timing ------------------------------------------------------------ */
 
 /* Kernel classes timed by the plan when profiling is on. */

@@ -68,6 +68,18 @@ extern "C" double prism_interaction_constant(double kv) {
     return 2.0 * PI * m * Q_ELECTRON * lam_m / (H_PLANCK * H_PLANCK) * 1e-10;
 }
 
+// alpha_max = largest probe semi-angle + f lambda dq (PRISM Algorithm section), plus the tilt of the
+// aperture's centre; dq on the coarser beam-lattice axis
+extern "C" int prism_recommended_alpha_max(const prism_grid *g, const prism_probe *probe, double *out) {
+    if (!g || !probe || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    if (!(g->kv > 0) || g->f < 1 || g->f_y < 0 || !(g->cell_x > 0) || !(g->cell_y > 0) || !(probe->alpha_mrad >= 0))
+        return fail(PRISM_ERR_INVALID, "prism_recommended_alpha_max: kv, f, f_y, cells or alpha out of range");
+    const int fy = g->f_y ? g->f_y : g->f;
+    const double step = std::max((double)g->f / g->cell_x, (double)fy / g->cell_y);
+    *out = probe->alpha_mrad + 1000.0 * std::hypot(probe->tilt_x, probe->tilt_y) + 1000.0 * prism_wavelength(g->kv) * step;
+    return PRISM_OK;
+}
+
 static inline int signed_index(int k, int n) { return k < n / 2 ? k : k - n; }
 static inline bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 

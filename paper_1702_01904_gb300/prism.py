@@ -43,7 +43,7 @@ EXPORTED = [
     "prism_scan_run_cbed", "prism_scan_run_accumulate",
     "multislice_scan_run", "multislice_scan_run_noalloc", "prism_plan_info", "prism_plan_smatrix_bytes", "prism_plan_beams",
     "prism_plan_smatrix", "prism_plan_smatrix_copy", "prism_plan_transmission", "prism_wavelength", "prism_interaction_constant",
-    "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
+    "prism_recommended_alpha_max", "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
     "prism_selftest_tcgen05", "prism_selftest_bounded_wait",
@@ -160,6 +160,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_transmission": (c_int, [P, POINTER(P)]),
         "prism_wavelength": (c_double, [c_double]),
         "prism_interaction_constant": (c_double, [c_double]),
+        "prism_recommended_alpha_max": (c_int, [POINTER(PrismGrid), POINTER(PrismProbe), POINTER(c_double)]),
         "prism_plan_set_profiling": (c_int, [P, c_int]),
         "prism_plan_kernel_stats": (c_int, [P, c_int, POINTER(c_long), POINTER(c_double)]),
         "prism_plan_launches": (c_long, [P]),
@@ -282,12 +283,6 @@ def prism_scan_run_accumulate(plan, probe, scan, det, weight, out_dev):
     return _check(load().prism_scan_run_accumulate(plan, byref(probe), byref(scan), byref(det), weight, _ptr(out_dev)))
 
 
-def recommended_alpha_max(probe_alpha_mrad, f, cell, kv, tilt_mrad=0.0):
-    """alpha_max = largest probe semi-angle + f * lambda * dq (PRISM Algorithm section), plus any
-    probe tilt, in mrad: the beam set that keeps the whole (tilted) aperture."""
-    return probe_alpha_mrad + abs(tilt_mrad) + 1000.0 * prism_wavelength(kv) * f / cell
-
-
 def multislice_scan_run(grid, V_dev, probe, scan, det, out_dev, cuda_stream=None, scratch_bytes=0):
     return _check(load().multislice_scan_run(byref(grid), _ptr(V_dev), byref(probe), byref(scan), byref(det),
                                              _ptr(out_dev), _stream(cuda_stream), scratch_bytes))
@@ -345,6 +340,14 @@ def prism_wavelength(kv):
 
 def prism_interaction_constant(kv):
     return load().prism_interaction_constant(kv)
+
+
+def prism_recommended_alpha_max(grid, probe):
+    """The plane-wave-set radius (mrad) that keeps every beam of `probe` with one lattice step of
+    margin (prism_recommended_alpha_max in include/prism.h)."""
+    out = c_double()
+    _check(load().prism_recommended_alpha_max(byref(grid), byref(probe), byref(out)))
+    return out.value
 
 
 def prism_plan_set_profiling(plan, enable=True):

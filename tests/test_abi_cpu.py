@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds and loads, exports every entry point the
 header declares, and the ctypes binding matches the header's constants and struct layouts."""
 import ctypes
+import math
 import os
 import re
 import subprocess
@@ -147,3 +148,42 @@ def test_no_cpu_fallback_without_a_gpu():
     with pytest.raises(RuntimeError):
         runtime.multislice(g, torch.zeros(1, 64, 64), P.make_probe(20.0), np.zeros(1), np.zeros(1),
                            P.make_detector(0.0, 1.0, 10))
+
+
+@pytest.mark.parametrize("f,f_y,cell_x,cell_y,alpha,tx,ty", [
+    (8, 0, 50.0, 50.0, 20.0, 0.0, 0.0),
+    (4, 0, 16.0, 16.0, 20.0, 0.004, -0.003),
+    (3, 2, 12.0, 8.0, 15.0, -0.006, 0.002),
+])
+def test_recommended_alpha_max_keeps_the_tilted_aperture_with_a_lattice_step_margin(f, f_y, cell_x, cell_y, alpha, tx, ty):
+    # the beam set of radius alpha_max (PRISM Algorithm section) must hold every lattice beam whose
+    # frequency lies within one lattice step of the tilted probe aperture lambda |q - q_t| <= alpha
+    from oracle import prism_oracle as O
+    kv = 300.0
+    g = P.make_grid(256, 256, 1, cell_x, cell_y, 2.0, kv, f, 2, 0.5, 0.0, f_y=f_y)
+    amax = P.prism_recommended_alpha_max(g, P.make_probe(alpha, tilt_x=tx, tilt_y=ty))
+    lam = O.wavelength(kv)
+    fy = f_y or f
+    m, n = O.beam_set(256, 256, cell_x, cell_y, kv, f, amax, fy)
+    have = set(zip(m.tolist(), n.tolist()))
+    step = max(f / cell_x, fy / cell_y)  # the coarser lattice step (1/A)
+    qtx, qty = tx / lam, ty / lam
+    r = int(amax / (1000 * lam * min(f / cell_x, fy / cell_y))) + 2
+    needed = 0
+    for mm in range(-r, r + 1):
+        for nn in range(-r, r + 1):
+            qx, qy = mm * f / cell_x, nn * fy / cell_y
+            if math.hypot(qx - qtx, qy - qty) <= alpha * 1e-3 / lam + step * (1 - 1e-9):
+                needed += 1
+                assert (mm, nn) in have, (mm, nn)
+    assert needed > 0
+
+
+def test_recommended_alpha_max_rejects_bad_arguments():
+    g = P.make_grid(64, 64, 1, 8.0, 8.0, 2.0, 300.0, 0)
+    with pytest.raises(P.PrismError) as e:
+        P.prism_recommended_alpha_max(g, P.make_probe(20.0))
+    assert e.value.status == P.PRISM_ERR_INVALID
+    g = P.make_grid(64, 64, 1, 8.0, 8.0, 2.0, 300.0, 2)
+    with pytest.raises(P.PrismError):
+        P.prism_recommended_alpha_max(g, P.make_probe(-1.0))
