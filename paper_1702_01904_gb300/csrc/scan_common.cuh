@@ -221,7 +221,9 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
         }
     }
     // annular bins: one thread per (window, bin) walks the bin's pixel list with four interleaved
-    // FP32 partial sums (fixed order; relative error <= (n/4 + 2) 2^-24 for n pixels), FP64 scale.
+    // FP32 partial sums of the FP32 intensities (fixed order; each partial carries a relative error
+    // <= (n/4) 2^-24 for n pixels), then adds the four partials and applies the normalisation in
+    // FP64 (the final accumulation of the bin), rounding once to FP32.
     // The lists are read by rank (entry i of bin k at bin_idx_t[i * nbins + k]), so the threads of
     // consecutive bins read consecutive words.
     if (a.out) {
@@ -248,7 +250,7 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
                 const float2 z = w[(u >> LNW) * PW + (u & (NWX - 1))];
                 s0 = fmaf(z.x, z.x, fmaf(z.y, z.y, s0));
             }
-            const float val = (float)((double)((s0 + s1) + (s2 + s3)) * a.inv_norm);
+            const float val = (float)((((double)s0 + (double)s1) + ((double)s2 + (double)s3)) * a.inv_norm);
             float *o = a.out + (size_t)oidx[p] * a.nbins + k;
             *o = a.accumulate ? *o + a.acc_w * val : val;
         }
