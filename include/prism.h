@@ -46,6 +46,7 @@ extern "C" {
 #define PRISM_ERR_DEVICE      -4  /* a kernel raised the device error flag: one of its bounded
                                      waits ran out (tensor-core scan, TMA-staged tiles or rows)    */
 #define PRISM_ERR_UNSUPPORTED -5  /* valid but not implemented here (e.g. non power-of-two N)   */
+#define PRISM_ERR_CANCELLED   -6  /* a serving request was cancelled (prism_server_cancel)        */
 
 /* Simulation grid and PRISM build parameters.
  *   nx, ny       wave / potential grid, powers of two in [16, 2048].
@@ -259,6 +260,11 @@ typedef struct prism_request_stats {
     double total_ms;    /* submission -> result in out_host              */
     int smatrix_reused; /* 1 if a resident S-matrix served the request  */
     int status;         /* PRISM_OK or the request's error code          */
+    double device_start_ms; /* when the request's stream reached its first operation (S-matrix
+                               build or scan) and when it finished its last (the copy of the
+                               result), in ms of device time since the server was created (CUDA
+                               events); -1 when the request never ran on the device */
+    double device_end_ms;
 } prism_request_stats;
 
 typedef struct prism_server_info {
@@ -284,6 +290,12 @@ int prism_server_submit(prism_server *server, const prism_request *req, unsigned
  * after a wait that does not time out.  stats may be NULL. */
 int prism_server_wait(prism_server *server, unsigned long long ticket, double timeout_s, prism_request_stats *stats);
 int prism_server_stats(prism_server *server, prism_server_info *out);
+/* Cancel a request.  A queued request leaves the queue at once; a running one finishes its device
+ * work (kernels are never interrupted) but its result is discarded and out_host is not written.
+ * Either way its prism_server_wait returns PRISM_ERR_CANCELLED.  INVALID for an unknown ticket or a
+ * request that has already completed.  (Failure handling of the serving loop; no counterpart in the
+ * paper.) */
+int prism_server_cancel(prism_server *server, unsigned long long ticket);
 /* Finish the queued and running requests, release every S-matrix and stop the worker. */
 void prism_server_destroy(prism_server *server);
 

@@ -64,10 +64,13 @@ struct Job {
     float *out_pinned = nullptr;
     size_t out_bytes = 0;
     cudaEvent_t done = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // device timestamps of the request's work
+    double dev_start_ms = -1.0, dev_end_ms = -1.0;
     Clock::time_point t_submit, t_admit, t_done;
     int status = PRISM_OK;
     int reused = 0;
     bool finished = false;
+    bool cancelled = false;
     std::string error;
 };
 
@@ -95,6 +98,7 @@ struct prism_server {
     std::vector<std::shared_ptr<Resident>> anonymous;             // key 0: freed after the request
     size_t used = 0, peak_used = 0;
     long admitted = 0, completed = 0;
+    cudaEvent_t ref = nullptr;  // device-time origin of the request timestamps
     // worker-side helpers (called with mu held)
     void loop();
     bool try_admit(std::shared_ptr<Job> &j);
@@ -225,6 +229,8 @@ bool prism_server::try_admit(std::shared_ptr<Job> &j) {
     peak_used = std::max(peak_used, used);
     auto bail = [&](int code, const std::string &msg) {
         fail_job(j, code, msg);
+        if (j->ev_start) cudaEventDestroy(j->ev_start);
+        j->ev_start = nullptr;
         res->users--;
         used -= extra;
         if (j->out_dev) cudaFreeAsync(j->out_dev, st);
@@ -242,6 +248,10 @@ bool prism_server::try_admit(std::shared_ptr<Job> &j) {
         return bail(PRISM_ERR_CUDA, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     if ((e = cudaMallocHost(&j->out_pinned, j->out_bytes ? j->out_bytes : 16)) != cudaSuccess)
         return bail(PRISM_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    if (ref && (cudaEventCreate(&j->ev_start) != cudaSuccess || cudaEventRecord(j->ev_start, st) != cudaSuccess)) {
+        if (j->ev_start) cudaEventDestroy(j->ev_start);
+        j->ev_start = nullptr;
+    }
     if (!res->built) {
         if ((rc = prism_build_smatrix_host(res->plan, j->V_host)) != PRISM_OK) return bail(rc, prism_last_error());
         res->built = true;
@@ -253,6 +263,10 @@ bool prism_server::try_admit(std::shared_ptr<Job> &j) {
     if ((e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventRecord(j->done, st)) != cudaSuccess)
         return bail(PRISM_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    if (j->ev_start && (cudaEventCreate(&j->ev_end) != cudaSuccess || cudaEventRecord(j->ev_end, st) != cudaSuccess)) {
+        if (j->ev_end) cudaEventDestroy(j->ev_end);
+        j->ev_end = nullptr;
+    }
     running.push_back(j);
     admitted++;
     return true;
@@ -269,9 +283,22 @@ void prism_server::reap() {
         if (q != cudaSuccess) {
             j->status = PRISM_ERR_CUDA;
             j->error = std::string("request failed on the device: ") + cudaGetErrorString(q);
+        } else if (j->cancelled) {
+            j->status = PRISM_ERR_CANCELLED;
+            j->error = "request " + std::to_string(j->ticket) + " was cancelled (its result was discarded)";
         } else if (j->out_bytes) {
             std::memcpy(j->out_host, j->out_pinned, j->out_bytes);
         }
+        if (q == cudaSuccess && j->ev_start && j->ev_end) {
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, ref, j->ev_start) == cudaSuccess && cudaEventElapsedTime(&b, ref, j->ev_end) == cudaSuccess) {
+                j->dev_start_ms = a;
+                j->dev_end_ms = b;
+            }
+        }
+        if (j->ev_start) cudaEventDestroy(j->ev_start);
+        if (j->ev_end) cudaEventDestroy(j->ev_end);
+        j->ev_start = j->ev_end = nullptr;
         cudaEventDestroy(j->done);
         cudaFreeAsync(j->out_dev, j->res->stream);
         cudaFreeHost(j->out_pinned);
@@ -321,6 +348,16 @@ extern "C" int prism_server_create(size_t hbm_budget_bytes, int max_inflight, pr
     S->budget = hbm_budget_bytes;
     S->max_inflight = max_inflight;
     cudaGetDevice(&S->device);
+    // device-time origin for the requests' timestamps (recorded once, completed before any request)
+    cudaStream_t s0 = nullptr;
+    if (cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking) == cudaSuccess) {
+        if (cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, s0) != cudaSuccess ||
+            cudaStreamSynchronize(s0) != cudaSuccess) {
+            if (S->ref) cudaEventDestroy(S->ref);
+            S->ref = nullptr;
+        }
+        cudaStreamDestroy(s0);
+    }
     S->worker = std::thread([S] { S->loop(); });
     *out = S;
     return PRISM_OK;
@@ -376,6 +413,8 @@ extern "C" int prism_server_wait(prism_server *S, unsigned long long ticket, dou
         stats->total_ms = ms_since(j->t_submit, j->t_done);
         stats->smatrix_reused = j->reused;
         stats->status = j->status;
+        stats->device_start_ms = j->dev_start_ms;
+        stats->device_end_ms = j->dev_end_ms;
     }
     S->jobs.erase(it);
     if (j->status != PRISM_OK) return prism::internal_fail(j->status, j->error.c_str());
@@ -395,6 +434,23 @@ extern "C" int prism_server_stats(prism_server *S, prism_server_info *out) {
     return PRISM_OK;
 }
 
+extern "C" int prism_server_cancel(prism_server *S, unsigned long long ticket) {
+    if (!S) return prism::internal_fail(PRISM_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->jobs.find(ticket);
+    if (it == S->jobs.end() || it->second->finished)
+        return prism::internal_fail(PRISM_ERR_INVALID, ("no queued or running request " + std::to_string(ticket)).c_str());
+    auto j = it->second;
+    auto q = std::find(S->pending.begin(), S->pending.end(), j);
+    if (q != S->pending.end()) {  // still queued: leaves the queue now
+        S->pending.erase(q);
+        S->fail_job(j, PRISM_ERR_CANCELLED, "request " + std::to_string(ticket) + " was cancelled before it ran");
+        return PRISM_OK;
+    }
+    j->cancelled = true;  // running: the worker discards its result when its device work is done
+    return PRISM_OK;
+}
+
 extern "C" void prism_server_destroy(prism_server *S) {
     if (!S) return;
     {
@@ -407,5 +463,6 @@ extern "C" void prism_server_destroy(prism_server *S) {
         prism_plan_destroy(kv.second->plan);
         cudaStreamDestroy(kv.second->stream);
     }
+    if (S->ref) cudaEventDestroy(S->ref);
     delete S;
 }

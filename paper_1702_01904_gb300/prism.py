@@ -22,6 +22,7 @@ PRISM_ERR_BUDGET = -2
 PRISM_ERR_CUDA = -3
 PRISM_ERR_DEVICE = -4
 PRISM_ERR_UNSUPPORTED = -5
+PRISM_ERR_CANCELLED = -6
 
 PRISM_K_TRANSMIT, PRISM_K_ROW_PLANE, PRISM_K_ROW, PRISM_K_COL, PRISM_K_ROW_OUT, PRISM_K_SCAN, PRISM_K_QUANT, PRISM_K_PLANE = range(8)
 PRISM_K_COUNT = 8
@@ -46,6 +47,7 @@ EXPORTED = [
     "prism_recommended_alpha_max", "prism_plan_set_profiling", "prism_plan_kernel_stats", "prism_plan_launches", "prism_plan_reset_stats",
     "prism_kernel_name",
     "prism_server_create", "prism_server_submit", "prism_server_wait", "prism_server_stats", "prism_server_destroy",
+    "prism_server_cancel",
     "prism_selftest_tcgen05", "prism_selftest_bounded_wait",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
     "prism_plan_autotune", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
@@ -92,7 +94,8 @@ class PrismRequest(ctypes.Structure):
 
 
 class PrismRequestStats(ctypes.Structure):
-    _fields_ = [("queued_ms", c_double), ("total_ms", c_double), ("smatrix_reused", c_int), ("status", c_int)]
+    _fields_ = [("queued_ms", c_double), ("total_ms", c_double), ("smatrix_reused", c_int), ("status", c_int),
+                ("device_start_ms", c_double), ("device_end_ms", c_double)]
 
 
 class PrismServerInfo(ctypes.Structure):
@@ -171,6 +174,7 @@ def load(path: str = LIB_PATH):
         "prism_server_wait": (c_int, [P, ctypes.c_ulonglong, c_double, POINTER(PrismRequestStats)]),
         "prism_server_stats": (c_int, [P, POINTER(PrismServerInfo)]),
         "prism_server_destroy": (None, [P]),
+        "prism_server_cancel": (c_int, [P, ctypes.c_ulonglong]),
         "prism_selftest_tcgen05": (c_int, [P, P, P]),
         "prism_selftest_bounded_wait": (c_int, [P, ctypes.c_longlong, c_int, P]),
     }
@@ -396,6 +400,10 @@ def prism_server_stats(server):
     info = PrismServerInfo()
     _check(load().prism_server_stats(server, byref(info)))
     return info
+
+
+def prism_server_cancel(server, ticket):
+    _check(load().prism_server_cancel(server, ticket))
 
 
 def prism_server_destroy(server):

@@ -273,6 +273,11 @@ class Server:
     def stats(self):
         return P.prism_server_stats(self.srv)
 
+    def cancel(self, ticket):
+        """Cancel a queued or running request: its wait() then raises PrismError(PRISM_ERR_CANCELLED)
+        and its output array is left as it was."""
+        P.prism_server_cancel(self.srv, ticket)
+
     def close(self):
         if getattr(self, "srv", None) is not None:
             P.prism_server_destroy(self.srv)

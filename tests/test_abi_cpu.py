@@ -73,6 +73,13 @@ int main(void) {
   F(prism_batch_info, graph_nodes) F(prism_batch_info, kernel_launches) F(prism_batch_info, device_bytes)
   printf("prism_tune_entry %zu\\n", sizeof(prism_tune_entry));
   F(prism_tune_entry, default_shape) F(prism_tune_entry, ms)
+  printf("prism_request %zu\\n", sizeof(prism_request));
+  printf("prism_request_stats %zu\\n", sizeof(prism_request_stats));
+  printf("prism_server_info %zu\\n", sizeof(prism_server_info));
+  F(prism_request, V_host) F(prism_request, smatrix_key) F(prism_request, probe) F(prism_request, scan)
+  F(prism_request, det) F(prism_request, out_host)
+  F(prism_request_stats, status) F(prism_request_stats, device_start_ms) F(prism_request_stats, device_end_ms)
+  F(prism_server_info, admitted) F(prism_server_info, peak_bytes)
   return 0;
 }
 """)
@@ -82,7 +89,9 @@ int main(void) {
                                                                 check=True).stdout.split("\n") if line)
     cls = {"prism_grid": P.PrismGrid, "prism_probe": P.PrismProbe, "prism_scan": P.PrismScan,
            "prism_detector": P.PrismDetector, "prism_info": P.PrismInfo, "prism_cell": P.PrismCell,
-           "prism_batch_info": P.PrismBatchInfo, "prism_tune_entry": P.PrismTuneEntry}
+           "prism_batch_info": P.PrismBatchInfo, "prism_tune_entry": P.PrismTuneEntry,
+           "prism_request": P.PrismRequest, "prism_request_stats": P.PrismRequestStats,
+           "prism_server_info": P.PrismServerInfo}
     for k, v in out.items():
         if "." in k:
             s, m = k.split(".")
