@@ -493,6 +493,10 @@ def main():
 
         for _ in range(args.warmup):
             step()
+        if not args.no_autotune:
+            # the scan's contraction tile shape, timed on this scan (every shape writes the same stack)
+            sim.autotune_scan(probe, x0, y0, det, out=out, px=w.scan_px, py=w.scan_py)
+            tune = sim.tune_result()
         stream.synchronize()
         sim.reset_stats()
         sim.set_profiling(False)  # the headline region runs without per-launch events

@@ -313,6 +313,7 @@ void prism_server_destroy(prism_server *server);
  * S-matrix is untouched).  The paper has no counterpart. */
 #define PRISM_TUNE_ROW 0
 #define PRISM_TUNE_COL 1
+#define PRISM_TUNE_SCAN 2  /* contraction tile shape of the FP32 GEMM scan (prism_plan_autotune_scan) */
 #define PRISM_TUNE_MAX_SHAPES 8
 typedef struct prism_tune_entry {
     int n_shapes;                     /* shapes listed for the pass                              */
@@ -321,13 +322,24 @@ typedef struct prism_tune_entry {
     double ms[PRISM_TUNE_MAX_SHAPES]; /* mean time per launch of each shape, -1 if not compiled   */
 } prism_tune_entry;
 int prism_plan_autotune(prism_plan *plan);
+/* The scan's contraction tile shape (the scan term of the Calculation Time section's cost model):
+ * raster blocks of 4 x 8, 8 x 4 or 2 x 16 probes and beam rings of 2 x 32 or 3 x 16, compiled for
+ * the FP32 GEMM scan with square windows of 16, 32 or 64 pixels.  Runs the given scan once per
+ * shape (a warm-up and two timed launches, CUDA events on the plan's stream), keeps the fastest
+ * for the plan's later scans (prism_plan_tune_result with PRISM_TUNE_SCAN) and leaves the detector
+ * stack in out_dev: every shape sums each pixel over the beams in the same order, so all give
+ * bitwise the same stack.  Other plans (16-bit modes, other windows) just run the scan.  Arguments
+ * and errors as prism_scan_run; synchronous.  No counterpart in the paper. */
+int prism_plan_autotune_scan(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
+                             const prism_detector *det, float *out_dev);
 int prism_plan_tune_result(const prism_plan *plan, int kind, prism_tune_entry *out);
 const char *prism_tune_shape_name(int kind, int shape);
-/* Pin the launch shape of one pass for the plan's later builds without timing: `shape` indexes the
- * pass's list (prism_tune_shape_name), -1 restores the default launcher.  PRISM_ERR_INVALID for a
- * NULL plan or a kind outside {PRISM_TUNE_ROW, PRISM_TUNE_COL}; PRISM_ERR_UNSUPPORTED for a shape
- * not compiled for the plan's N, or one that stages through TMA when the plan holds no tensor map
- * of its wave scratch.  Every shape computes bitwise the same result. */
+/* Pin the launch shape of one pass (or the scan's contraction shape, PRISM_TUNE_SCAN) for the
+ * plan's later builds (scans) without timing: `shape` indexes the kind's list
+ * (prism_tune_shape_name), -1 restores the default.  PRISM_ERR_INVALID for a NULL plan or a kind
+ * outside {PRISM_TUNE_ROW, PRISM_TUNE_COL, PRISM_TUNE_SCAN}; PRISM_ERR_UNSUPPORTED for a shape not
+ * compiled for the plan's N (window), or one that stages through TMA when the plan holds no tensor
+ * map of its wave scratch.  Every shape computes bitwise the same result. */
 int prism_plan_set_tune_shape(prism_plan *plan, int kind, int shape);
 
 /* ---- batches of uneven cells: one captured CUDA graph ------------------------------

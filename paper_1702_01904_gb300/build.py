@@ -21,9 +21,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh", "tune_shapes.cuh")] + \
+HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh", "tune_shapes.cuh", "scan_gemm.cuh")] + \
     [os.path.join(INCLUDE, "prism.h")]
-CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_row.cu", "kernels_scan.cu", "kernels_tc.cu", "noalloc.cu"]
+CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_row.cu", "kernels_scan.cu", "kernels_tune_scan.cu",
+              "kernels_tc.cu", "noalloc.cu"]
 HOST_UNITS = ["engine.cpp", "server.cpp"]
 
 

@@ -389,6 +389,9 @@ struct prism_plan {
     int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
     double tune_ms[2][PRISM_TUNE_MAX_SHAPES];
     bool tuned[2] = {false, false};
+    int scan_shape = 0;            // contraction tile shape of the FP32 GEMM scan (0: default)
+    double scan_ms[PRISM_TUNE_MAX_SHAPES];
+    bool scan_tuned = false;
     float2 *prop_x = nullptr, *prop_y = nullptr;
     int *aa_kmax = nullptr;
     float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr, *tww_fy = nullptr;
@@ -974,15 +977,22 @@ static int split_counters(prism_plan *P, ScanArgs &a, int grid) {
 // window scratch grown on demand)
 // FP32: the GEMM scan over 8 x 4 raster blocks when its shared memory fits (grid > 0), else the
 // grouped / per-probe kernels (grid 0); 16-bit: the tensor-core scan
+// the GEMM scan's contraction shape in use: the tuned or pinned one where it is compiled for the
+// plan's window, else the default
+static int gemm_shape(const prism_plan *P) {
+    return P->scan_shape > 0 && scan_gemm_shape_valid(P->nw, P->nwy, P->scan_shape) ? P->scan_shape : 0;
+}
+
 static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
     *grid = 0;
     if (P->prec == PRISM_PRECISION_FP32) {
-        *grid = scan_gemm_grid(P->nw, P->nwy, P->nbeams, a.scan_px, a.scan_py);
+        const int sh = gemm_shape(P);
+        *grid = scan_gemm_grid(P->nw, P->nwy, sh, P->nbeams, a.scan_px, a.scan_py);
         if (*grid <= 0) {
             *grid = 0;
             return PRISM_OK;
         }
-        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, *grid, a.scan_px, a.scan_py));
+        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, sh, *grid, a.scan_px, a.scan_py));
         if (rc) return rc;
         return split_counters(P, a, *grid);
     }
@@ -996,7 +1006,8 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
 static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
     if (P->prec == PRISM_PRECISION_FP32)
         return plan_launch(P, PRISM_K_SCAN, [&] {
-            return grid > 0 ? launch_scan_gemm(P->nw, P->nwy, grid, a, P->stream) : launch_scan_rect(P->nw, P->nwy, a, P->stream);
+            return grid > 0 ? launch_scan_gemm(P->nw, P->nwy, gemm_shape(P), grid, a, P->stream)
+                            : launch_scan_rect(P->nw, P->nwy, a, P->stream);
         });
     return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), grid, a, P->stream); });
 }
@@ -1462,7 +1473,14 @@ static std::map<TuneKey, TuneVal> g_tune_cache;
 
 extern "C" int prism_plan_set_tune_shape(prism_plan *P, int kind, int shape) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
-    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "kind must be PRISM_TUNE_ROW or PRISM_TUNE_COL");
+    if (kind == PRISM_TUNE_SCAN) {
+        if (shape >= 0 && (P->prec != PRISM_PRECISION_FP32 || shape >= scan_gemm_shapes() || !scan_gemm_shape_valid(P->nw, P->nwy, shape)))
+            return fail(PRISM_ERR_UNSUPPORTED, std::string("contraction shape ") + std::to_string(shape) + " is not compiled for this plan's "
+                                                   "scan (FP32 GEMM scan, square windows of 16, 32 or 64 pixels)");
+        P->scan_shape = shape < 0 ? 0 : shape;
+        return PRISM_OK;
+    }
+    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "kind must be PRISM_TUNE_ROW, PRISM_TUNE_COL or PRISM_TUNE_SCAN");
     if (shape >= 0) {
         const int n = kind == PRISM_TUNE_ROW ? P->g.nx : P->g.ny;
         if (shape >= tune_shapes(kind) || !tune_shape_valid(kind, n, shape))
@@ -1545,6 +1563,14 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
 
 extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_entry *out) {
     if (!P || !out) return fail(PRISM_ERR_INVALID, "NULL argument");
+    if (kind == PRISM_TUNE_SCAN) {
+        const bool gemm = P->prec == PRISM_PRECISION_FP32;
+        out->n_shapes = gemm ? std::min(scan_gemm_shapes(), PRISM_TUNE_MAX_SHAPES) : 0;
+        out->chosen = gemm ? gemm_shape(P) : -1;
+        out->default_shape = gemm ? 0 : -1;
+        for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) out->ms[v] = P->scan_tuned ? P->scan_ms[v] : -1.0;
+        return PRISM_OK;
+    }
     if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "bad tune kind");
     const int n = kind == 0 ? P->g.nx : P->g.ny;
     out->n_shapes = std::min(tune_shapes(kind), PRISM_TUNE_MAX_SHAPES);
@@ -1555,7 +1581,61 @@ extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_
     return PRISM_OK;
 }
 
-extern "C" const char *prism_tune_shape_name(int kind, int shape) { return tune_shape_name(kind, shape); }
+extern "C" const char *prism_tune_shape_name(int kind, int shape) {
+    return kind == PRISM_TUNE_SCAN ? scan_gemm_shape_name(shape) : tune_shape_name(kind, shape);
+}
+
+// The scan's contraction tile shape (Calculation Time section: the scan term P B N^2 / (4 f^4) is
+// the rate-limiting one for large f): run the caller's scan once per compiled shape (one warm-up and
+// two timed launches each, CUDA events on the plan's stream), keep the fastest for the plan's later
+// scans.  Every shape writes bitwise the same detector stack, which is left in out_dev.
+extern "C" int prism_plan_autotune_scan(prism_plan *P, const prism_probe *probe, const prism_scan *sc,
+                                        const prism_detector *det, float *out_dev) {
+    if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    ScanArgs a;
+    int rc = scan_prepare(P, probe, sc, det, a);
+    if (rc) return rc;
+    if (a.n_probes == 0) return PRISM_OK;
+    if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
+    a.out = out_dev;
+    if (P->prec != PRISM_PRECISION_FP32) return scan_launch(P, a);  // one shape: just the scan
+    for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->scan_ms[v] = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = 0;
+    double best_ms = -1.0;
+    for (int v = 0; v < scan_gemm_shapes() && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
+        if (!scan_gemm_shape_valid(P->nw, P->nwy, v)) continue;
+        P->scan_shape = v;
+        int grid = 0;
+        if ((rc = scan_setup(P, a, &grid))) break;
+        if (grid <= 0) continue;  // this shape's coefficient block does not fit shared memory
+        if ((rc = scan_go(P, a, grid))) break;
+        cudaError_t e = cudaEventRecord(e0, P->stream);
+        for (int r = 0; r < 2 && e == cudaSuccess && !rc; ++r) rc = scan_go(P, a, grid);
+        if (rc) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(PRISM_ERR_CUDA, std::string("scan autotune ") + scan_gemm_shape_name(v) + ": " + cudaGetErrorString(e));
+            break;
+        }
+        P->scan_ms[v] = ms / 2.0;
+        if (best_ms < 0 || ms / 2.0 < best_ms) {
+            best = v;
+            best_ms = ms / 2.0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->scan_shape = best;
+    P->scan_tuned = !rc;
+    if (rc) return rc;
+    return scan_launch(P, a);  // the detector stack of the chosen shape (bitwise that of every shape)
+}
 
 // ------------------------------------------------------------------ batches of cells (one CUDA graph)
 struct prism_batch {

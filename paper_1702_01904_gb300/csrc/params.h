@@ -144,12 +144,19 @@ cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
 // per side) through the grouped kernel; scan_rect_supported says whether a launch can succeed
 cudaError_t launch_scan_rect(int nwx, int nwy, const ScanArgs &a, cudaStream_t s);
 bool scan_rect_supported(int nwx, int nwy, int n_beams);
-// FP32 GEMM scan over 8 x 4 raster blocks (window sides 16, 32, 64): persistent grid (0 if it does
-// not fit), launch, and the window scratch it needs ([grid][32][nwy][nwx] complex64)
-int scan_gemm_grid(int nwx, int nwy, int n_beams, int scan_px, int scan_py);
-cudaError_t launch_scan_gemm(int nwx, int nwy, int grid, const ScanArgs &a, cudaStream_t s);
+// FP32 GEMM scan over raster blocks of 32 probes (window sides 16, 32, 64) in one of the
+// contraction tile shapes (0 = default 4 x 8 blocks; the others for square windows): persistent
+// grid (0 if it does not fit), launch, and the window scratch it needs
+int scan_gemm_grid(int nwx, int nwy, int shape, int n_beams, int scan_px, int scan_py);
+cudaError_t launch_scan_gemm(int nwx, int nwy, int shape, int grid, const ScanArgs &a, cudaStream_t s);
 // window scratch of the FP32 GEMM scan: one slot per CTA plus one per split group of the last round
-size_t scan_gemm_win_bytes(int nwx, int nwy, int grid, int scan_px, int scan_py);
+size_t scan_gemm_win_bytes(int nwx, int nwy, int shape, int grid, int scan_px, int scan_py);
+// the contraction shapes: count, whether one is compiled for a window, its name; the tuned unit
+int scan_gemm_shapes();
+bool scan_gemm_shape_valid(int nwx, int nwy, int shape);
+const char *scan_gemm_shape_name(int shape);
+int scan_gemm_grid_tuned(int nwx, int nwy, int shape, int n_beams, int scan_px, int scan_py);
+cudaError_t launch_scan_gemm_tuned(int nwx, int nwy, int shape, int grid, const ScanArgs &a, cudaStream_t s);
 // completion counters of the split groups (int[grid]; zeroed once, each launch leaves them zero)
 size_t scan_gemm_cnt_bytes(int grid);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);

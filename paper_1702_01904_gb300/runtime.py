@@ -100,13 +100,27 @@ class PrismSimulation:
         P.prism_plan_autotune(self.plan)
         return self.tune_result()
 
+    def autotune_scan(self, probe, x0, y0, det, out: torch.Tensor | None = None, px=None, py=None):
+        """Run this scan once per contraction tile shape of the FP32 GEMM scan, keep the fastest for
+        later scans (prism_plan_autotune_scan); returns the detector stack (the same for every shape)."""
+        x0 = np.ascontiguousarray(x0, np.float64)
+        y0 = np.ascontiguousarray(y0, np.float64)
+        n = len(x0)
+        px = n if px is None else px
+        py = 1 if py is None else py
+        assert px * py == n
+        if out is None:
+            out = torch.empty((n, det.nbins), dtype=torch.float32, device="cuda")
+        P.prism_plan_autotune_scan(self.plan, probe, P.make_scan(px, py, x0, y0), det, out)
+        return out
+
     def set_shape(self, kind, shape):
         """Pin one pass's launch shape by index (prism_plan_set_tune_shape); -1 restores the default."""
         P.prism_plan_set_tune_shape(self.plan, kind, shape)
 
     def tune_result(self):
         out = {}
-        for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col")):
+        for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col"), (P.PRISM_TUNE_SCAN, "scan")):
             e = P.prism_plan_tune_result(self.plan, kind)
             name = (lambda v: P.prism_tune_shape_name(kind, v) if v >= 0 else "default")
             out[label] = {"chosen": name(e.chosen), "default": name(e.default_shape),

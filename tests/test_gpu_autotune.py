@@ -119,3 +119,50 @@ def test_autotuned_batch_equals_untuned():
         b.close()
     for u, t in zip(*outs):
         assert np.array_equal(u, t)
+
+
+@pytest.mark.parametrize("n,cell,f,px,py,step", [(256, 16.0, 4, 13, 9, 0.3), (256, 32.0, 8, 10, 21, 0.45),
+                                                (512, 32.0, 4, 23, 17, 0.25)])
+def test_every_scan_contraction_shape_is_bitwise_identical(n, cell, f, px, py, step):
+    # FP32 GEMM scan with 32-, 16- and 64-pixel windows: raster blocks 4 x 8, 8 x 4, 2 x 16 and beam
+    # rings 2 x 32, 3 x 16 sum every window pixel over the beams in the same order; ragged rasters
+    # (px, py not multiples of the block sides) cover partial blocks and the split last round
+    grid = P.make_grid(n, n, 3, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0)
+    V = rand_v(3, n, 21)
+    X, Y = np.meshgrid(0.7 + step * np.arange(px), cell - 1.0 + step * np.arange(py))  # wraps in y
+    x0, y0 = X.ravel(), Y.ravel()
+    probe = P.make_probe(20.0, c1=12.0)
+    sim = PrismSimulation(grid)
+    sim.build(V)
+    nw = sim.info.nw_x
+    assert nw == n // 2 // f
+    ref = sim.scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy()
+    n_shapes = P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes
+    assert n_shapes == 5
+    for v in range(n_shapes):
+        sim.set_shape(P.PRISM_TUNE_SCAN, v)
+        got = sim.scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy()
+        assert np.array_equal(got, ref), P.prism_tune_shape_name(P.PRISM_TUNE_SCAN, v)
+    sim.set_shape(P.PRISM_TUNE_SCAN, -1)
+    out = sim.autotune_scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy()
+    assert np.array_equal(out, ref)
+    res = sim.tune_result()["scan"]
+    assert len(res["ms"]) == n_shapes and all(t > 0 for t in res["ms"].values())
+    assert res["ms"][res["chosen"]] == min(res["ms"].values())
+    assert np.array_equal(sim.scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy(), ref)
+    sim.close()
+
+
+def test_scan_shape_limits():
+    # 16-bit plans have one (tensor-core) scan shape; shapes past the list are refused
+    grid = P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0, precision=P.PRISM_PRECISION_FP16)
+    sim = PrismSimulation(grid)
+    with pytest.raises(P.PrismError) as e:
+        sim.set_shape(P.PRISM_TUNE_SCAN, 1)
+    assert e.value.status == P.PRISM_ERR_UNSUPPORTED
+    assert P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes == 0
+    sim.close()
+    sim = PrismSimulation(P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0))
+    with pytest.raises(P.PrismError):
+        sim.set_shape(P.PRISM_TUNE_SCAN, 5)
+    sim.close()

@@ -130,3 +130,38 @@ def test_batch_errors():
     bad = cells_of([dict(SPECS[0], prec=P.PRISM_PRECISION_FP16, f=4)], 85)  # 8-pixel window: no 16-bit scan
     st, msg = code(lambda: Batch(cells + bad))
     assert st == P.PRISM_ERR_UNSUPPORTED and "cell 2" in msg
+
+
+def test_uneven_workload_cells_in_one_graph_match_oracle():
+    # five cells of the seeded 64-cell uneven workload spanning N = 256, 512, 1024 and f = 4, 8
+    # (seeds 126, 112, 150, 132, 136: 10-17 slices, 49 to about 830 beams), run together in one graph
+    # launch with their 16 x 16 raster scans; four probes of each against the oracle (one
+    # multislice of each probe's d/f-periodic wave, Eq. PRISMfinal linearity)
+    import oracle_pool
+    from paper_1702_01904_gb300 import specimens
+    seeds = (126, 112, 150, 132, 136)
+    cells, work = [], []
+    for s in seeds:
+        w, V = specimens.batch_cell_potential(s)
+        x0, y0 = w.scan_positions()
+        cells.append(dict(grid=P.grid_from_workload(w), V=torch.from_numpy(V).cuda(), probe=P.make_probe(w.alpha_mrad),
+                          x0=x0, y0=y0, px=w.scan_px, py=w.scan_py, det=DET))
+        work.append((w, V, x0, y0))
+    assert {w.nx for w, *_ in work} == {256, 512, 1024} and {w.f for w, *_ in work} == {4, 8}
+    b = Batch(cells, n_branches=4)
+    b.run()
+    b.sync()
+    det = dict(start_mrad=0.0, step_mrad=1.0, nbins=100)
+    for (w, V, x0, y0), out in zip(work, b.outs):
+        g = dict(nx=w.nx, ny=w.ny, cell_x=w.cell_x, cell_y=w.cell_y, n_slices=w.n_slices, dz=w.dz, kv=w.kv, f=w.f,
+                 downsample=w.downsample, aa_frac=w.aa_frac, alpha_mrad=w.alpha_mrad)
+        pick = [0, 17, 130, 255]
+        ref = np.array(oracle_pool.evaluate("prism", V, g, [(dict(alpha_mrad=w.alpha_mrad), det, float(x0[k]), float(y0[k]))
+                                                             for k in pick]))
+        got = out.cpu().numpy().astype(np.float64)[pick]
+        bright = ref.mean(0) >= 1e-7
+        assert bright.sum() >= 10
+        err = O.rel_l2_per_image(got[:, bright], ref[:, bright]).max()
+        assert err <= 1e-4, (w.name, err)
+        assert np.max(np.abs(got[:, ~bright] - ref[:, ~bright])) <= 1e-9
+    b.close()
