@@ -164,11 +164,14 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             };
 #pragma unroll
             for (int l = 0; l < S - 1; ++l) load(ls0 + l);
-            float2 acc[4][4];
+            // psi = sum_b S_b Re(alpha_b) + i sum_b S_b Im(alpha_b): two complex accumulators per
+            // (pixel, probe), each advanced by one packed FP32x2 FMA of the S value with a real
+            // coefficient (accr += S Re a, acci += S Im a), combined when the M tile is done
+            float2 accr[4][4], acci[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+                for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = make_float2(0.f, 0.f);
             for (int ls = ls0; ls < ls1; ++ls) {
                 const int mt = ls / nkc, c = ls - mt * nkc;
                 cp_async_wait<S - 2>();
@@ -182,15 +185,17 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
 #pragma unroll 4
                     for (int kk = 0; kk < bn; ++kk) {
                         const float4 a01 = al[(size_t)kk * (G / 2)], a23 = al[(size_t)kk * (G / 2) + 1];
-                        const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
-                                              make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+                        const float2 ar[4] = {make_float2(a01.x, a01.x), make_float2(a01.z, a01.z),
+                                              make_float2(a23.x, a23.x), make_float2(a23.z, a23.z)};
+                        const float2 ai[4] = {make_float2(a01.y, a01.y), make_float2(a01.w, a01.w),
+                                              make_float2(a23.y, a23.y), make_float2(a23.w, a23.w)};
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const float2 sv = cur[kk * MT + lane + 32 * i];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                acc[i][j].x = fmaf(av[j].x, sv.x, fmaf(-av[j].y, sv.y, acc[i][j].x));
-                                acc[i][j].y = fmaf(av[j].x, sv.y, fmaf(av[j].y, sv.x, acc[i][j].y));
+                                accr[i][j] = __ffma2_rn(sv, ar[j], accr[i][j]);
+                                acci[i][j] = __ffma2_rn(sv, ai[j], acci[i][j]);
                             }
                         }
                     }
@@ -207,9 +212,11 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                                 const int p = 4 * warp + j;
                                 const bool act = uni ? meta[136 + p] >= 0 : p == sg;
                                 const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
+                                // psi = accr + i acci
+                                const float2 v = make_float2(accr[i][j].x - acci[i][j].y, accr[i][j].y + acci[i][j].x);
                                 if (act && idx < npx && (unsigned)wy < (unsigned)NWY && (unsigned)wx < (unsigned)NWX)
-                                    __stcs(a.win + ((size_t)slot * G + p) * (NWX * NWY) + wy * NWX + wx, acc[i][j]);
-                                acc[i][j] = make_float2(0.f, 0.f);
+                                    __stcs(a.win + ((size_t)slot * G + p) * (NWX * NWY) + wy * NWX + wx, v);
+                                accr[i][j] = acci[i][j] = make_float2(0.f, 0.f);
                             }
                         }
                     }
