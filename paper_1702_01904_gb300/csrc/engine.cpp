@@ -100,7 +100,15 @@ static float2 phase_cycles(double c) {
 
 static Tw64 make_tw64() {
     Tw64 t;
-    for (int j = 0; j < 64; ++j) t.w[j] = wN(j, 64);
+    for (int j = 0; j < 64; ++j) {
+        t.w[j] = wN(j, 64);
+        // tangent form (the kernels pick the same form from j at compile time)
+        const double a = -2.0 * PI * (double)j / 64.0, c = std::cos(a), s = std::sin(a);
+        const bool tan_form = (j & 31) <= 8 || (j & 31) >= 24;
+        const float sc = (float)(tan_form ? c : s);
+        t.sc[j] = make_float2(sc, sc);
+        t.tk[j] = (float)(tan_form ? s / c : c / s);
+    }
     return t;
 }
 

@@ -72,6 +72,97 @@ __device__ __forceinline__ float2 twiddle64(float2 a, const Tw64 &tw) {
     }
 }
 
+// fn(std::integral_constant<int, r>) for r = 0 ... N-1, unrolled at compile time (lets the body
+// branch on compile-time properties of the register index)
+template <class Fn, int... Is>
+__device__ __forceinline__ void static_for_impl(Fn &fn, std::integer_sequence<int, Is...>) {
+    (fn(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class Fn>
+__device__ __forceinline__ void static_for(Fn fn) {
+    static_for_impl(fn, std::make_integer_sequence<int, N>{});
+}
+// Tangent form of W_64^J (INV: of its conjugate), for butterflies that take the twiddle's scale
+// into a packed FMA: W y = s u with
+//   |cos| >= |sin| ((J mod 32) <= 8 or >= 24): s = cos, k = tan, u = (y.x - k y.y, y.y + k y.x)
+//   otherwise:                                   s = sin, k = cot, u = (k y.x - y.y, k y.y + y.x)
+// (the conjugate flips k, and in the cot form also s).  Multiples of 16 are free rotations and are
+// not put in this form.
+template <int J>
+struct TanForm {
+    static constexpr int j = J & 63;
+    static constexpr bool tan = (j & 31) <= 8 || (j & 31) >= 24;
+    static constexpr bool rotation = (j & 15) == 0;  // 1, -i, -1, +i: no multiply
+};
+
+template <int J, bool INV>
+__device__ __forceinline__ float2 tan_u(float2 y, const Tw64 &tw) {
+    constexpr int j = TanForm<J>::j;
+    const float k = tw.tk[j];
+    if constexpr (TanForm<J>::tan) {
+        return INV ? make_float2(fmaf(k, y.y, y.x), fmaf(-k, y.x, y.y)) : make_float2(fmaf(-k, y.y, y.x), fmaf(k, y.x, y.y));
+    } else {
+        return INV ? make_float2(fmaf(-k, y.x, -y.y), fmaf(-k, y.y, y.x)) : make_float2(fmaf(k, y.x, -y.y), fmaf(k, y.y, y.x));
+    }
+}
+
+template <int J, bool INV>
+__device__ __forceinline__ float2 tan_s(const Tw64 &tw) {
+    const float2 s = tw.sc[TanForm<J>::j];
+    return (!TanForm<J>::tan && INV) ? make_float2(-s.x, -s.y) : s;
+}
+
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// DFT-4 of (x[0], W^J1 x[S], W^J2 x[2S], W^J3 x[3S]) (W = W_64, conjugated for INV), natural order
+// in and out, with every twiddle in tangent form: its scale enters the butterfly's packed FMA, so a
+// twiddled input costs 2 FP32 lane operations on top of the plain DFT-4 instead of 4.
+template <int J1, int J2, int J3, int S, bool INV>
+struct Dft4Tw {
+    __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
+        using F1 = TanForm<J1>;
+        using F2 = TanForm<J2>;
+        using F3 = TanForm<J3>;
+        const float2 x0 = x[0];
+        float2 A, B, C, D;  // x0 +- W^J2 x2, W^J1 x1 +- W^J3 x3
+        if constexpr (F2::rotation) {
+            const float2 v2 = twiddle64<J2, INV>(x[2 * S], tw);
+            A = cadd(x0, v2);
+            B = csub(x0, v2);
+        } else {
+            const float2 u2 = tan_u<J2, INV>(x[2 * S], tw), s2 = tan_s<J2, INV>(tw);
+            A = __ffma2_rn(s2, u2, x0);
+            B = __ffma2_rn(cneg(s2), u2, x0);
+        }
+        if constexpr (F1::rotation && F3::rotation) {
+            const float2 v1 = twiddle64<J1, INV>(x[S], tw), v3 = twiddle64<J3, INV>(x[3 * S], tw);
+            C = cadd(v1, v3);
+            D = csub(v1, v3);
+        } else if constexpr (F1::rotation) {
+            const float2 v1 = twiddle64<J1, INV>(x[S], tw);
+            const float2 u3 = tan_u<J3, INV>(x[3 * S], tw), s3 = tan_s<J3, INV>(tw);
+            C = __ffma2_rn(s3, u3, v1);
+            D = __ffma2_rn(cneg(s3), u3, v1);
+        } else if constexpr (F3::rotation) {
+            const float2 v3 = twiddle64<J3, INV>(x[3 * S], tw);
+            const float2 u1 = tan_u<J1, INV>(x[S], tw), s1 = tan_s<J1, INV>(tw);
+            C = __ffma2_rn(s1, u1, v3);
+            D = __ffma2_rn(s1, u1, cneg(v3));
+        } else {
+            const float2 u1 = tan_u<J1, INV>(x[S], tw), s1 = tan_s<J1, INV>(tw);
+            const float2 u3 = tan_u<J3, INV>(x[3 * S], tw), s3 = tan_s<J3, INV>(tw);
+            const float2 p1 = __fmul2_rn(s1, u1);
+            C = __ffma2_rn(s3, u3, p1);
+            D = __ffma2_rn(cneg(s3), u3, p1);
+        }
+        const float2 rd = rot4<INV>(D);
+        x[0] = cadd(A, C);
+        x[2 * S] = csub(A, C);
+        x[S] = cadd(B, rd);
+        x[3 * S] = csub(B, rd);
+    }
+};
+
 // In-place DFT of R elements x[0], x[S], ..., x[(R-1)S]; natural order in and out.
 template <int R, int S, bool INV>
 struct Dft;
@@ -114,11 +205,8 @@ struct Dft<8, S, INV> {
             b[k] = cadd(x[k * S], x[(k + 4) * S]);
             c[k] = csub(x[k * S], x[(k + 4) * S]);
         }
-        c[1] = twiddle64<8, INV>(c[1], tw);
-        c[2] = rot4<INV>(c[2]);
-        c[3] = twiddle64<24, INV>(c[3], tw);
         Dft<4, 1, INV>::run(b, tw);
-        Dft<4, 1, INV>::run(c, tw);
+        Dft4Tw<8, 16, 24, 1, INV>::run(c, tw);  // c_k W_8^k, then the DFT-4
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             x[(2 * m) * S] = b[m];
@@ -155,10 +243,18 @@ struct Dft {
         // stage 1: DFT over n1 of elements (R2 n1 + n2) for each n2
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) Dft<R1, R2 * S, INV>::run(x + n2 * S, tw);
-        DftTw<R1, R2, S, INV, R2>::template go<0>(x, tw);
-        // stage 2: DFT over n2 of elements (R2 k1 + n2) for each k1 -> X[k1 + R1 k2] at (R2 k1 + k2)
+        // stage 2: DFT over n2 of elements (R2 k1 + n2) times W_R^{n2 k1}, for each k1 -> X[k1 + R1 k2]
+        // at (R2 k1 + k2); radix 4 with the twiddles in the butterflies, else twiddles then DFTs
+        if constexpr (R2 == 4) {
+            static_for<R1>([&](auto kc) {
+                constexpr int k1 = decltype(kc)::value, jj = k1 * (64 / R);
+                Dft4Tw<jj, 2 * jj, 3 * jj, S, INV>::run(x + R2 * k1 * S, tw);
+            });
+        } else {
+            DftTw<R1, R2, S, INV, R2>::template go<0>(x, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV>::run(x + R2 * k1 * S, tw);
+            for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV>::run(x + R2 * k1 * S, tw);
+        }
         float2 tmp[R];
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1)
@@ -261,16 +357,6 @@ struct BlockFft {
 // the compiler removes their arithmetic from the first and the last register DFT.
 enum { BAND_IN = 0, BAND_OUT = 1, BAND_MIXED = 2 };
 
-// fn(std::integral_constant<int, r>) for r = 0 ... N-1, unrolled at compile time (lets the body
-// branch on compile-time properties of the register index)
-template <class Fn, int... Is>
-__device__ __forceinline__ void static_for_impl(Fn &fn, std::integer_sequence<int, Is...>) {
-    (fn(std::integral_constant<int, Is>{}), ...);
-}
-template <int N, class Fn>
-__device__ __forceinline__ void static_for(Fn fn) {
-    static_for_impl(fn, std::make_integer_sequence<int, N>{});
-}
 template <class F, int N>
 struct BandClass {
     __host__ __device__ static constexpr bool in_band(int e) { return e < N / 4 || e > N - N / 4; }

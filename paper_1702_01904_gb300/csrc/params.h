@@ -11,7 +11,11 @@
 namespace prism {
 
 struct Tw64 {
-    float2 w[64];  // W_64^j = exp(-2 pi i j / 64)
+    float2 w[64];   // W_64^j = exp(-2 pi i j / 64)
+    // tangent form of the same twiddles, W_64^j = s (1 + i k) when |cos| >= |sin| (s = cos, k = tan;
+    // (j mod 32) <= 8 or >= 24), else W_64^j = s (k + i) (s = sin, k = cot): sc[j] = (s, s), tk[j] = k
+    float2 sc[64];
+    float tk[64];
 };
 
 enum RowMode { ROW_STD = 0, ROW_PLANE = 1, ROW_OUT = 2 };
