@@ -114,99 +114,139 @@ __device__ __forceinline__ float2 tan_s(const Tw64 &tw) {
 
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// Known zeros.  The codelets below take a compile-time mask Z of inputs that are exactly zero in
+// every thread (bit i: element i S), e.g. the frequencies the anti-aliasing aperture removed, and
+// leave out the arithmetic on them (the compiler may not drop x + 0 itself: -0 + 0 is +0).
+__host__ __device__ constexpr bool zbit(unsigned long long z, int i) { return (z >> i) & 1ull; }
+
+template <bool ZA, bool ZB>
+__device__ __forceinline__ float2 zadd(float2 a, float2 b) {
+    if constexpr (ZA && ZB) return make_float2(0.f, 0.f);
+    else if constexpr (ZB) return a;
+    else if constexpr (ZA) return b;
+    else return cadd(a, b);
+}
+template <bool ZA, bool ZB>
+__device__ __forceinline__ float2 zsub(float2 a, float2 b) {
+    if constexpr (ZA && ZB) return make_float2(0.f, 0.f);
+    else if constexpr (ZB) return a;
+    else if constexpr (ZA) return cneg(b);
+    else return csub(a, b);
+}
+
+// One input of a twiddled DFT-4: exactly zero, a plain value (twiddle 1 or a free rotation), or
+// s u (a tangent-form twiddle, see tan_u / tan_s).
+enum { TERM_ZERO = 0, TERM_PLAIN = 1, TERM_SCALED = 2 };
+template <int J, bool Z, bool INV>
+struct Term {
+    static constexpr int kind = Z ? TERM_ZERO : TanForm<J>::rotation ? TERM_PLAIN : TERM_SCALED;
+    float2 v, s;  // PLAIN: v; SCALED: u in v, scale in s
+    __device__ __forceinline__ Term(float2 y, const Tw64 &tw) {
+        if constexpr (kind == TERM_PLAIN) {
+            v = twiddle64<J, INV>(y, tw);
+        } else if constexpr (kind == TERM_SCALED) {
+            v = tan_u<J, INV>(y, tw);
+            s = tan_s<J, INV>(tw);
+        }
+    }
+};
+// a + b and a - b of two terms (plain results); a SCALED a and b share the product s_a u_a
+template <class TA, class TB>
+__device__ __forceinline__ void term_sum_diff(const TA &a, const TB &b, float2 &sum, float2 &diff) {
+    constexpr int ka = TA::kind, kb = TB::kind;
+    if constexpr (ka == TERM_ZERO && kb == TERM_ZERO) {
+        sum = diff = make_float2(0.f, 0.f);
+    } else if constexpr (kb == TERM_ZERO) {
+        sum = diff = ka == TERM_PLAIN ? a.v : __fmul2_rn(a.s, a.v);
+    } else if constexpr (ka == TERM_ZERO) {
+        sum = kb == TERM_PLAIN ? b.v : __fmul2_rn(b.s, b.v);
+        diff = kb == TERM_PLAIN ? cneg(b.v) : __fmul2_rn(cneg(b.s), b.v);
+    } else if constexpr (ka == TERM_PLAIN && kb == TERM_PLAIN) {
+        sum = cadd(a.v, b.v);
+        diff = csub(a.v, b.v);
+    } else if constexpr (ka == TERM_PLAIN) {
+        sum = __ffma2_rn(b.s, b.v, a.v);
+        diff = __ffma2_rn(cneg(b.s), b.v, a.v);
+    } else if constexpr (kb == TERM_PLAIN) {
+        sum = __ffma2_rn(a.s, a.v, b.v);
+        diff = __ffma2_rn(a.s, a.v, cneg(b.v));
+    } else {
+        const float2 p = __fmul2_rn(a.s, a.v);
+        sum = __ffma2_rn(b.s, b.v, p);
+        diff = __ffma2_rn(cneg(b.s), b.v, p);
+    }
+}
+
 // DFT-4 of (x[0], W^J1 x[S], W^J2 x[2S], W^J3 x[3S]) (W = W_64, conjugated for INV), natural order
 // in and out, with every twiddle in tangent form: its scale enters the butterfly's packed FMA, so a
-// twiddled input costs 2 FP32 lane operations on top of the plain DFT-4 instead of 4.
-template <int J1, int J2, int J3, int S, bool INV>
+// twiddled input costs 2 FP32 lane operations on top of the plain DFT-4 instead of 4.  Z: known
+// zero inputs.
+template <int J1, int J2, int J3, int S, bool INV, unsigned long long Z = 0>
 struct Dft4Tw {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
-        using F1 = TanForm<J1>;
-        using F2 = TanForm<J2>;
-        using F3 = TanForm<J3>;
-        const float2 x0 = x[0];
+        const Term<0, zbit(Z, 0), INV> t0(x[0], tw);
+        const Term<J1, zbit(Z, 1), INV> t1(x[S], tw);
+        const Term<J2, zbit(Z, 2), INV> t2(x[2 * S], tw);
+        const Term<J3, zbit(Z, 3), INV> t3(x[3 * S], tw);
         float2 A, B, C, D;  // x0 +- W^J2 x2, W^J1 x1 +- W^J3 x3
-        if constexpr (F2::rotation) {
-            const float2 v2 = twiddle64<J2, INV>(x[2 * S], tw);
-            A = cadd(x0, v2);
-            B = csub(x0, v2);
-        } else {
-            const float2 u2 = tan_u<J2, INV>(x[2 * S], tw), s2 = tan_s<J2, INV>(tw);
-            A = __ffma2_rn(s2, u2, x0);
-            B = __ffma2_rn(cneg(s2), u2, x0);
-        }
-        if constexpr (F1::rotation && F3::rotation) {
-            const float2 v1 = twiddle64<J1, INV>(x[S], tw), v3 = twiddle64<J3, INV>(x[3 * S], tw);
-            C = cadd(v1, v3);
-            D = csub(v1, v3);
-        } else if constexpr (F1::rotation) {
-            const float2 v1 = twiddle64<J1, INV>(x[S], tw);
-            const float2 u3 = tan_u<J3, INV>(x[3 * S], tw), s3 = tan_s<J3, INV>(tw);
-            C = __ffma2_rn(s3, u3, v1);
-            D = __ffma2_rn(cneg(s3), u3, v1);
-        } else if constexpr (F3::rotation) {
-            const float2 v3 = twiddle64<J3, INV>(x[3 * S], tw);
-            const float2 u1 = tan_u<J1, INV>(x[S], tw), s1 = tan_s<J1, INV>(tw);
-            C = __ffma2_rn(s1, u1, v3);
-            D = __ffma2_rn(s1, u1, cneg(v3));
-        } else {
-            const float2 u1 = tan_u<J1, INV>(x[S], tw), s1 = tan_s<J1, INV>(tw);
-            const float2 u3 = tan_u<J3, INV>(x[3 * S], tw), s3 = tan_s<J3, INV>(tw);
-            const float2 p1 = __fmul2_rn(s1, u1);
-            C = __ffma2_rn(s3, u3, p1);
-            D = __ffma2_rn(cneg(s3), u3, p1);
-        }
+        term_sum_diff(t0, t2, A, B);
+        term_sum_diff(t1, t3, C, D);
+        constexpr bool zac = zbit(Z, 0) && zbit(Z, 2), zc = zbit(Z, 1) && zbit(Z, 3);
         const float2 rd = rot4<INV>(D);
-        x[0] = cadd(A, C);
-        x[2 * S] = csub(A, C);
-        x[S] = cadd(B, rd);
-        x[3 * S] = csub(B, rd);
+        x[0] = zadd<zac, zc>(A, C);
+        x[2 * S] = zsub<zac, zc>(A, C);
+        x[S] = zadd<zac, zc>(B, rd);
+        x[3 * S] = zsub<zac, zc>(B, rd);
     }
 };
 
-// In-place DFT of R elements x[0], x[S], ..., x[(R-1)S]; natural order in and out.
-template <int R, int S, bool INV>
+// In-place DFT of R elements x[0], x[S], ..., x[(R-1)S]; natural order in and out.  Z: inputs known
+// to be exactly zero (bit i: element i S).
+template <int R, int S, bool INV, unsigned long long Z = 0>
 struct Dft;
 
-template <int S, bool INV>
-struct Dft<1, S, INV> {
+template <int S, bool INV, unsigned long long Z>
+struct Dft<1, S, INV, Z> {
     __device__ __forceinline__ static void run(float2 *, const Tw64 &) {}
 };
 
-template <int S, bool INV>
-struct Dft<2, S, INV> {
+template <int S, bool INV, unsigned long long Z>
+struct Dft<2, S, INV, Z> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
         float2 a = x[0], b = x[S];
-        x[0] = cadd(a, b);
-        x[S] = csub(a, b);
+        x[0] = zadd<zbit(Z, 0), zbit(Z, 1)>(a, b);
+        x[S] = zsub<zbit(Z, 0), zbit(Z, 1)>(a, b);
     }
 };
 
-template <int S, bool INV>
-struct Dft<4, S, INV> {
+template <int S, bool INV, unsigned long long Z>
+struct Dft<4, S, INV, Z> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
-        float2 t0 = cadd(x[0], x[2 * S]);
-        float2 t1 = csub(x[0], x[2 * S]);
-        float2 t2 = cadd(x[S], x[3 * S]);
-        float2 t3 = rot4<INV>(csub(x[S], x[3 * S]));
-        x[0] = cadd(t0, t2);
-        x[2 * S] = csub(t0, t2);
-        x[S] = cadd(t1, t3);
-        x[3 * S] = csub(t1, t3);
+        constexpr bool z0 = zbit(Z, 0), z1 = zbit(Z, 1), z2 = zbit(Z, 2), z3 = zbit(Z, 3);
+        float2 t0 = zadd<z0, z2>(x[0], x[2 * S]);
+        float2 t1 = zsub<z0, z2>(x[0], x[2 * S]);
+        float2 t2 = zadd<z1, z3>(x[S], x[3 * S]);
+        float2 t3 = rot4<INV>(zsub<z1, z3>(x[S], x[3 * S]));
+        x[0] = zadd<z0 && z2, z1 && z3>(t0, t2);
+        x[2 * S] = zsub<z0 && z2, z1 && z3>(t0, t2);
+        x[S] = zadd<z0 && z2, z1 && z3>(t1, t3);
+        x[3 * S] = zsub<z0 && z2, z1 && z3>(t1, t3);
     }
 };
 
-template <int S, bool INV>
-struct Dft<8, S, INV> {
+template <int S, bool INV, unsigned long long Z>
+struct Dft<8, S, INV, Z> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
         // decimation in frequency: b_k = a_k + a_{k+4} (even outputs), c_k = (a_k - a_{k+4}) W8^k (odd)
         float2 b[4], c[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            b[k] = cadd(x[k * S], x[(k + 4) * S]);
-            c[k] = csub(x[k * S], x[(k + 4) * S]);
-        }
-        Dft<4, 1, INV>::run(b, tw);
-        Dft4Tw<8, 16, 24, 1, INV>::run(c, tw);  // c_k W_8^k, then the DFT-4
+        static_for<4>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            b[k] = zadd<zbit(Z, k), zbit(Z, k + 4)>(x[k * S], x[(k + 4) * S]);
+            c[k] = zsub<zbit(Z, k), zbit(Z, k + 4)>(x[k * S], x[(k + 4) * S]);
+        });
+        constexpr unsigned long long ZH = (Z & (Z >> 4)) & 15ull;  // b_k, c_k zero when both inputs are
+        Dft<4, 1, INV, ZH>::run(b, tw);
+        Dft4Tw<8, 16, 24, 1, INV, ZH>::run(c, tw);  // c_k W_8^k, then the DFT-4
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             x[(2 * m) * S] = b[m];
@@ -234,23 +274,44 @@ struct DftTw {
     }
 };
 
-template <int R, int S, bool INV>
+// bits n1 < R1 of a mask over elements R2 n1 + n2 (the inputs of stage-1 sub-DFT n2)
+template <int R1, int R2>
+__host__ __device__ constexpr unsigned long long sub_mask(unsigned long long z, int n2) {
+    unsigned long long m = 0;
+    for (int n1 = 0; n1 < R1; ++n1)
+        if (zbit(z, R2 * n1 + n2)) m |= 1ull << n1;
+    return m;
+}
+// stage-2 inputs known zero: those of stage-1 sub-DFTs whose inputs were all zero
+template <int R1, int R2>
+__host__ __device__ constexpr unsigned long long stage2_mask(unsigned long long z) {
+    unsigned long long m = 0;
+    for (int n2 = 0; n2 < R2; ++n2)
+        if (sub_mask<R1, R2>(z, n2) == (R1 >= 64 ? ~0ull : ((1ull << R1) - 1))) m |= 1ull << n2;
+    return m;
+}
+
+template <int R, int S, bool INV, unsigned long long Z>
 struct Dft {
     static constexpr int R1 = DftSplit<R>::R1;
     static constexpr int R2 = DftSplit<R>::R2;
     static_assert(R1 > 0, "unsupported register DFT size");
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
         // stage 1: DFT over n1 of elements (R2 n1 + n2) for each n2
-#pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) Dft<R1, R2 * S, INV>::run(x + n2 * S, tw);
+        static_for<R2>([&](auto nc) {
+            constexpr int n2 = decltype(nc)::value;
+            Dft<R1, R2 * S, INV, sub_mask<R1, R2>(Z, n2)>::run(x + n2 * S, tw);
+        });
         // stage 2: DFT over n2 of elements (R2 k1 + n2) times W_R^{n2 k1}, for each k1 -> X[k1 + R1 k2]
         // at (R2 k1 + k2); radix 4 with the twiddles in the butterflies, else twiddles then DFTs
+        constexpr unsigned long long Z2 = stage2_mask<R1, R2>(Z);
         if constexpr (R2 == 4) {
             static_for<R1>([&](auto kc) {
                 constexpr int k1 = decltype(kc)::value, jj = k1 * (64 / R);
-                Dft4Tw<jj, 2 * jj, 3 * jj, S, INV>::run(x + R2 * k1 * S, tw);
+                Dft4Tw<jj, 2 * jj, 3 * jj, S, INV, Z2>::run(x + R2 * k1 * S, tw);
             });
         } else {
+            static_assert(Z2 == 0, "known-zero stage-2 inputs need the radix-4 stage");
             DftTw<R1, R2, S, INV, R2>::template go<0>(x, tw);
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV>::run(x + R2 * k1 * S, tw);
@@ -292,11 +353,14 @@ struct BlockFft {
 
     // GTW: the twiddle table is in global memory (read through the read-only path); otherwise it
     // is in shared memory
-    template <class Ex, bool GTW = false>
+    // ZIN: input registers known to be exactly zero in every thread (bit r: register r)
+    template <class Ex, bool GTW = false, unsigned long long ZIN = 0>
     __device__ __forceinline__ static void run(float2 (&x)[E], int t, const float2 *__restrict__ stw,
                                                const Tw64 &tw, Ex &ex) {
-#pragma unroll
-        for (int j = 0; j < J; ++j) Dft<N1, J, INV>::run(x + j, tw);
+        static_for<J>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            Dft<N1, J, INV, sub_mask<N1, J>(ZIN, j)>::run(x + j, tw);
+        });
         if constexpr (!GTW) {
             // shared-memory table: all twiddle loads before any exchange store (the table and the
             // exchange share the address space, and this order lets the loads issue back to back)
@@ -369,6 +433,15 @@ struct BandClass {
         return any_in && any_out ? BAND_MIXED : any_in ? BAND_IN : BAND_OUT;
     }
 };
+
+// registers that hold a band-outside element in every thread (input or output layout): known zeros
+template <class F, int N>
+__host__ __device__ constexpr unsigned long long band_zero_mask(bool input) {
+    unsigned long long m = 0;
+    for (int r = 0; r < F::E; ++r)
+        if (BandClass<F, N>::of(r, input) == BAND_OUT) m |= 1ull << r;
+    return m;
+}
 
 template <int N>
 using FwdFft = BlockFft<FftShape<N>::N1, FftShape<N>::N2, false>;

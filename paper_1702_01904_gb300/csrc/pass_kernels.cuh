@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
     using Inv = InvFft<NX>;
     constexpr int T = C::T, E = FS::E;
     static_assert(!TM || (BL && T == 32 && MODE != ROW_PLANE), "bulk staging: compile-time band, one slot per warp");
+    // with the compile-time band the inverse transform's out-of-band inputs are exact zeros
+    constexpr unsigned long long ZIN = BL && MODE != ROW_PLANE ? band_zero_mask<Inv, NX>(true) : 0ull;
     extern __shared__ float2 smem[];
     __shared__ __align__(8) uint64_t rbar[C::SLOTS];  // TM: a slot's next row has landed
     uint32_t rphase = 0;
@@ -251,16 +253,16 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                     float2 tv[E];
 #pragma unroll
                     for (int r = 0; r < E; ++r) tv[r] = __ldcg(tp + Inv::out_elem(r, t));
-                    Inv::run(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], tv[r]);
                 } else {
-                    Inv::run(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], __ldcg(tp + Inv::out_elem(r, t)));
                 }
             } else {
-                Inv::run(v, t, twi, a.tw, exI);
+                Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
             }
         }
         if constexpr (MODE == ROW_OUT) {
@@ -517,7 +519,9 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                 continue;
             }
         }
-        Inv::template run<decltype(exI), !C::SMEM_TW>(v, t, twi, a.tw, exI);
+        // after the propagator the out-of-band registers are exact zeros (band4, compile-time band)
+        constexpr unsigned long long ZC = BL && MODE != COL_PROBE ? band_zero_mask<Fwd, NY>(false) : 0ull;
+        Inv::template run<decltype(exI), !C::SMEM_TW, ZC>(v, t, twi, a.tw, exI);
         if constexpr (MODE == COL_PROBE) {
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = cscale(v[r], a.probe_scale);
