@@ -83,6 +83,12 @@ bool tune_shape_needs_map(int kind, int v) { return kind == 1 && v >= 0 && v < N
 
 bool tune_shape_fills_sm(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].mb >= 3; }
 
+int tune_row_staged_shape(int thr) {
+    for (int v = 0; v < N_ROW; ++v)
+        if (ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma && ROW_SHAPES[v].a == thr) return v;
+    return -1;
+}
+
 int tune_col_tma_shape(int w) {
     for (int v = 0; v < N_COL; ++v)
         if (COL_SHAPES[v].tma && COL_SHAPES[v].a == w) return v;

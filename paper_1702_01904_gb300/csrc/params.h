@@ -185,6 +185,7 @@ int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
 bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
 int tune_col_tma_shape(int w);                // the TMA-staged column shape of w columns per CTA, or -1
+int tune_row_staged_shape(int thr);           // the cp.async-staged row shape of thr threads per CTA, or -1
 bool tune_shape_fills_sm(int kind, int v);    // 3 or more CTAs per SM, each with a third of its resources
 cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s);
