@@ -1225,7 +1225,7 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             ra.n_rows = nb * ny;
             ra.kx_half = kx_half;  // every row pass reads a wave band-limited in x (aperture and probe)
             ra.tw = tw;
-            if ((rc = check(launch_row(nx, ROW_STD, ra, st), "row pass"))) return done(rc);
+            if ((rc = check(launch_row_std(nx, ra, st), "row pass"))) return done(rc);
             const int pi = T.slice_prop[p];
             ColArgs ca = col_args(T, wave, prop_x + (size_t)pi * nx, prop_y + (size_t)pi * ny, aa, twc_f, twc_i, tw);
             ca.batch = nb;

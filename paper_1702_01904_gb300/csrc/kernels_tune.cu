@@ -83,6 +83,14 @@ bool tune_shape_needs_map(int kind, int v) { return kind == 1 && v >= 0 && v < N
 
 bool tune_shape_fills_sm(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].mb >= 3; }
 
+cudaError_t launch_row_std(int nx, const RowArgs &a, cudaStream_t s) {
+    if (nx == 1024) {
+        const int v = tune_row_staged_shape(256);
+        if (v >= 0 && tune_row_valid(1024, v)) return tune_row_launch(1024, v, a, s);
+    }
+    return launch_row(nx, ROW_STD, a, s);
+}
+
 int tune_row_staged_shape(int thr) {
     for (int v = 0; v < N_ROW; ++v)
         if (ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma && ROW_SHAPES[v].a == thr) return v;

@@ -174,7 +174,7 @@ extern "C" int multislice_scan_run_noalloc(const prism_grid *grid, const float *
             ra.n_rows = nb * ny;
             ra.kx_half = M.kx_half;
             ra.tw = M.tw;
-            if ((rc = check(launch_row(nx, ROW_STD, ra, st), "row pass"))) return rc;
+            if ((rc = check(launch_row_std(nx, ra, st), "row pass"))) return rc;
             const int pi = M.slice_prop[p];
             ColArgs ca = ci;
             ca.prop_x = prop_x + (size_t)pi * nx;
