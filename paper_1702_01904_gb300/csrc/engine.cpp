@@ -744,13 +744,14 @@ static int col_default_shape(const prism_plan *P) {
     return v >= 0 && tune_shape_valid(PRISM_TUNE_COL, 1024, v) ? v : -1;
 }
 
-// the row pass's launch shape when none is tuned or pinned: at N = 1024, 256 threads with the next
-// row staged by cp.async (0.314 ms per launch on the 1024^2 carbon workload, against 0.332 for 128
-// threads unstaged); in a batch graph, whose branches share the SMs, the default launcher's smaller
-// CTAs (the staged shape holds 150 KB of shared memory per CTA)
+// the row pass's launch shape when none is tuned or pinned: at N = 1024, 384 threads (12 warps per
+// SM) with the next row's two kept quarters staged by bulk TMA copies (0.292 ms per launch on the
+// 1024^2 carbon workload, against 0.315 for 256 threads staged by cp.async and 0.333 for 128 threads
+// unstaged); in a batch graph, whose branches share the SMs, the default launcher's smaller CTAs
+// (this shape holds 163 KB of shared memory per CTA)
 static int row_default_shape(const prism_plan *P) {
     if (P->g.nx != 1024 || P->shared_sms) return -1;
-    const int v = tune_row_staged_shape(256);
+    const int v = tune_row_find(384, false, true);
     return v >= 0 && tune_shape_valid(PRISM_TUNE_ROW, 1024, v) ? v : -1;
 }
 

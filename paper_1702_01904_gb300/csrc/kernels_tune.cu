@@ -19,7 +19,8 @@ using tune::COL_SHAPES;
 using tune::N_COL;
 using tune::N_ROW;
 using tune::ROW_SHAPES;
-const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged", "128 thr, TMA"};
+const char *ROW_NAMES[N_ROW] = {"128 thr", "256 thr", "128 thr, staged", "256 thr, staged", "128 thr, TMA",
+                                "256 thr, TMA", "384 thr, staged", "384 thr, TMA"};
 const char *COL_NAMES[N_COL] = {"W4, staged", "W8, staged", "W16, staged", "W4, TMA, 3/SM", "W8", "W8, TMA", "W8, 2/SM", "W4, staged, 3/SM"};
 
 template <int N, int I>
@@ -83,18 +84,18 @@ bool tune_shape_needs_map(int kind, int v) { return kind == 1 && v >= 0 && v < N
 
 bool tune_shape_fills_sm(int kind, int v) { return kind == 1 && v >= 0 && v < N_COL && COL_SHAPES[v].mb >= 3; }
 
+int tune_row_find(int thr, bool stg, bool tma) {
+    for (int v = 0; v < N_ROW; ++v)
+        if (ROW_SHAPES[v].a == thr && ROW_SHAPES[v].stg == stg && ROW_SHAPES[v].tma == tma) return v;
+    return -1;
+}
+
 cudaError_t launch_row_std(int nx, const RowArgs &a, cudaStream_t s) {
     if (nx == 1024) {
-        const int v = tune_row_staged_shape(256);
+        const int v = tune_row_find(384, false, true);
         if (v >= 0 && tune_row_valid(1024, v)) return tune_row_launch(1024, v, a, s);
     }
     return launch_row(nx, ROW_STD, a, s);
-}
-
-int tune_row_staged_shape(int thr) {
-    for (int v = 0; v < N_ROW; ++v)
-        if (ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma && ROW_SHAPES[v].a == thr) return v;
-    return -1;
 }
 
 int tune_col_tma_shape(int w) {

@@ -33,12 +33,16 @@ cudaError_t row_n(int v, const RowArgs &a, cudaStream_t s) {
         case 2: return row_shape<N, 2>(a, s);
         case 3: return row_shape<N, 3>(a, s);
         case 4: return row_shape<N, 4>(a, s);
+        case 5: return row_shape<N, 5>(a, s);
+        case 6: return row_shape<N, 6>(a, s);
+        case 7: return row_shape<N, 7>(a, s);
     }
     return cudaErrorInvalidValue;
 }
 template <int N>
 bool row_valid_n(int v) {
-    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>(), row_ok<N, 4>()};
+    constexpr bool ok[N_ROW] = {row_ok<N, 0>(), row_ok<N, 1>(), row_ok<N, 2>(), row_ok<N, 3>(),
+                                row_ok<N, 4>(), row_ok<N, 5>(), row_ok<N, 6>(), row_ok<N, 7>()};
     return v >= 0 && v < N_ROW && ok[v];
 }
 }  // namespace

@@ -185,11 +185,12 @@ int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
 bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
 int tune_col_tma_shape(int w);                // the TMA-staged column shape of w columns per CTA, or -1
-int tune_row_staged_shape(int thr);           // the cp.async-staged row shape of thr threads per CTA, or -1
+int tune_row_find(int thr, bool stg, bool tma);  // the row shape of thr threads per CTA and that staging, or -1
 bool tune_shape_fills_sm(int kind, int v);    // 3 or more CTAs per SM, each with a third of its resources
 cudaError_t launch_row_shape(int nx, int v, const RowArgs &a, cudaStream_t s);
-// the standard row pass of a multislice scan: at nx = 1024 the 256-thread cp.async-staged shape
-// (the fastest there), elsewhere the default launcher; every shape computes the same rows
+// the standard row pass of a multislice scan: at nx = 1024 the 384-thread shape with the next row's
+// kept quarters staged by bulk TMA copies (the fastest there), elsewhere the default launcher; every
+// shape computes the same rows
 cudaError_t launch_row_std(int nx, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col_shape(int ny, int v, const ColArgs &a, cudaStream_t s);
 // smallest scan-window / FFT sizes the kernels are instantiated for

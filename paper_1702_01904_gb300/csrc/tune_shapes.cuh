@@ -13,7 +13,7 @@ struct Shape {
                 // pass, bulk copies of its kept quarters) staged by TMA
 };
 constexpr Shape ROW_SHAPES[] = {{128, false, 0, false}, {256, false, 0, false}, {128, true, 0, false}, {256, true, 0, false},
-                                {128, false, 0, true}};
+                                {128, false, 0, true},  {256, false, 0, true},  {384, true, 0, false}, {384, false, 0, true}};
 constexpr Shape COL_SHAPES[] = {{4, true, 0, false},  {8, true, 0, false},  {16, true, 0, false}, {4, false, 3, true},
                                 {8, false, 0, false}, {8, false, 0, true},  {8, false, 2, false}, {4, true, 3, false}};
 constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
