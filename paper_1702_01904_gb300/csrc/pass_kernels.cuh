@@ -353,6 +353,7 @@ struct ColCfg {
     static constexpr bool PERSIST = true;  // grid = resident CTAs, each looping over tiles
     static constexpr int MINB = MB > 0 ? MB : (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
     static constexpr int EX = ColExSize<NY, W>::value;
+    static_assert(EX >= NY * W, "the exchange buffer holds a whole tile (TMA stores)");
     static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
@@ -457,6 +458,12 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
         int b, kx0;
         locate(tile, b, kx0);
         const int kx = kx0 + c;
+        // TMA-staged shapes store their tile from the exchange buffer: before the exchange is written
+        // again (after the barrier inside the forward transform), the previous tile's stores must
+        // have read it
+        if constexpr (C::TMA) {
+            if (threadIdx.x == 0) tc::bulk_wait_read_all();
+        }
 
         float2 *col = a.wave + (size_t)b * NY * a.nx + kx;
         float2 v[E];
@@ -476,9 +483,11 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                     tphase ^= 1;
                     const bool ok = tc::mbar_wait_bounded(&tbar, ph, COL_TMA_WAIT_CYCLES);
                     if (__syncthreads_or(!ok)) {
-                        // report, give the boxes in flight one more bounded wait, leave (every thread)
+                        // report, give the boxes in flight one more bounded wait, let the stores
+                        // issued so far finish, leave (every thread)
                         if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
                         tc::mbar_wait_bounded(&tbar, ph, COL_TMA_WAIT_CYCLES);
+                        if (threadIdx.x == 0) tc::bulk_wait_all();
                         return;
                     }
                 } else {
@@ -526,10 +535,26 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = cscale(v[r], a.probe_scale);
         }
-        if (valid) {
+        if constexpr (C::TMA) {
+            // the tile through shared memory, [NY][W] in the exchange buffer (free once every thread
+            // has left the inverse transform), then NY / BOXR box stores by one thread
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < E; ++r) exb[Inv::out_elem(r, t) * W + c] = v[r];
+            tc::fence_proxy_async();  // the generic writes before the async-proxy reads
+            __syncthreads();
+            if (threadIdx.x == 0 && valid) {
+                const CUtensorMap *map = W == 8 ? &a.wave_map : &a.wave_map4;
+                for (int y0 = 0; y0 < NY; y0 += C::BOXR) tc::tma_store_3d(map, 2 * kx0, y0, b, exb + y0 * W);
+                tc::bulk_commit();
+            }
+        } else if (valid) {
 #pragma unroll
             for (int r = 0; r < E; ++r) col[(size_t)Inv::out_elem(r, t) * a.nx] = v[r];
         }
+    }
+    if constexpr (C::TMA) {
+        if (threadIdx.x == 0) tc::bulk_wait_all();  // the last stores complete before the CTA leaves
     }
 }
 

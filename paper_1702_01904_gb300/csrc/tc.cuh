@@ -136,6 +136,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int c0, 
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
         : "memory");
 }
+// --- TMA store of one box of a 3-D tensor map from shared memory (128-byte aligned, the box's
+// layout), tracked by the issuing thread's bulk groups: commit, then wait until the source has been
+// read (the buffer may be reused) or until the writes are complete
+__device__ __forceinline__ void tma_store_3d(const void *map, int c0, int c1, int c2, const void *src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(map), "r"(c0),
+                 "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 // --- bulk copy (TMA, no tensor map): `bytes` (a multiple of 16) from global to shared memory, both
 // 16-byte aligned, completing on `mbar`
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
