@@ -202,7 +202,9 @@ int prism_scan_run_accumulate(prism_plan *plan, const prism_probe *probe, const 
  * sum |Psi0|^2, annular bins.  Same grid rules as a plan (f, downsample and alpha_max are
  * ignored).  V_dev as above, out_dev float32 [py][px][nbins].  Uses its own stream-ordered
  * scratch on `cuda_stream`, sized to at most max(1, scratch_bytes / (8 nx ny)) probes in flight
- * (scratch_bytes = 0: 1 GiB).  Asynchronous; synchronise the stream before reading out_dev. */
+ * (scratch_bytes = 0: 1 GiB).  Asynchronous; synchronise the stream before reading out_dev.  At
+ * 1024^2 the column passes stage their tiles through TMA with bounded waits; a wait that runs out
+ * (which would leave a wave incomplete) makes that batch's bins NaN. */
 int multislice_scan_run(const prism_grid *grid, const float *V_dev, const prism_probe *probe,
                         const prism_scan *scan, const prism_detector *det, float *out_dev,
                         void *cuda_stream, size_t scratch_bytes);

@@ -1177,6 +1177,22 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
     if ((rc = A.upload(&d_off, off))) return done(rc);
     if ((rc = A.upload(&d_idx, idx))) return done(rc);
     if ((rc = A.alloc((void **)&pos, (size_t)Pn * 2 * sizeof(double)))) return done(rc);
+    // the column passes between slices as in a plan's build: at 1024^2 the TMA-staged shape (tiles
+    // loaded and stored by TMA through tensor maps of this call's wave buffer); their bounded waits
+    // report to an error word that turns the affected bins into NaN
+    int *err = nullptr;
+    if ((rc = A.alloc((void **)&err, 16))) return done(rc);
+    {
+        const cudaError_t e = cudaMemsetAsync(err, 0, 16, st);
+        if (e != cudaSuccess) {
+            fail(PRISM_ERR_CUDA, std::string("error word: ") + cudaGetErrorString(e));
+            return done(PRISM_ERR_CUDA);
+        }
+    }
+    CUtensorMap map8, map4;
+    const int col_tma = ny == 1024 ? tune_col_tma_shape(4) : -1;
+    const bool maps_ok = col_tma >= 0 && tune_shape_valid(PRISM_TUNE_COL, ny, col_tma) && encode_wave_map(map8, wave, nx, ny, Pb, 8) &&
+                         encode_wave_map(map4, wave, nx, ny, Pb, 4);
     {
         // the probe phase uses r0 - h tan(theta) (zero without tilt)
         std::vector<double> xy((size_t)Pn * 2);
@@ -1235,7 +1251,15 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             // columns the row passes skip) and writes every intensity
             ca.kx_half = p + 1 == g.n_slices ? 0 : kx_half;
             ca.band4 = T.band4;
-            if ((rc = check(launch_col(ny, p + 1 == g.n_slices ? COL_DETECT : COL_STD, ca, st), "column pass"))) return done(rc);
+            if (p + 1 < g.n_slices && maps_ok) {
+                ca.wave_map = map8;
+                ca.wave_map4 = map4;
+                ca.wave_map_ok = 1;
+                ca.err = err;
+                if ((rc = check(launch_col_shape(ny, col_tma, ca, st), "column pass"))) return done(rc);
+            } else if ((rc = check(launch_col(ny, p + 1 == g.n_slices ? COL_DETECT : COL_STD, ca, st), "column pass"))) {
+                return done(rc);
+            }
         }
         BinArgs ba;
         ba.inten = inten;
@@ -1247,6 +1271,7 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
         ba.npix = (int)px;
         ba.nbins = det->nbins;
         ba.batch = nb;
+        ba.err = err;
         if ((rc = check(launch_bins(ba, st), "bins"))) return done(rc);
     }
     // pageable uploads were staged before their calls returned; the frees below are stream-ordered

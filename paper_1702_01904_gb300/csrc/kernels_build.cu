@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(256) k_bins(const __grid_constant__ BinArgs a)
         for (int i = a.bin_off[k] + lane; i < e; i += 32) s += (double)__ldg(img + __ldg(a.bin_idx + i));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) a.out[(size_t)b * a.nbins + k] = (float)(s * a.scale);
+        // a pass whose bounded wait ran out left this wave incomplete: the result says so (NaN)
+        if (lane == 0) a.out[(size_t)b * a.nbins + k] = (a.err && *a.err) ? __int_as_float(0x7fc00000) : (float)(s * a.scale);
     }
 }
 

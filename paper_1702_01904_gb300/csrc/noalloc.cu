@@ -187,6 +187,7 @@ extern "C" int multislice_scan_run_noalloc(const prism_grid *grid, const float *
             if ((rc = check(launch_col(ny, p + 1 == H ? COL_DETECT : COL_STD, ca, st), "column pass"))) return rc;
         }
         BinArgs ba;
+        std::memset(&ba, 0, sizeof(ba));
         ba.inten = inten;
         ba.bin_off = d_off;
         ba.bin_idx = d_idx;

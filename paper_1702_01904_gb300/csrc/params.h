@@ -134,6 +134,7 @@ struct BinArgs {
     float *out;                // [batch][nbins]
     double scale;
     int npix, nbins, batch;
+    const int *err;            // optional device error word of the passes: non-zero -> the bins are NaN
 };
 
 // launchers (kernels_build.cu, kernels_scan.cu); return cudaSuccess or the launch error
