@@ -305,18 +305,22 @@ void prism_server_destroy(prism_server *server);
  *
  * The build is two streaming passes per slice (Calculation Time section: its cost grows with
  * beams x slices x N^2); their fastest launch shape (threads or interleaved columns per CTA,
- * staging of the next row or tile through shared memory by cp.async or by TMA, or none) depends on
- * N and the beam batch.  At N = 1024 the untuned column pass already uses the TMA-staged shape.  prism_plan_autotune times every
+ * staging of the next row or tile through shared memory by cp.async or by TMA, or none) and FFT radix
+ * (the split of the 32- and 64-point register DFTs, prism_tune_shape_fft_variant) depend on N and
+ * the beam batch.  At N = 1024 the untuned column pass already uses the TMA-staged shape.  prism_plan_autotune times every
  * compiled shape of the row pass (PRISM_TUNE_ROW) and the column pass (PRISM_TUNE_COL) on the
  * plan's own wave scratch (5 launches each after 2 warm-ups, CUDA events on the plan's stream)
  * and keeps the fastest for the plan's later builds.  Shapes exist for N = 256 ... 2048; smaller
- * grids keep their single shape.  Every shape computes bitwise the same result.  Results are
+ * grids keep their single shape.  Shapes of one radix variant compute bitwise the same result; the
+ * radix variants compute the same transforms rounded differently (they agree to FP32 rounding,
+ * well inside the FP32 path's tolerance against the FP64 oracle), so a plan that picks another
+ * variant than the default's reproduces its S-matrix to rounding, not bit for bit.  Results are
  * cached for the process per (pass, N, batch).  Synchronous; overwrites the wave scratch only (the
  * S-matrix is untouched).  The paper has no counterpart. */
 #define PRISM_TUNE_ROW 0
 #define PRISM_TUNE_COL 1
 #define PRISM_TUNE_SCAN 2  /* contraction tile shape of the FP32 GEMM scan (prism_plan_autotune_scan) */
-#define PRISM_TUNE_MAX_SHAPES 8
+#define PRISM_TUNE_MAX_SHAPES 16
 typedef struct prism_tune_entry {
     int n_shapes;                     /* shapes listed for the pass                              */
     int chosen;                       /* index of the shape in use (-1: the single default shape)  */
@@ -336,12 +340,18 @@ int prism_plan_autotune_scan(prism_plan *plan, const prism_probe *probe, const p
                              const prism_detector *det, float *out_dev);
 int prism_plan_tune_result(const prism_plan *plan, int kind, prism_tune_entry *out);
 const char *prism_tune_shape_name(int kind, int shape);
+/* FFT radix variant of a row or column shape: bit 0 for the forward, bit 1 for the inverse
+ * transform of the pass, each 0 for the default split of its 32- and 64-point register DFTs
+ * (32 = 8 x 4 and 64 = 8 x 8, second stage radix 4 with tangent-form twiddles where it applies) or 1
+ * for a radix-4 first stage (32 = 4 x 8, 64 = 4 x 16); -1 for another kind or an unknown shape. */
+int prism_tune_shape_fft_variant(int kind, int shape);
 /* Pin the launch shape of one pass (or the scan's contraction shape, PRISM_TUNE_SCAN) for the
  * plan's later builds (scans) without timing: `shape` indexes the kind's list
  * (prism_tune_shape_name), -1 restores the default.  PRISM_ERR_INVALID for a NULL plan or a kind
  * outside {PRISM_TUNE_ROW, PRISM_TUNE_COL, PRISM_TUNE_SCAN}; PRISM_ERR_UNSUPPORTED for a shape not
  * compiled for the plan's N (window), or one that stages through TMA when the plan holds no tensor
- * map of its wave scratch.  Every shape computes bitwise the same result. */
+ * map of its wave scratch.  Shapes of the default's FFT radix variant compute bitwise the same
+ * result; the other variant agrees to rounding. */
 int prism_plan_set_tune_shape(prism_plan *plan, int kind, int shape);
 
 /* ---- batches of uneven cells: one captured CUDA graph ------------------------------

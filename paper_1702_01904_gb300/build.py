@@ -2,8 +2,8 @@
 
 Usage: ``python -m paper_1702_01904_gb300.build [--force] [--verbose]``.
 Objects go to ``paper_1702_01904_gb300/_build`` and the library to
-``paper_1702_01904_gb300/libprism.so``; both are git-ignored.  The three translation units
-compile in parallel; a unit is rebuilt only when it or a header is newer than its object.
+``paper_1702_01904_gb300/libprism.so``; both are git-ignored.  The translation units compile
+in parallel; a unit is rebuilt only when it or a header is newer than its object.
 """
 from __future__ import annotations
 
@@ -21,10 +21,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh", "tune_shapes.cuh", "scan_gemm.cuh")] + \
+HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh",
+                                           "tune_shapes.cuh", "tune_pass.cuh", "scan_gemm.cuh")] + \
     [os.path.join(INCLUDE, "prism.h")]
-CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_row.cu", "kernels_scan.cu", "kernels_tune_scan.cu",
-              "kernels_tc.cu", "noalloc.cu"]
+CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_256.cu", "kernels_tune_512.cu", "kernels_tune_1024.cu",
+              "kernels_tune_2048.cu", "kernels_scan.cu", "kernels_tune_scan.cu", "kernels_tc.cu", "noalloc.cu"]
 HOST_UNITS = ["engine.cpp", "server.cpp"]
 
 

@@ -391,6 +391,7 @@ struct prism_plan {
     int *win_cnt = nullptr;    // FP32 GEMM scan: completion counters of split groups
     size_t cnt_cap = 0;
     CUtensorMap wave_map, wave_map4;  // the wave stack for the TMA-staged column pass (8 / 4 columns per box)
+    CUtensorMap out_map, out_map4;    // its stores (ColArgs::out_map)
     bool shared_sms = false;   // a batch runs this plan's kernels beside other cells' (see col_default_shape)
     bool wave_map_ok = false;
     int *dev_err = nullptr;    // device error word
@@ -475,11 +476,8 @@ static int tc_mode(int prec) { return prec == PRISM_PRECISION_BF16 ? 1 : prec ==
 // 16-bit rows stored per pixel
 static int tc_parts(int prec) { return prec == PRISM_PRECISION_FP16X2 ? 2 : 1; }
 
-// Tensor map of a wave stack [batch][ny][nx] complex64 for the TMA-staged column pass: FP32 view
-// [batch][ny][2 nx], boxes of 2 w floats (w = 4 or 8 columns) x min(ny, 256) rows x 1.  The encoder comes from
-// the driver through the runtime's entry-point query; false (shape not used) if it is unavailable
-// or the stack breaks a rule of the map (16-byte aligned base, strides multiples of 16 bytes).
-static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch, int w) {
+// The driver's tensor-map encoder through the runtime's entry-point query (null if unavailable)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -488,6 +486,15 @@ static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny
             fn = nullptr;
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
+    return encode;
+}
+
+// Tensor map of a wave stack [batch][ny][nx] complex64 for the TMA-staged column pass: FP32 view
+// [batch][ny][2 nx], boxes of 2 w floats (w = 4 or 8 columns) x min(ny, 256) rows x 1.  The encoder comes from
+// the driver through the runtime's entry-point query; false (shape not used) if it is unavailable
+// or the stack breaks a rule of the map (16-byte aligned base, strides multiples of 16 bytes).
+static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch, int w) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     std::memset(&map, 0, sizeof(map));
     if (!encode || !wave || ((uintptr_t)wave & 15) || nx < 8 || nx % 8 || ny < 1 || batch < 1) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)batch};
@@ -497,6 +504,34 @@ static bool encode_wave_map(CUtensorMap &map, const float2 *wave, int nx, int ny
     return encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(wave), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor map for the TMA stores of the column pass: the same stack as FP32 [batch][lanes][regs][2 nx]
+// with row y = lane + lanes * reg (the column transform's result layout, col_fft_geometry), boxes of
+// 2 w floats x (regs + 1) x 32 / w x 1: one warp's lanes of a finished tile in the exchange layout,
+// whose pad entry (reg = regs) lies outside the map and is not stored.
+static bool encode_out_map(CUtensorMap &map, const float2 *wave, int nx, int ny, int batch, int w) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    std::memset(&map, 0, sizeof(map));
+    int lanes = 0, regs = 0;
+    if (!encode || !wave || ((uintptr_t)wave & 15) || nx < 8 || nx % 8 || batch < 1 || (w != 4 && w != 8) ||
+        !col_fft_geometry(ny, &lanes, &regs) || lanes * regs != ny || lanes % (32 / w) || regs + 1 > 256)
+        return false;
+    const cuuint64_t row = (cuuint64_t)2 * nx * sizeof(float);
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * nx, (cuuint64_t)regs, (cuuint64_t)lanes, (cuuint64_t)batch};
+    const cuuint64_t strides[3] = {row * lanes, row, row * ny};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * w), (cuuint32_t)(regs + 1), (cuuint32_t)(32 / w), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2 *>(wave), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the load and store maps of a wave stack for both column counts; false if any cannot be encoded
+static bool encode_wave_maps(CUtensorMap &m8, CUtensorMap &m4, CUtensorMap &o8, CUtensorMap &o4, const float2 *wave, int nx,
+                             int ny, int batch) {
+    return encode_wave_map(m8, wave, nx, ny, batch, 8) && encode_wave_map(m4, wave, nx, ny, batch, 4) &&
+           encode_out_map(o8, wave, nx, ny, batch, 8) && encode_out_map(o4, wave, nx, ny, batch, 4);
 }
 
 extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes, void *cuda_stream, prism_plan **out) {
@@ -635,7 +670,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     if ((rc = A.alloc((void **)&P->t0f, px * 8))) return bail(rc);
     if ((rc = A.alloc((void **)&P->zero_mn, 2 * sizeof(int)))) return bail(rc);
     CUDA_TRY(cudaMemsetAsync(P->zero_mn, 0, 2 * sizeof(int), P->stream));
-    P->wave_map_ok = encode_wave_map(P->wave_map, P->wave, g.nx, g.ny, batch, 8) && encode_wave_map(P->wave_map4, P->wave, g.nx, g.ny, batch, 4);
+    P->wave_map_ok = encode_wave_maps(P->wave_map, P->wave_map4, P->out_map, P->out_map4, P->wave, g.nx, g.ny, batch);
     if ((rc = A.upload(&P->prop_x, P->T.prop_x))) return bail(rc);
     if ((rc = A.upload(&P->prop_y, P->T.prop_y))) return bail(rc);
     if ((rc = A.upload(&P->aa_kmax, P->T.aa_kmax))) return bail(rc);
@@ -759,6 +794,8 @@ static int row_default_shape(const prism_plan *P) {
 static void col_wave_map(const prism_plan *P, ColArgs &ca) {
     ca.wave_map = P->wave_map;
     ca.wave_map4 = P->wave_map4;
+    ca.out_map = P->out_map;
+    ca.out_map4 = P->out_map4;
     ca.wave_map_ok = P->wave_map_ok ? 1 : 0;
     ca.err = P->dev_err;
 }
@@ -1189,10 +1226,10 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             return done(PRISM_ERR_CUDA);
         }
     }
-    CUtensorMap map8, map4;
+    CUtensorMap map8, map4, out8, out4;
     const int col_tma = ny == 1024 ? tune_col_tma_shape(4) : -1;
-    const bool maps_ok = col_tma >= 0 && tune_shape_valid(PRISM_TUNE_COL, ny, col_tma) && encode_wave_map(map8, wave, nx, ny, Pb, 8) &&
-                         encode_wave_map(map4, wave, nx, ny, Pb, 4);
+    const bool maps_ok =
+        col_tma >= 0 && tune_shape_valid(PRISM_TUNE_COL, ny, col_tma) && encode_wave_maps(map8, map4, out8, out4, wave, nx, ny, Pb);
     {
         // the probe phase uses r0 - h tan(theta) (zero without tilt)
         std::vector<double> xy((size_t)Pn * 2);
@@ -1254,6 +1291,8 @@ extern "C" int multislice_scan_run(const prism_grid *grid, const float *V_dev, c
             if (p + 1 < g.n_slices && maps_ok) {
                 ca.wave_map = map8;
                 ca.wave_map4 = map4;
+                ca.out_map = out8;
+                ca.out_map4 = out4;
                 ca.wave_map_ok = 1;
                 ca.err = err;
                 if ((rc = check(launch_col_shape(ny, col_tma, ca, st), "column pass"))) return done(rc);
@@ -1627,6 +1666,10 @@ extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_
 
 extern "C" const char *prism_tune_shape_name(int kind, int shape) {
     return kind == PRISM_TUNE_SCAN ? scan_gemm_shape_name(shape) : tune_shape_name(kind, shape);
+}
+
+extern "C" int prism_tune_shape_fft_variant(int kind, int shape) {
+    return kind == PRISM_TUNE_ROW || kind == PRISM_TUNE_COL ? tune_shape_fft_variant(kind, shape) : -1;
 }
 
 // The scan's contraction tile shape (Calculation Time section: the scan term P B N^2 / (4 f^4) is

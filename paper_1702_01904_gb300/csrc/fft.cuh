@@ -201,17 +201,18 @@ struct Dft4Tw {
 };
 
 // In-place DFT of R elements x[0], x[S], ..., x[(R-1)S]; natural order in and out.  Z: inputs known
-// to be exactly zero (bit i: element i S).
-template <int R, int S, bool INV, unsigned long long Z = 0>
+// to be exactly zero (bit i: element i S).  V: split variant of the 32- and 64-point codelets
+// (DftSplit); the 1- to 8-point codelets have one form.
+template <int R, int S, bool INV, unsigned long long Z = 0, int V = 0>
 struct Dft;
 
-template <int S, bool INV, unsigned long long Z>
-struct Dft<1, S, INV, Z> {
+template <int S, bool INV, unsigned long long Z, int V>
+struct Dft<1, S, INV, Z, V> {
     __device__ __forceinline__ static void run(float2 *, const Tw64 &) {}
 };
 
-template <int S, bool INV, unsigned long long Z>
-struct Dft<2, S, INV, Z> {
+template <int S, bool INV, unsigned long long Z, int V>
+struct Dft<2, S, INV, Z, V> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
         float2 a = x[0], b = x[S];
         x[0] = zadd<zbit(Z, 0), zbit(Z, 1)>(a, b);
@@ -219,8 +220,8 @@ struct Dft<2, S, INV, Z> {
     }
 };
 
-template <int S, bool INV, unsigned long long Z>
-struct Dft<4, S, INV, Z> {
+template <int S, bool INV, unsigned long long Z, int V>
+struct Dft<4, S, INV, Z, V> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &) {
         constexpr bool z0 = zbit(Z, 0), z1 = zbit(Z, 1), z2 = zbit(Z, 2), z3 = zbit(Z, 3);
         float2 t0 = zadd<z0, z2>(x[0], x[2 * S]);
@@ -234,8 +235,8 @@ struct Dft<4, S, INV, Z> {
     }
 };
 
-template <int S, bool INV, unsigned long long Z>
-struct Dft<8, S, INV, Z> {
+template <int S, bool INV, unsigned long long Z, int V>
+struct Dft<8, S, INV, Z, V> {
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
         // decimation in frequency: b_k = a_k + a_{k+4} (even outputs), c_k = (a_k - a_{k+4}) W8^k (odd)
         float2 b[4], c[4];
@@ -255,10 +256,16 @@ struct Dft<8, S, INV, Z> {
     }
 };
 
-template <int R>
+// Split R = R1 x R2 of the larger register DFTs (stage 1: R2 DFTs of R1 points, stage 2: R1 DFTs of
+// R2 points).  Variant 0: R1 = 4 for 16, 8 for 32 and 64 (16 = 4 x 4, 32 = 8 x 4 with the radix-4
+// second stage taking its twiddles in tangent form, 64 = 8 x 8).  Variant 1: a radix-4 first stage
+// (32 = 4 x 8, 64 = 4 x 16), whose DFT-4s are cheap where the inputs are known zeros (the band-
+// limited inputs of the passes) but whose second stage multiplies its twiddles separately.  Both
+// compute the same DFT; they round differently.
+template <int R, int V = 0>
 struct DftSplit {
-    static constexpr int R1 = (R == 16) ? 4 : (R == 32) ? 8 : (R == 64) ? 8 : 0;
-    static constexpr int R2 = R / R1;
+    static constexpr int R1 = (R != 16 && R != 32 && R != 64) ? 0 : (R == 16 || V == 1) ? 4 : 8;
+    static constexpr int R2 = R1 ? R / R1 : 0;
 };
 
 template <int R1, int R2, int S, bool INV, int N2>
@@ -291,16 +298,16 @@ __host__ __device__ constexpr unsigned long long stage2_mask(unsigned long long 
     return m;
 }
 
-template <int R, int S, bool INV, unsigned long long Z>
+template <int R, int S, bool INV, unsigned long long Z, int V>
 struct Dft {
-    static constexpr int R1 = DftSplit<R>::R1;
-    static constexpr int R2 = DftSplit<R>::R2;
+    static constexpr int R1 = DftSplit<R, V>::R1;
+    static constexpr int R2 = DftSplit<R, V>::R2;
     static_assert(R1 > 0, "unsupported register DFT size");
     __device__ __forceinline__ static void run(float2 *x, const Tw64 &tw) {
         // stage 1: DFT over n1 of elements (R2 n1 + n2) for each n2
         static_for<R2>([&](auto nc) {
             constexpr int n2 = decltype(nc)::value;
-            Dft<R1, R2 * S, INV, sub_mask<R1, R2>(Z, n2)>::run(x + n2 * S, tw);
+            Dft<R1, R2 * S, INV, sub_mask<R1, R2>(Z, n2), V>::run(x + n2 * S, tw);
         });
         // stage 2: DFT over n2 of elements (R2 k1 + n2) times W_R^{n2 k1}, for each k1 -> X[k1 + R1 k2]
         // at (R2 k1 + k2); radix 4 with the twiddles in the butterflies, else twiddles then DFTs
@@ -314,7 +321,7 @@ struct Dft {
             static_assert(Z2 == 0, "known-zero stage-2 inputs need the radix-4 stage");
             DftTw<R1, R2, S, INV, R2>::template go<0>(x, tw);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV>::run(x + R2 * k1 * S, tw);
+            for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, INV, 0, V>::run(x + R2 * k1 * S, tw);
         }
         float2 tmp[R];
 #pragma unroll
@@ -339,12 +346,19 @@ struct FftShape {
     static_assert(N1 > 0, "unsupported FFT length");
 };
 
+// A no-op in place of BlockFft::run's hook
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // Two-level transform of length N = N1*N2 over T threads.  `stw` is the inter-stage twiddle
 // table laid out [k1][n2] = W_N^{n2 k1} (forward sign; the inverse conjugates it); kernels keep
 // it in shared memory (lanes read consecutive n2: conflict-free).  `Ex` is the exchange:
 // write(k1, n2, v), read(k1, n2), sync().
-template <int N1, int N2, bool INV>
+// V: split variant of the register DFTs (DftSplit)
+template <int N1, int N2, bool INV, int V = 0>
 struct BlockFft {
+    static constexpr int SPLIT1 = N1, SPLIT2 = N2;  // first-stage, second-stage DFT lengths
     static constexpr int N = N1 * N2;
     static constexpr int E = N1 > N2 ? N1 : N2;
     static constexpr int T = N / E;
@@ -354,12 +368,15 @@ struct BlockFft {
     // GTW: the twiddle table is in global memory (read through the read-only path); otherwise it
     // is in shared memory
     // ZIN: input registers known to be exactly zero in every thread (bit r: register r)
-    template <class Ex, bool GTW = false, unsigned long long ZIN = 0>
+    // LEAD: synchronise before the exchange is written (off where the caller has already ordered
+    // every earlier access of the buffer before this call's writes)
+    // hook(): called by every thread right after the barrier that follows the exchange writes
+    template <class Ex, bool GTW = false, unsigned long long ZIN = 0, bool LEAD = true, class Hook = NoHook>
     __device__ __forceinline__ static void run(float2 (&x)[E], int t, const float2 *__restrict__ stw,
-                                               const Tw64 &tw, Ex &ex) {
+                                               const Tw64 &tw, Ex &ex, Hook hook = Hook{}) {
         static_for<J>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            Dft<N1, J, INV, sub_mask<N1, J>(ZIN, j)>::run(x + j, tw);
+            Dft<N1, J, INV, sub_mask<N1, J>(ZIN, j), V>::run(x + j, tw);
         });
         if constexpr (!GTW) {
             // shared-memory table: all twiddle loads before any exchange store (the table and the
@@ -373,7 +390,7 @@ struct BlockFft {
                     x[k1 * J + j] = INV ? cmulc(x[k1 * J + j], w) : cmul(x[k1 * J + j], w);
                 }
             }
-            ex.sync();  // previous readers of the exchange are done
+            if constexpr (LEAD) ex.sync();  // previous readers of the exchange are done
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int n2 = t + T * j;
@@ -383,7 +400,7 @@ struct BlockFft {
         } else {
             // global table (read-only path, L1-resident): interleave load, multiply and store, which
             // keeps register pressure at the level of one element
-            ex.sync();
+            if constexpr (LEAD) ex.sync();
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int n2 = t + T * j;
@@ -399,6 +416,7 @@ struct BlockFft {
             }
         }
         ex.sync();
+        hook();
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             const int k1 = t + T * i;
@@ -406,7 +424,7 @@ struct BlockFft {
             for (int n2 = 0; n2 < N2; ++n2) x[n2 * I + i] = ex.read(k1, n2);
         }
 #pragma unroll
-        for (int i = 0; i < I; ++i) Dft<N2, I, INV>::run(x + i, tw);
+        for (int i = 0; i < I; ++i) Dft<N2, I, INV, 0, V>::run(x + i, tw);
     }
 
     // element index held in register r (input / output layouts)
@@ -443,10 +461,10 @@ __host__ __device__ constexpr unsigned long long band_zero_mask(bool input) {
     return m;
 }
 
-template <int N>
-using FwdFft = BlockFft<FftShape<N>::N1, FftShape<N>::N2, false>;
-template <int N>
-using InvFft = BlockFft<FftShape<N>::N2, FftShape<N>::N1, true>;
+template <int N, int V = 0>
+using FwdFft = BlockFft<FftShape<N>::N1, FftShape<N>::N2, false, V>;
+template <int N, int V = 0>
+using InvFft = BlockFft<FftShape<N>::N2, FftShape<N>::N1, true, V>;
 
 // Exchange for transforms held by T consecutive lanes of one warp (T <= 32); each transform
 // owns N1*(N2+1) float2 of shared memory (the +1 pad keeps stage-2 reads at two wavefronts).

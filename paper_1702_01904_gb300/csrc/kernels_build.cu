@@ -135,6 +135,29 @@ cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s) {
     }
 }
 
+template <int NY>
+static bool col_geom(int *lanes, int *regs) {
+    using Inv = InvFft<NY>;
+    static_assert(Inv::I == 1 && Inv::SPLIT1 == Inv::T && Inv::SPLIT2 == Inv::E, "result row = lane + lanes * register");
+    *lanes = Inv::T;
+    *regs = Inv::E;
+    return true;
+}
+
+bool col_fft_geometry(int ny, int *lanes, int *regs) {
+    switch (ny) {
+        case 16: return col_geom<16>(lanes, regs);
+        case 32: return col_geom<32>(lanes, regs);
+        case 64: return col_geom<64>(lanes, regs);
+        case 128: return col_geom<128>(lanes, regs);
+        case 256: return col_geom<256>(lanes, regs);
+        case 512: return col_geom<512>(lanes, regs);
+        case 1024: return col_geom<1024>(lanes, regs);
+        case 2048: return col_geom<2048>(lanes, regs);
+        default: return false;
+    }
+}
+
 bool row_supported(int n) { return n >= 16 && n <= 2048 && (n & (n - 1)) == 0; }
 bool col_supported(int n) { return row_supported(n); }
 

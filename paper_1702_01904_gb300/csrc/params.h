@@ -48,6 +48,12 @@ struct ColArgs {
     CUtensorMap wave_map;      // TMA staging (STD): `wave` as FP32 [batch][ny][2 nx], boxes of 16 floats
                                // (8 columns) x min(ny, 256) rows x 1; valid when wave_map_ok
     CUtensorMap wave_map4;     // the same with boxes of 8 floats (4 columns)
+    CUtensorMap out_map;       // TMA stores (STD): `wave` as FP32 [batch][lanes][regs][2 nx] with row
+                               // y = lane + lanes * reg (lanes, regs: the column transform's threads
+                               // and registers per column, col_fft_geometry), boxes of 16 floats x
+                               // (regs + 1) x 32/8 x 1 -- one warp's rows of a finished tile in the
+                               // padded exchange layout; the pad entry lies past `regs` and is not stored
+    CUtensorMap out_map4;      // the same for 4 columns: boxes of 8 floats x (regs + 1) x 32/4 x 1
     float2 *wave;              // [batch][ny][nx]
     float *inten;              // DETECT: [batch][ny][nx] |Psi|^2 (scaled later)
     const float2 *prop_x;      // [nx]  exp(-i pi lambda dz qx^2)
@@ -66,7 +72,7 @@ struct ColArgs {
     int band4;                 // 1: the aperture keeps |ky| < ny/4 on every column (aa_kmax < ny/4), so
                                // the column transforms may drop that band's complement at compile
                                // time (STD, DETECT)
-    int wave_map_ok;           // 1: wave_map and wave_map4 describe `wave` (the TMA-staged shapes may run)
+    int wave_map_ok;           // 1: the four maps describe `wave` (the TMA-staged shapes may run)
     int *err;                  // device error word: a TMA wait that ran out sets bit 1
     Tw64 tw;
 };
@@ -144,6 +150,9 @@ cudaError_t launch_plane(const float2 *T0, float2 *wave, const int *beam_mn, int
                          int kx_half, cudaStream_t s);
 cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s);
 cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s);
+// the column transform of length ny: threads (lanes) per column and registers per thread, whose
+// result row is lane + lanes * register (false for an unsupported ny)
+bool col_fft_geometry(int ny, int *lanes, int *regs);
 cudaError_t launch_scan(int nw, const ScanArgs &a, cudaStream_t s);
 // nw_x x nw_y windows (separate f_x, f_y): square ones as launch_scan, rectangular ones (16, 32, 64
 // per side) through the grouped kernel; scan_rect_supported says whether a launch can succeed
@@ -185,6 +194,7 @@ const char *tune_shape_name(int kind, int v);
 int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
 bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
+int tune_shape_fft_variant(int kind, int v);  // its FFT radix variant (DftSplit), -1 if unknown
 int tune_col_tma_shape(int w);                // the TMA-staged column shape of w columns per CTA, or -1
 int tune_row_find(int thr, bool stg, bool tma);  // the row shape of thr threads per CTA and that staging, or -1
 bool tune_shape_fills_sm(int kind, int v);    // 3 or more CTAs per SM, each with a third of its resources

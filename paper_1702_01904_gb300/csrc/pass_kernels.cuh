@@ -92,12 +92,14 @@ struct RowCfg {
 constexpr long long ROW_TMA_WAIT_CYCLES = 2000000000LL;
 
 // BL: the kept columns are exactly |kx| < NX/4 (kx_half == NX/4), known at compile time
-template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool BL = false, bool TM = false>
+// RV: split variants of the register DFTs (DftSplit) of the forward (bit 0) and the inverse (bit 1)
+// transform: the same transforms, rounded differently
+template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool BL = false, bool TM = false, int RV = 0>
 __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) {
     using C = RowCfg<NX, THR, STG, TM>;
     using FS = FftShape<NX>;
-    using Fwd = FwdFft<NX>;
-    using Inv = InvFft<NX>;
+    using Fwd = FwdFft<NX, RV & 1>;
+    using Inv = InvFft<NX, (RV >> 1) & 1>;
     constexpr int T = C::T, E = FS::E;
     static_assert(!TM || (BL && T == 32 && MODE != ROW_PLANE), "bulk staging: compile-time band, one slot per warp");
     // with the compile-time band the inverse transform's out-of-band inputs are exact zeros
@@ -301,20 +303,20 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
     }
 }
 
-template <int NX, int MODE, int THR, bool STG, bool BL, bool TM = false>
+template <int NX, int MODE, int THR, bool STG, bool BL, bool TM = false, int RV = 0>
 static cudaError_t row_go_bl(const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<NX, THR, STG, TM>;
     int grid = 0;
-    cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG, BL, TM>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
+    cudaError_t e = persistent_grid(k_row<NX, MODE, THR, STG, BL, TM, RV>, C::THREADS, C::SMEM, (a.n_rows + C::SLOTS - 1) / C::SLOTS,
                                     &grid, C::PERSIST);
     if (e != cudaSuccess) return e;
-    k_row<NX, MODE, THR, STG, BL, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
+    k_row<NX, MODE, THR, STG, BL, TM, RV><<<grid, C::THREADS, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
 // TM: bulk staging where it applies (the compile-time band, one slot per warp, rows read from the
 // wave); elsewhere the same shape without it, which computes the same rows
-template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool TM = false>
+template <int NX, int MODE, int THR = row_default_threads<NX>(), bool STG = false, bool TM = false, int RV = 0>
 static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
     using C = RowCfg<NX, THR, STG, TM>;
     if constexpr (C::SMEM > 227 * 1024 || THR % C::T != 0 || THR > 1024) {
@@ -323,11 +325,11 @@ static cudaError_t row_go(const RowArgs &a, cudaStream_t s) {
         // the compile-time band for the default aperture (aa_frac 1/2 on a square grid: |kx| < NX/4)
         if constexpr (NX >= 64) {
             if (a.kx_half * 4 == NX) {
-                if constexpr (TM && C::T == 32 && MODE != ROW_PLANE) return row_go_bl<NX, MODE, THR, STG, true, true>(a, s);
-                else return row_go_bl<NX, MODE, THR, STG, true>(a, s);
+                if constexpr (TM && C::T == 32 && MODE != ROW_PLANE) return row_go_bl<NX, MODE, THR, STG, true, true, RV>(a, s);
+                else return row_go_bl<NX, MODE, THR, STG, true, false, RV>(a, s);
             }
         }
-        return row_go_bl<NX, MODE, THR, STG, false>(a, s);
+        return row_go_bl<NX, MODE, THR, STG, false, false, RV>(a, s);
     }
 }
 
@@ -354,6 +356,7 @@ struct ColCfg {
     static constexpr int MINB = MB > 0 ? MB : (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
     static constexpr int EX = ColExSize<NY, W>::value;
     static_assert(EX >= NY * W, "the exchange buffer holds a whole tile (TMA stores)");
+    static_assert(!TM || (FS::T % (32 / W) == 0 && FS::T * W >= 32), "TMA stores: whole warps of lanes per column");
     static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
@@ -361,12 +364,14 @@ struct ColCfg {
 constexpr long long COL_TMA_WAIT_CYCLES = 2000000000LL;
 
 // BL: every column keeps at most |ky| < NY/4 (band4), known at compile time
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool BL = false, bool TM = false>
+// RV: split variants of the register DFTs (DftSplit) of the forward (bit 0) and the inverse (bit 1)
+// transform: the same transforms, rounded differently
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool BL = false, bool TM = false, int RV = 0>
 __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<NY, WC, STG, MB, TM>::MINB) k_col(const __grid_constant__ ColArgs a) {
     using C = ColCfg<NY, WC, STG, MB, TM>;
     using FS = FftShape<NY>;
-    using Fwd = FwdFft<NY>;
-    using Inv = InvFft<NY>;
+    using Fwd = FwdFft<NY, RV & 1>;
+    using Inv = InvFft<NY, (RV >> 1) & 1>;
     constexpr int W = C::W, E = FS::E, THREADS = C::THREADS;
     extern __shared__ __align__(128) float2 smem_c[];
     float2 *smem = smem_c;
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
     }
     float2 *stg = smem + (C::SMEM_TW ? 2 * NY : 0);
     float2 *exb = stg + (C::STAGE ? NY * W : 0);
-    const int c = threadIdx.x % W, t = threadIdx.x / W;
+    const int c = threadIdx.x % W, t = threadIdx.x / W, lane = threadIdx.x & 31;
     ColExchange<FS::N1, FS::N2, W> exF{exb, c};
     ColExchange<FS::N2, FS::N1, W> exI{exb, c};
     // column tiles of W columns: all of them, or (kx_half > 0) only the low ones [0, lo W) and the
@@ -458,11 +463,11 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
         int b, kx0;
         locate(tile, b, kx0);
         const int kx = kx0 + c;
-        // TMA-staged shapes store their tile from the exchange buffer: before the exchange is written
-        // again (after the barrier inside the forward transform), the previous tile's stores must
-        // have read it
+        // TMA-staged shapes store their tile from the exchange buffer, one box per warp: before the
+        // exchange is written again (right after the barrier that follows the tile's arrival), every
+        // warp's store of the previous tile must have read it
         if constexpr (C::TMA) {
-            if (threadIdx.x == 0) tc::bulk_wait_read_all();
+            if (lane == 0) tc::bulk_wait_read_all();
         }
 
         float2 *col = a.wave + (size_t)b * NY * a.nx + kx;
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                         // issued so far finish, leave (every thread)
                         if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
                         tc::mbar_wait_bounded(&tbar, ph, COL_TMA_WAIT_CYCLES);
-                        if (threadIdx.x == 0) tc::bulk_wait_all();
+                        if (lane == 0) tc::bulk_wait_all();
                         return;
                     }
                 } else {
@@ -496,13 +501,24 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                 }
 #pragma unroll
                 for (int r = 0; r < E; ++r) v[r] = stg[Fwd::in_elem(r, t) * W + c];
-                __syncthreads();  // the staging buffer is refilled next
-                if (it + 1 < iters) stage(tile + gridDim.x);
+                if constexpr (!C::TMA) {
+                    __syncthreads();  // the staging buffer is refilled next
+                    if (it + 1 < iters) stage(tile + gridDim.x);
+                }
             } else {
 #pragma unroll
                 for (int r = 0; r < E; ++r) v[r] = col[(size_t)Fwd::in_elem(r, t) * a.nx];
             }
-            Fwd::template run<decltype(exF), !C::SMEM_TW>(v, t, twf, a.tw, exF);
+            if constexpr (C::TMA) {
+                // the barrier after the tile's arrival ordered every earlier use of the exchange
+                // before its writes here (no leading barrier), and the barrier after them is the
+                // point where every thread has read the staging buffer: its refill starts there
+                Fwd::template run<decltype(exF), !C::SMEM_TW, 0ull, false>(v, t, twf, a.tw, exF, [&] {
+                    if (it + 1 < iters) stage(tile + gridDim.x);
+                });
+            } else {
+                Fwd::template run<decltype(exF), !C::SMEM_TW>(v, t, twf, a.tw, exF);
+            }
             // Fresnel propagator exp(-i pi lambda t |q|^2) (separable) inside the anti-aliasing
             // aperture, which on column kx is |ky| <= aa_kmax[kx]
             const float2 px = __ldg(a.prop_x + kx);
@@ -536,16 +552,21 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
             for (int r = 0; r < E; ++r) v[r] = cscale(v[r], a.probe_scale);
         }
         if constexpr (C::TMA) {
-            // the tile through shared memory, [NY][W] in the exchange buffer (free once every thread
-            // has left the inverse transform), then NY / BOXR box stores by one thread
-            __syncthreads();
+            // result register r of lane t is row t + T r: it goes back to the exchange slot (t, r) that
+            // this thread alone read in the inverse transform's second stage, so no barrier is needed
+            // before the writes; the slots of a warp's lanes (T / (32 / W) consecutive t) are one
+            // contiguous box of the store map, [t][E + 1][W], which lane 0 stores once the warp's
+            // writes are visible to the async proxy
+            static_assert(Inv::I == 1 && Inv::SPLIT1 == FS::T && Inv::SPLIT2 == E, "result row = t + T r");
+            constexpr int TPW = 32 / W;  // lanes t per warp
 #pragma unroll
-            for (int r = 0; r < E; ++r) exb[Inv::out_elem(r, t) * W + c] = v[r];
+            for (int r = 0; r < E; ++r) exb[(t * (E + 1) + r) * W + c] = v[r];
             tc::fence_proxy_async();  // the generic writes before the async-proxy reads
-            __syncthreads();
-            if (threadIdx.x == 0 && valid) {
-                const CUtensorMap *map = W == 8 ? &a.wave_map : &a.wave_map4;
-                for (int y0 = 0; y0 < NY; y0 += C::BOXR) tc::tma_store_3d(map, 2 * kx0, y0, b, exb + y0 * W);
+            __syncwarp();
+            if (lane == 0 && valid) {
+                const CUtensorMap *map = W == 8 ? &a.out_map : &a.out_map4;
+                const int t0 = (threadIdx.x >> 5) * TPW;
+                tc::tma_store_4d(map, 2 * kx0, 0, t0, b, exb + t0 * (E + 1) * W);
                 tc::bulk_commit();
             }
         } else if (valid) {
@@ -554,7 +575,7 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
         }
     }
     if constexpr (C::TMA) {
-        if (threadIdx.x == 0) tc::bulk_wait_all();  // the last stores complete before the CTA leaves
+        if (lane == 0) tc::bulk_wait_all();  // the last stores complete before the CTA leaves
     }
 }
 
@@ -569,7 +590,7 @@ static inline long long col_tiles(int nx, int w, int kx_half, int batch) {
     return (long long)(lo + (nx / w - hs)) * batch;
 }
 
-template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false>
+template <int NY, int MODE, int WC = col_default_w<NY>(), bool STG = true, int MB = 0, bool TM = false, int RV = 0>
 static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
     using C = ColCfg<NY, WC, STG, MB, TM>;
     if constexpr (C::SMEM > 227 * 1024 || C::THREADS > 1024 || (TM && (MODE != COL_STD || (WC != 4 && WC != 8) || NY % C::BOXR))) {
@@ -583,15 +604,15 @@ static cudaError_t col_go(const ColArgs &a, cudaStream_t s) {
         cudaError_t e;
         if constexpr (NY >= 64 && MODE != COL_PROBE) {
             if (a.band4) {
-                e = persistent_grid(k_col<NY, MODE, WC, STG, MB, true, TM>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
+                e = persistent_grid(k_col<NY, MODE, WC, STG, MB, true, TM, RV>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
                 if (e != cudaSuccess) return e;
-                k_col<NY, MODE, WC, STG, MB, true, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
+                k_col<NY, MODE, WC, STG, MB, true, TM, RV><<<grid, C::THREADS, C::SMEM, s>>>(a);
                 return cudaGetLastError();
             }
         }
-        e = persistent_grid(k_col<NY, MODE, WC, STG, MB, false, TM>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
+        e = persistent_grid(k_col<NY, MODE, WC, STG, MB, false, TM, RV>, C::THREADS, C::SMEM, work, &grid, C::PERSIST);
         if (e != cudaSuccess) return e;
-        k_col<NY, MODE, WC, STG, MB, false, TM><<<grid, C::THREADS, C::SMEM, s>>>(a);
+        k_col<NY, MODE, WC, STG, MB, false, TM, RV><<<grid, C::THREADS, C::SMEM, s>>>(a);
         return cudaGetLastError();
     }
 }

@@ -144,6 +144,12 @@ __device__ __forceinline__ void tma_store_3d(const void *map, int c0, int c1, in
                  "r"(c1), "r"(c2), "r"(smem_u32(src))
                  : "memory");
 }
+// the same for a 4-D tensor map
+__device__ __forceinline__ void tma_store_4d(const void *map, int c0, int c1, int c2, int c3, const void *src) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(map), "r"(c0),
+                 "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }

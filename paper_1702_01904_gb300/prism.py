@@ -35,7 +35,7 @@ PRISM_PRECISION_FP16X2 = 3
 PRISM_TUNE_ROW = 0
 PRISM_TUNE_COL = 1
 PRISM_TUNE_SCAN = 2
-PRISM_TUNE_MAX_SHAPES = 8
+PRISM_TUNE_MAX_SHAPES = 16
 PRISM_BATCH_AUTOTUNE = 1
 
 # every entry point declared in include/prism.h
@@ -52,6 +52,7 @@ EXPORTED = [
     "prism_selftest_tcgen05", "prism_selftest_bounded_wait",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
     "prism_plan_autotune", "prism_plan_autotune_scan", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
+    "prism_tune_shape_fft_variant",
     "prism_plan_load_smatrix",
 ]
 
@@ -108,7 +109,7 @@ _lib = None
 
 
 class PrismTuneEntry(ctypes.Structure):
-    _fields_ = [("n_shapes", c_int), ("chosen", c_int), ("default_shape", c_int), ("ms", c_double * 8)]
+    _fields_ = [("n_shapes", c_int), ("chosen", c_int), ("default_shape", c_int), ("ms", c_double * PRISM_TUNE_MAX_SHAPES)]
 
 
 class PrismCell(ctypes.Structure):
@@ -156,6 +157,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_autotune_scan": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
         "prism_plan_tune_result": (c_int, [P, c_int, POINTER(PrismTuneEntry)]),
         "prism_tune_shape_name": (c_char_p, [c_int, c_int]),
+        "prism_tune_shape_fft_variant": (c_int, [c_int, c_int]),
         "prism_plan_set_tune_shape": (c_int, [P, c_int, c_int]),
         "prism_plan_load_smatrix": (c_int, [P, P]),
         "prism_batch_run": (c_int, [P]),
@@ -470,6 +472,10 @@ def prism_plan_tune_result(plan, kind):
 
 def prism_tune_shape_name(kind, shape):
     return load().prism_tune_shape_name(kind, shape).decode()
+
+
+def prism_tune_shape_fft_variant(kind, shape):
+    return load().prism_tune_shape_fft_variant(kind, shape)
 
 
 def prism_plan_set_tune_shape(plan, kind, shape):

@@ -144,6 +144,25 @@ def test_tune_shape_arguments_rejected_without_a_device():
     assert "W8, TMA" in names and "W8, staged" in names
 
 
+def test_tune_shapes_list_both_fft_radix_variants():
+    """Each pass lists launch shapes of both FFT radix variants (the split of the 32- and 64-point
+    register DFTs); the defaults are variant 0, other kinds and unknown shapes report -1."""
+    for kind in (P.PRISM_TUNE_ROW, P.PRISM_TUNE_COL):
+        rv = {}
+        for v in range(P.PRISM_TUNE_MAX_SHAPES):
+            name = P.prism_tune_shape_name(kind, v)
+            if name == "?":
+                assert P.prism_tune_shape_fft_variant(kind, v) == -1
+                continue
+            rv[name] = P.prism_tune_shape_fft_variant(kind, v)
+        assert set(rv.values()) == {0, 1, 2, 3}  # forward (bit 0) and inverse (bit 1) split
+        assert all(("radix-4 first" in n) == (r != 0) for n, r in rv.items())
+        assert all(n.endswith({1: "forward", 2: "inverse", 3: "both"}[r]) for n, r in rv.items() if r)
+    assert rv["W4, TMA, 3/SM"] == 0 and rv["W8, staged"] == 0
+    assert P.prism_tune_shape_fft_variant(P.PRISM_TUNE_SCAN, 0) == -1
+    assert P.prism_tune_shape_fft_variant(P.PRISM_TUNE_ROW, P.PRISM_TUNE_MAX_SHAPES) == -1
+
+
 def test_no_cpu_fallback_without_a_gpu():
     """The torch-facing layer refuses to run without a CUDA device instead of falling back to a
     host path (there is none)."""
