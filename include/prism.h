@@ -25,7 +25,8 @@
  *   - Status: every int-returning call returns PRISM_OK (0) or a negative PRISM_ERR_* code;
  *     prism_last_error() then describes the failure (thread-local string).
  *   - Determinism: the same inputs give bitwise-identical outputs (no order-dependent
- *     atomics; fixed reduction trees).
+ *     atomics; fixed reduction trees) for the same launch shapes; an autotuned plan may pick
+ *     another FFT radix variant by timing, which agrees to rounding (prism_plan_autotune).
  *   - Memory: the caller owns every pointer it passes in; the plan owns the transmission
  *     functions, the S-matrix, its wave scratch and small tables, allocated with
  *     stream-ordered cudaMallocAsync and released by prism_plan_destroy().
