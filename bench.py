@@ -337,7 +337,7 @@ def batch_leg(n_cells=64, runs=2, n_branches=4, autotune=True):
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         t1 = time.perf_counter()
-        b = Batch(cells, n_branches=n_branches, stream=stream, autotune=autotune)
+        b = Batch(cells, n_branches=n_branches, stream=stream, autotune=autotune, fft_radix=autotune)
         create_s = time.perf_counter() - t1
         b.run()
         b.sync()
@@ -484,7 +484,7 @@ def main():
     with torch.cuda.stream(stream):
         sim = PrismSimulation(grid, 0, stream)
         Bn = sim.info.n_beams
-        tune = None if args.no_autotune else sim.autotune()
+        tune = None if args.no_autotune else sim.autotune(fft_radix=True)
         out = torch.empty((P, DET["nbins"]), dtype=torch.float32, device="cuda")
 
         def step():

@@ -25,8 +25,8 @@
  *   - Status: every int-returning call returns PRISM_OK (0) or a negative PRISM_ERR_* code;
  *     prism_last_error() then describes the failure (thread-local string).
  *   - Determinism: the same inputs give bitwise-identical outputs (no order-dependent
- *     atomics; fixed reduction trees) for the same launch shapes; an autotuned plan may pick
- *     another FFT radix variant by timing, which agrees to rounding (prism_plan_autotune).
+ *     atomics; fixed reduction trees), autotuned or not; only a plan tuned with the FFT radix
+ *     variants (PRISM_AUTOTUNE_FFT_RADIX) may pick another rounding by timing.
  *   - Memory: the caller owns every pointer it passes in; the plan owns the transmission
  *     functions, the S-matrix, its wave scratch and small tables, allocated with
  *     stream-ordered cudaMallocAsync and released by prism_plan_destroy().
@@ -314,8 +314,9 @@ void prism_server_destroy(prism_server *server);
  * and keeps the fastest for the plan's later builds.  Shapes exist for N = 256 ... 2048; smaller
  * grids keep their single shape.  Shapes of one radix variant compute bitwise the same result; the
  * radix variants compute the same transforms rounded differently (they agree to FP32 rounding,
- * well inside the FP32 path's tolerance against the FP64 oracle), so a plan that picks another
- * variant than the default's reproduces its S-matrix to rounding, not bit for bit.  Results are
+ * well inside the FP32 path's tolerance against the FP64 oracle) and are candidates only when the
+ * caller asks for them (prism_plan_autotune_flags), so that a plainly autotuned plan reproduces the
+ * untuned plan bit for bit.  Results are
  * cached for the process per (pass, N, batch).  Synchronous; overwrites the wave scratch only (the
  * S-matrix is untouched).  The paper has no counterpart. */
 #define PRISM_TUNE_ROW 0
@@ -329,6 +330,12 @@ typedef struct prism_tune_entry {
     double ms[PRISM_TUNE_MAX_SHAPES]; /* mean time per launch of each shape, -1 if not compiled   */
 } prism_tune_entry;
 int prism_plan_autotune(prism_plan *plan);
+/* prism_plan_autotune with flags: PRISM_AUTOTUNE_FFT_RADIX also times the FFT radix variants
+ * (prism_tune_shape_fft_variant) and may keep one, whose results agree with the default's to
+ * rounding but not bit for bit; without it (prism_plan_autotune) the tuner keeps the default radix
+ * and every result stays bitwise that of the untuned plan.  INVALID for unknown flags. */
+#define PRISM_AUTOTUNE_FFT_RADIX 1
+int prism_plan_autotune_flags(prism_plan *plan, int flags);
 /* The scan's contraction tile shape (the scan term of the Calculation Time section's cost model):
  * raster blocks of 4 x 8, 8 x 4 or 2 x 16 probes and beam rings of 2 x 32 or 3 x 16, compiled for
  * the FP32 GEMM scan with square windows of 16, 32 or 64 pixels.  Runs the given scan once per
@@ -389,7 +396,8 @@ typedef struct prism_batch prism_batch;
  * index in the message), upload its scan inputs, optionally autotune it (flags), and capture the
  * graph.  n_branches in [1, 16] (0 = min(n_cells, 4)).  hbm_budget_bytes bounds the sum of the plans' device memory (0 = no
  * limit; BUDGET if exceeded).  The graph is launched into cuda_stream (NULL = legacy default). */
-#define PRISM_BATCH_AUTOTUNE 1  /* flags: autotune every cell's plan before the capture */
+#define PRISM_BATCH_AUTOTUNE 1  /* flags: autotune every cell's plan's launch shapes before the capture */
+#define PRISM_BATCH_AUTOTUNE_FFT_RADIX 2  /* flags: the same with the FFT radix variants as candidates */
 int prism_batch_create(const prism_cell *cells, int n_cells, size_t hbm_budget_bytes, int n_branches, int flags,
                        void *cuda_stream, prism_batch **out);
 /* Enqueue one run of the whole batch (asynchronous on the batch's stream). */

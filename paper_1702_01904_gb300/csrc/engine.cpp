@@ -1543,8 +1543,13 @@ int internal_multislice_tables(const prism_grid *grid, const prism_probe *probe,
 struct TuneKey {
     int kind, n, batch;
     bool shared;  // tuned for a batch whose branches share the SMs
+    bool radix;   // the FFT radix variants were candidates
     bool operator<(const TuneKey &o) const {
-        return kind != o.kind ? kind < o.kind : n != o.n ? n < o.n : batch != o.batch ? batch < o.batch : shared < o.shared;
+        return kind != o.kind     ? kind < o.kind
+               : n != o.n         ? n < o.n
+               : batch != o.batch ? batch < o.batch
+               : shared != o.shared ? shared < o.shared
+                                    : radix < o.radix;
     }
 };
 struct TuneVal {
@@ -1575,8 +1580,12 @@ extern "C" int prism_plan_set_tune_shape(prism_plan *P, int kind, int shape) {
     return PRISM_OK;
 }
 
-extern "C" int prism_plan_autotune(prism_plan *P) {
+extern "C" int prism_plan_autotune(prism_plan *P) { return prism_plan_autotune_flags(P, 0); }
+
+extern "C" int prism_plan_autotune_flags(prism_plan *P, int flags) {
     if (!P) return fail(PRISM_ERR_INVALID, "plan is NULL");
+    if (flags & ~PRISM_AUTOTUNE_FFT_RADIX) return fail(PRISM_ERR_INVALID, "unknown autotune flags");
+    const bool radix = (flags & PRISM_AUTOTUNE_FFT_RADIX) != 0;
     const prism_grid &g = P->g;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -1584,7 +1593,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
     int rc = PRISM_OK;
     for (int kind = 0; kind < 2 && !rc; ++kind) {
         const int n = kind == 0 ? g.nx : g.ny;
-        const TuneKey key{kind, n, P->batch, P->shared_sms};
+        const TuneKey key{kind, n, P->batch, P->shared_sms, radix};
         for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->tune_ms[kind][v] = -1.0;
         P->tuned[kind] = true;
         {
@@ -1600,7 +1609,7 @@ extern "C" int prism_plan_autotune(prism_plan *P) {
         double best_ms = 0;
         for (int v = 0; v < tune_shapes(kind) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
             if (!tune_shape_valid(kind, n, v) || (tune_shape_needs_map(kind, v) && !P->wave_map_ok) ||
-                (P->shared_sms && tune_shape_fills_sm(kind, v)))
+                (P->shared_sms && tune_shape_fills_sm(kind, v)) || (!radix && tune_shape_fft_variant(kind, v) != 0))
                 continue;
             RowArgs ra = row_args(P);
             ra.trans = P->t;
@@ -1761,6 +1770,7 @@ extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t h
     *out = nullptr;
     if (!cells || n_cells < 1) return fail(PRISM_ERR_INVALID, "need at least one cell");
     if (n_branches < 0 || n_branches > 16) return fail(PRISM_ERR_INVALID, "n_branches must be in [0, 16]");
+    if (flags & ~(PRISM_BATCH_AUTOTUNE | PRISM_BATCH_AUTOTUNE_FFT_RADIX)) return fail(PRISM_ERR_INVALID, "unknown batch flags");
     const int nb = n_branches ? std::min(n_branches, n_cells) : std::min(n_cells, 4);
     int rc;
     for (int i = 0; i < n_cells; ++i) {
@@ -1793,7 +1803,9 @@ extern "C" int prism_batch_create(const prism_cell *cells, int n_cells, size_t h
         if ((rc = prism_plan_create(&c.grid, 0, B->origin, &P))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
         B->plans.push_back(P);
         P->shared_sms = nb > 1;
-        if ((flags & PRISM_BATCH_AUTOTUNE) && (rc = prism_plan_autotune(P))) return bail(rc);
+        if ((flags & (PRISM_BATCH_AUTOTUNE | PRISM_BATCH_AUTOTUNE_FFT_RADIX)) &&
+            (rc = prism_plan_autotune_flags(P, (flags & PRISM_BATCH_AUTOTUNE_FFT_RADIX) ? PRISM_AUTOTUNE_FFT_RADIX : 0)))
+            return bail(rc);
         ScanArgs a;
         if ((rc = scan_prepare(P, &c.probe, &c.scan, &c.det, a, false))) return fail(rc, "cell " + std::to_string(i) + ": " + g_err), bail(rc);
         a.out = c.out_dev;

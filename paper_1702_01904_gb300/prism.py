@@ -37,6 +37,8 @@ PRISM_TUNE_COL = 1
 PRISM_TUNE_SCAN = 2
 PRISM_TUNE_MAX_SHAPES = 16
 PRISM_BATCH_AUTOTUNE = 1
+PRISM_BATCH_AUTOTUNE_FFT_RADIX = 2
+PRISM_AUTOTUNE_FFT_RADIX = 1
 
 # every entry point declared in include/prism.h
 EXPORTED = [
@@ -52,7 +54,7 @@ EXPORTED = [
     "prism_selftest_tcgen05", "prism_selftest_bounded_wait",
     "prism_batch_create", "prism_batch_run", "prism_batch_sync", "prism_batch_info_get", "prism_batch_destroy",
     "prism_plan_autotune", "prism_plan_autotune_scan", "prism_plan_tune_result", "prism_tune_shape_name", "prism_plan_set_tune_shape",
-    "prism_tune_shape_fft_variant",
+    "prism_tune_shape_fft_variant", "prism_plan_autotune_flags",
     "prism_plan_load_smatrix",
 ]
 
@@ -154,6 +156,7 @@ def load(path: str = LIB_PATH):
         "prism_plan_smatrix_copy": (c_int, [P, P]),
         "prism_batch_create": (c_int, [POINTER(PrismCell), c_int, c_size_t, c_int, c_int, P, POINTER(P)]),
         "prism_plan_autotune": (c_int, [P]),
+        "prism_plan_autotune_flags": (c_int, [P, c_int]),
         "prism_plan_autotune_scan": (c_int, [P, POINTER(PrismProbe), POINTER(PrismScan), POINTER(PrismDetector), P]),
         "prism_plan_tune_result": (c_int, [P, c_int, POINTER(PrismTuneEntry)]),
         "prism_tune_shape_name": (c_char_p, [c_int, c_int]),
@@ -458,6 +461,10 @@ def prism_batch_destroy(batch):
 # ------------------------------------------------------------------ autotuner
 def prism_plan_autotune(plan):
     _check(load().prism_plan_autotune(plan))
+
+
+def prism_plan_autotune_flags(plan, flags):
+    _check(load().prism_plan_autotune_flags(plan, flags))
 
 
 def prism_plan_autotune_scan(plan, probe, scan, det, out_dev):

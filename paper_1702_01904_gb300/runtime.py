@@ -94,10 +94,12 @@ class PrismSimulation:
     def sync(self):
         P.prism_sync(self.plan)
 
-    def autotune(self):
+    def autotune(self, fft_radix: bool = False):
         """Time every launch shape of the row and column passes on this plan and keep the fastest
-        (prism_plan_autotune); returns {pass: {"chosen": name, "default": name, "ms": {name: ms}}}."""
-        P.prism_plan_autotune(self.plan)
+        (prism_plan_autotune); with fft_radix also the FFT radix variants, which round differently
+        (prism_plan_autotune_flags).  Returns {pass: {"chosen": name, "default": name, "ms": {name:
+        ms}, "fft_variant": v}}."""
+        P.prism_plan_autotune_flags(self.plan, P.PRISM_AUTOTUNE_FFT_RADIX if fft_radix else 0)
         return self.tune_result()
 
     def autotune_scan(self, probe, x0, y0, det, out: torch.Tensor | None = None, px=None, py=None):
@@ -207,9 +209,11 @@ class Batch:
     ``cells`` is a list of dicts with keys grid (PrismGrid), V (CUDA float32 tensor
     [n_slices][ny][nx]), probe, x0, y0, det and optionally px, py.  The potentials are read and the
     outputs (``self.outs[i]``, [px*py][nbins]) written at every ``run``; V's contents may change
-    between runs."""
+    between runs.  ``autotune`` times each cell's pass launch shapes before the capture,
+    ``fft_radix`` adds the FFT radix variants as candidates (results then agree to rounding)."""
 
-    def __init__(self, cells, hbm_budget_bytes: int = 0, n_branches: int = 0, stream=None, autotune: bool = False):
+    def __init__(self, cells, hbm_budget_bytes: int = 0, n_branches: int = 0, stream=None, autotune: bool = False,
+                 fft_radix: bool = False):
         _require_cuda()
         P.load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -233,8 +237,8 @@ class Batch:
             self._keep.append((V, sc, g))
             self.outs.append(out)
         torch.cuda.current_stream().synchronize()
-        self.batch = P.prism_batch_create(cs, hbm_budget_bytes, n_branches, self.stream,
-                                          P.PRISM_BATCH_AUTOTUNE if autotune else 0)
+        flags = (P.PRISM_BATCH_AUTOTUNE_FFT_RADIX if fft_radix else P.PRISM_BATCH_AUTOTUNE) if autotune else 0
+        self.batch = P.prism_batch_create(cs, hbm_budget_bytes, n_branches, self.stream, flags)
         self.info = P.prism_batch_info_get(self.batch)
 
     def run(self):

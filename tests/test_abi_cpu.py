@@ -160,6 +160,9 @@ def test_tune_shapes_list_both_fft_radix_variants():
         assert all(n.endswith({1: "forward", 2: "inverse", 3: "both"}[r]) for n, r in rv.items() if r)
     assert rv["W4, TMA, 3/SM"] == 0 and rv["W8, staged"] == 0
     assert P.prism_tune_shape_fft_variant(P.PRISM_TUNE_SCAN, 0) == -1
+    with pytest.raises(P.PrismError) as e:
+        P.prism_plan_autotune_flags(None, P.PRISM_AUTOTUNE_FFT_RADIX)
+    assert e.value.status == P.PRISM_ERR_INVALID
     assert P.prism_tune_shape_fft_variant(P.PRISM_TUNE_ROW, P.PRISM_TUNE_MAX_SHAPES) == -1
 
 

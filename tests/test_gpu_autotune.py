@@ -40,9 +40,9 @@ def rel_l2(a, b):
 RADIX_TOL = {P.PRISM_PRECISION_FP32: 1e-5, P.PRISM_PRECISION_FP16: 1e-4}
 
 
-def run(grid, V, tune, x0, y0):
+def run(grid, V, tune, x0, y0, fft_radix=False):
     sim = PrismSimulation(grid)
-    res = sim.autotune() if tune else None
+    res = sim.autotune(fft_radix) if tune else None
     sim.build(V)
     out = sim.scan(P.make_probe(20.0, c1=8.0), x0, y0, DET, px=len(x0), py=1).cpu().numpy()
     S = sim.smatrix().cpu().numpy()
@@ -50,27 +50,33 @@ def run(grid, V, tune, x0, y0):
     return out, S, res
 
 
+@pytest.mark.parametrize("fft_radix", [False, True])
 @pytest.mark.parametrize("n,cell,f,prec", [(256, 16.0, 4, P.PRISM_PRECISION_FP32), (512, 32.0, 8, P.PRISM_PRECISION_FP16)])
-def test_autotuned_plan_matches_the_default_plan(n, cell, f, prec):
+def test_autotuned_plan_matches_the_default_plan(n, cell, f, prec, fft_radix):
+    # plain autotuning keeps the default FFT radix: bit for bit; with the radix variants as
+    # candidates a plan that keeps one agrees to rounding
     grid = P.make_grid(n, n, 3, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0, precision=prec)
     V = rand_v(3, n, 11)
     x0 = np.linspace(0.0, cell, 13, endpoint=False)
     y0 = np.linspace(1.0, 3.0, 13)
     a, Sa, _ = run(grid, V, False, x0, y0)
-    b, Sb, res = run(grid, V, True, x0, y0)
+    b, Sb, res = run(grid, V, True, x0, y0, fft_radix)
     if res["row"]["fft_variant"] == 0 and res["col"]["fft_variant"] == 0:
         assert np.array_equal(a, b) and np.array_equal(Sa, Sb)
     else:
-        assert n >= 512  # the radix variants exist where the transforms use 32- or 64-point DFTs
+        assert fft_radix and n >= 512  # variants only when asked for, where 32-/64-point DFTs are used
         assert rel_l2(Sb, Sa) <= RADIX_TOL[prec] and rel_l2(b, a) <= RADIX_TOL[prec]
     for label in ("row", "col"):
+        names = [k for k in res[label]["ms"]]
+        assert fft_radix or not any("radix-4 first" in k for k in names)
+        assert not fft_radix or n < 512 or any("radix-4 first" in k for k in names)
         ms = res[label]["ms"]
         assert len(ms) >= 2 and all(v > 0 for v in ms.values())
         assert res[label]["chosen"] in ms and res[label]["default"] in ms
         assert ms[res[label]["chosen"]] == min(ms.values())
     # a second plan of the same shape reuses the cached choice
     sim = PrismSimulation(grid)
-    assert sim.autotune() == res
+    assert sim.autotune(fft_radix) == res
     sim.close()
 
 
@@ -132,7 +138,8 @@ def test_small_grid_has_only_the_default_shape():
     sim.close()
 
 
-def test_autotuned_batch_equals_untuned():
+@pytest.mark.parametrize("fft_radix", [False, True])
+def test_autotuned_batch_equals_untuned(fft_radix):
     cells = []
     for i, (n, cell, f, H) in enumerate([(256, 16.0, 4, 3), (512, 32.0, 8, 2), (128, 12.8, 2, 2)]):
         x0 = np.linspace(0.0, 4.0, 8)
@@ -140,14 +147,15 @@ def test_autotuned_batch_equals_untuned():
                           probe=P.make_probe(20.0), x0=x0, y0=np.full(8, 1.5), det=DET))
     outs = []
     for tune in (False, True):
-        b = Batch(cells, n_branches=2, autotune=tune)
+        b = Batch(cells, n_branches=2, autotune=tune, fft_radix=fft_radix and tune)
         b.run()
         b.sync()
         outs.append([o.cpu().numpy() for o in b.outs])
         b.close()
     for c, u, t in zip(cells, *outs):
-        # below N = 512 there is one radix variant: bit for bit; the 512^2 cell may take the other
-        if c["grid"].nx < 512:
+        # launch shapes alone, or below N = 512 (one radix variant): bit for bit; the 512^2 cell tuned
+        # with the radix variants may take another
+        if not fft_radix or c["grid"].nx < 512:
             assert np.array_equal(u, t)
         else:
             assert np.array_equal(u, t) or rel_l2(t, u) <= RADIX_TOL[P.PRISM_PRECISION_FP32]
