@@ -288,8 +288,11 @@ struct TcCfg {
     static constexpr int GX = 8, GY = 4, G = GX * GY, N = 2 * G;
     static constexpr int BLOCK = 256;
     static constexpr int PARTS = SPLIT ? 2 : 1;              // hi (and lo) operand parts
-    static constexpr int STAGES = 2;
-    static constexpr int KCMAX = SPLIT ? 32 : 128;           // K (16-bit values) per ring stage
+    // ring of K chunks: 3 stages of 96 (a load is issued two steps before its MMAs; K = 272 of the
+    // 129-beam set is 3 chunks, as with 2 stages of 128), or 2 of 32 in split mode (its two operand
+    // parts fill the shared memory of two CTAs per SM)
+    static constexpr int STAGES = SPLIT ? 2 : 3;
+    static constexpr int KCMAX = SPLIT ? 32 : 96;            // K (16-bit values) per ring stage
     static constexpr int PART_BYTES = 128 * KCMAX * 2;       // 128 pixels x KCMAX of one part
     static constexpr int STAGE_BYTES = PARTS * PART_BYTES;
     static constexpr int RING = STAGES * STAGE_BYTES;
