@@ -79,7 +79,10 @@ __device__ void group_geometry(const ScanArgs &a, int p0, int gn, int *meta) {
 // Geometry of a GX x GY block of the probe raster (group gx, gy), NWX x NWY windows; executed by
 // one warp, lane p = slot j * GX + i for raster row gy*GY + j, column gx*GX + i (GX*GY <= 32).
 // Window origins follow Eq. RegionBounds in FP64; the union tile of the slots' windows is used
-// when it is no larger than their windows together, else each probe runs on its own window.
+// when it is no larger than their windows together, else each probe runs on its own window.  The
+// union tile starts on an even column and has an even width (a leading column where the windows
+// start on an odd one, a trailing one to an even width), so that its rows are 16-byte aligned runs
+// of pixel pairs.
 // meta (ints): [0] union tile  [1] tile width  [2] tile height  [3] tile x0  [4] tile y0
 // [5] probes in the group; per slot p < 32: [8+p] window x0  [40+p] window y0  [72+p] x offset in
 // the tile  [104+p] y offset in the tile  [136+p] probe index or -1; [168+e] slot of the e-th
@@ -103,11 +106,12 @@ __device__ void raster_group_geometry(const ScanArgs &a, int gx, int gy, int *me
     const int dymin = __reduce_min_sync(0xffffffffu, dy), dymax = __reduce_max_sync(0xffffffffu, dy);
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
     const int nvalid = __popc(vm);
-    const int tw = dxmax - dxmin + NWX, th = dymax - dymin + NWY;
+    const int tx0 = (sx0 + dxmin) & (a.nx_s - 1), shift = tx0 & 1;
+    const int tw = (dxmax - dxmin + NWX + shift + 1) & ~1, th = dymax - dymin + NWY;
     if (p < G) {
         meta[8 + p] = sx;
         meta[40 + p] = sy;
-        meta[72 + p] = dx - dxmin;
+        meta[72 + p] = dx - dxmin + shift;
         meta[104 + p] = dy - dymin;
         meta[136 + p] = valid ? row * a.scan_px + col : -1;
     }
@@ -117,10 +121,10 @@ __device__ void raster_group_geometry(const ScanArgs &a, int gx, int gy, int *me
         meta[200 + e] = row * a.scan_px + col;
     }
     if (lane == 0) {
-        meta[0] = (long long)tw * th <= (long long)nvalid * NWX * NWY;
+        meta[0] = (long long)(dxmax - dxmin + NWX) * th <= (long long)nvalid * NWX * NWY;  // before the even padding
         meta[1] = tw;
         meta[2] = th;
-        meta[3] = (sx0 + dxmin) & (a.nx_s - 1);
+        meta[3] = tx0 - shift;
         meta[4] = (sy0 + dymin) & (a.ny_s - 1);
         meta[5] = nvalid;
     }

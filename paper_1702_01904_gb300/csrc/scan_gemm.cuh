@@ -18,7 +18,9 @@ namespace prism {
 // union tile of their windows, on the CUDA cores in FP32: psi_p(r) = sum_b S_b(r) alpha_bp for the
 // tile pixels r (M) and the block's 32 probes (N), K = the beams.  The tile is streamed in M tiles
 // of 128 pixels; per M tile the beams pass through a 2-stage cp.async ring (KB beams x 128 pixels
-// per stage, one 8-byte copy per pixel and beam); thread (lane, warp) accumulates pixels lane +
+// per stage, one 16-byte copy per pixel pair and beam: the union tile starts on an even column and
+// has an even width, so a pair never straddles a row or the cell's edge and is 16-byte aligned in
+// the S-matrix); thread (lane, warp) accumulates pixels lane +
 // 32 i (i < 4) for probes 4 warp + j (j < 4) -- raster row `warp` of the block -- in registers, so
 // one 8-byte shared-memory load feeds four complex MACs.  A warp skips the M tiles that lie wholly
 // above or below its row's windows (the union tile is NWY + 7 probe steps high, a row's windows
@@ -124,8 +126,10 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
         const bool uni = meta[0] != 0;
         for (int sg = 0; sg < (uni ? 1 : G); ++sg) {
             if (!uni && (meta[136 + sg] < 0 || sg % np != part)) continue;
-            const int tw = uni ? meta[1] : NWX, th = uni ? meta[2] : NWY;
-            const int tx0 = uni ? meta[3] : meta[8 + sg], ty0 = uni ? meta[4] : meta[40 + sg];
+            // probe by probe: the window widened to start on an even column (ox = its odd start)
+            const int ox = uni ? 0 : meta[8 + sg] & 1;
+            const int tw = uni ? meta[1] : NWX + 2 * ox, th = uni ? meta[2] : NWY;
+            const int tx0 = uni ? meta[3] : meta[8 + sg] - ox, ty0 = uni ? meta[4] : meta[40 + sg];
             const int npx = tw * th, nmt = (npx + MT - 1) / MT;
             // ring steps (M tile, beam chunk) of this unit: all, or a split block's share of M tiles
             const int ls0 = uni ? part * nmt / np * nkc : 0, ls1 = uni ? (part + 1) * nmt / np * nkc : nmt * nkc;
@@ -146,8 +150,10 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                     }
                 }
             }
-            // loader: thread -> tile pixel m = tid % MT, beams kk = tid / MT, + 2, ...
-            const int lm = tid & (MT - 1), lk = tid >> 7;
+            // loader: thread -> tile pixel pair m = 2 (tid % (MT/2)), beams kk = tid / (MT/2), + 4, ...
+            // (tw, tx0 and the M tile bounds even: the pair lies in one row, on an even column)
+            constexpr int PAIRS = MT / 2, KSTEP = BLOCK / PAIRS;
+            const int lm = 2 * (tid & (PAIRS - 1)), lk = tid / PAIRS;
             auto load = [&](int ls) {
                 if (ls < ls1) {
                     const int mt = ls / nkc, c = ls - mt * nkc;
@@ -157,7 +163,8 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                         const int ty = idx / tw, tx = idx - ty * tw;
                         const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
                         float2 *dst = ring + (ls % S) * (KB * MT) + lm;
-                        for (int kk = lk; kk < bn; kk += BLOCK / MT) cp_async8(dst + kk * MT, a.S + (size_t)(b0 + kk) * npix_s + gp);
+                        const float2 *src = a.S + (size_t)(b0 + lk) * npix_s + gp;
+                        for (int kk = lk; kk < bn; kk += KSTEP, src += (size_t)KSTEP * npix_s) cp_async16(dst + kk * MT, src);
                     }
                 }
                 cp_async_commit();
@@ -211,7 +218,7 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                             for (int j = 0; j < 4; ++j) {
                                 const int p = 4 * warp + j;
                                 const bool act = uni ? meta[136 + p] >= 0 : p == sg;
-                                const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
+                                const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : ox);
                                 // psi = accr + i acci
                                 const float2 v = make_float2(accr[i][j].x - acci[i][j].y, accr[i][j].y + acci[i][j].x);
                                 if (act && idx < npx && (unsigned)wy < (unsigned)NWY && (unsigned)wx < (unsigned)NWX)
@@ -281,6 +288,8 @@ static int gemm_grid(int n_beams, int scan_px, int scan_py) {
 template <int NWX, int NWY, int SH = 0>
 static cudaError_t gemm_launch(int grid, const ScanArgs &a, cudaStream_t s) {
     using C = GemmCfg<NWX, NWY, SH>;
+    // the ring's 16-byte copies read pixel pairs of the S-matrix
+    if (reinterpret_cast<uintptr_t>(a.S) & 15) return cudaErrorMisalignedAddress;
     const size_t smem = C::smem(a.n_beams);
     cudaError_t e = cudaFuncSetAttribute(k_scan_gemm<NWX, NWY, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
