@@ -346,6 +346,9 @@ struct FftShape {
     static_assert(N1 > 0, "unsupported FFT length");
 };
 
+// Where BlockFft::run finds its inter-stage twiddle table and in which order it reads it
+enum { TW_SMEM = 0, TW_GLOBAL = 1, TW_SMEM_SEQ = 2 };
+
 // A no-op in place of BlockFft::run's hook
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
@@ -365,20 +368,22 @@ struct BlockFft {
     static constexpr int J = E / N1;
     static constexpr int I = E / N2;
 
-    // GTW: the twiddle table is in global memory (read through the read-only path); otherwise it
-    // is in shared memory
+    // GTW: where the twiddle table is and how it is read: TW_SMEM (shared memory, every twiddle
+    // loaded before the first exchange store), TW_GLOBAL (global memory through the read-only path,
+    // each twiddle loaded, applied and stored in turn, which keeps register pressure at the level
+    // of one element) or TW_SMEM_SEQ (shared memory, read in that interleaved order)
     // ZIN: input registers known to be exactly zero in every thread (bit r: register r)
     // LEAD: synchronise before the exchange is written (off where the caller has already ordered
     // every earlier access of the buffer before this call's writes)
     // hook(): called by every thread right after the barrier that follows the exchange writes
-    template <class Ex, bool GTW = false, unsigned long long ZIN = 0, bool LEAD = true, class Hook = NoHook>
+    template <class Ex, int GTW = TW_SMEM, unsigned long long ZIN = 0, bool LEAD = true, class Hook = NoHook>
     __device__ __forceinline__ static void run(float2 (&x)[E], int t, const float2 *__restrict__ stw,
                                                const Tw64 &tw, Ex &ex, Hook hook = Hook{}) {
         static_for<J>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             Dft<N1, J, INV, sub_mask<N1, J>(ZIN, j), V>::run(x + j, tw);
         });
-        if constexpr (!GTW) {
+        if constexpr (GTW == TW_SMEM) {
             // shared-memory table: all twiddle loads before any exchange store (the table and the
             // exchange share the address space, and this order lets the loads issue back to back)
 #pragma unroll
@@ -398,8 +403,7 @@ struct BlockFft {
                 for (int k1 = 0; k1 < N1; ++k1) ex.write(k1, n2, x[k1 * J + j]);
             }
         } else {
-            // global table (read-only path, L1-resident): interleave load, multiply and store, which
-            // keeps register pressure at the level of one element
+            // interleave load, multiply and store (TW_GLOBAL: read-only path, L1-resident)
             if constexpr (LEAD) ex.sync();
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -408,7 +412,7 @@ struct BlockFft {
                 for (int k1 = 0; k1 < N1; ++k1) {
                     float2 v = x[k1 * J + j];
                     if (k1 != 0) {
-                        const float2 w = __ldg(stw + k1 * N2 + n2);
+                        const float2 w = GTW == TW_GLOBAL ? __ldg(stw + k1 * N2 + n2) : stw[k1 * N2 + n2];
                         v = INV ? cmulc(v, w) : cmul(v, w);
                     }
                     ex.write(k1, n2, v);

@@ -255,16 +255,16 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                     float2 tv[E];
 #pragma unroll
                     for (int r = 0; r < E; ++r) tv[r] = __ldcg(tp + Inv::out_elem(r, t));
-                    Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], tv[r]);
                 } else {
-                    Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], __ldcg(tp + Inv::out_elem(r, t)));
                 }
             } else {
-                Inv::template run<decltype(exI), false, ZIN>(v, t, twi, a.tw, exI);
+                Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
             }
         }
         if constexpr (MODE == ROW_OUT) {
@@ -351,13 +351,17 @@ struct ColCfg {
     static constexpr bool TMA = TM;
     static constexpr bool STAGE = STG || TM;  // staging of the next tile (cp.async or TMA)
     static constexpr int BOXR = NY < 256 ? NY : 256;  // rows per TMA box
-    static constexpr bool SMEM_TW = false; // stage twiddles in shared memory (else L1 broadcast loads)
+    // TMA-staged shapes of a square split (forward and inverse use the same table, the inverse its
+    // conjugate): one twiddle table in shared memory, read interleaved with the exchange stores;
+    // else the tables through L1 (read-only path)
+    static constexpr bool SMEM_TW = TM && FS::N1 == FS::N2;
+    static constexpr int TW_MODE = SMEM_TW ? TW_SMEM_SEQ : TW_GLOBAL;
     static constexpr bool PERSIST = true;  // grid = resident CTAs, each looping over tiles
     static constexpr int MINB = MB > 0 ? MB : (PERSIST || STAGE) ? 1 : 2;  // CTAs per SM the registers must allow
     static constexpr int EX = ColExSize<NY, W>::value;
     static_assert(EX >= NY * W, "the exchange buffer holds a whole tile (TMA stores)");
     static_assert(!TM || (FS::T % (32 / W) == 0 && FS::T * W >= 32), "TMA stores: whole warps of lanes per column");
-    static constexpr size_t SMEM = (size_t)((SMEM_TW ? 2 * NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)((SMEM_TW ? NY : 0) + (STAGE ? NY * W : 0) + EX) * sizeof(float2);
 };
 
 // TMA staging gives up after this many SM cycles (about a second) and reports it in the error word
@@ -388,15 +392,12 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
     const float2 *twf = a.tw_fwd, *twi = a.tw_inv;
     if constexpr (C::SMEM_TW) {
         float2 *tws = smem;
-        for (int i = threadIdx.x; i < NY; i += THREADS) {
-            tws[i] = a.tw_fwd[i];
-            tws[NY + i] = a.tw_inv[i];
-        }
+        for (int i = threadIdx.x; i < NY; i += THREADS) tws[i] = a.tw_fwd[i];
         __syncthreads();
         twf = tws;
-        twi = tws + NY;
+        twi = tws;  // the square split's inverse table holds the same values
     }
-    float2 *stg = smem + (C::SMEM_TW ? 2 * NY : 0);
+    float2 *stg = smem + (C::SMEM_TW ? NY : 0);
     float2 *exb = stg + (C::STAGE ? NY * W : 0);
     const int c = threadIdx.x % W, t = threadIdx.x / W, lane = threadIdx.x & 31;
     ColExchange<FS::N1, FS::N2, W> exF{exb, c};
@@ -513,11 +514,11 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                 // the barrier after the tile's arrival ordered every earlier use of the exchange
                 // before its writes here (no leading barrier), and the barrier after them is the
                 // point where every thread has read the staging buffer: its refill starts there
-                Fwd::template run<decltype(exF), !C::SMEM_TW, 0ull, false>(v, t, twf, a.tw, exF, [&] {
+                Fwd::template run<decltype(exF), C::TW_MODE, 0ull, false>(v, t, twf, a.tw, exF, [&] {
                     if (it + 1 < iters) stage(tile + gridDim.x);
                 });
             } else {
-                Fwd::template run<decltype(exF), !C::SMEM_TW>(v, t, twf, a.tw, exF);
+                Fwd::template run<decltype(exF), C::TW_MODE>(v, t, twf, a.tw, exF);
             }
             // Fresnel propagator exp(-i pi lambda t |q|^2) (separable) inside the anti-aliasing
             // aperture, which on column kx is |ky| <= aa_kmax[kx]
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
         }
         // after the propagator the out-of-band registers are exact zeros (band4, compile-time band)
         constexpr unsigned long long ZC = BL && MODE != COL_PROBE ? band_zero_mask<Fwd, NY>(false) : 0ull;
-        Inv::template run<decltype(exI), !C::SMEM_TW, ZC>(v, t, twi, a.tw, exI);
+        Inv::template run<decltype(exI), C::TW_MODE, ZC>(v, t, twi, a.tw, exI);
         if constexpr (MODE == COL_PROBE) {
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = cscale(v[r], a.probe_scale);
