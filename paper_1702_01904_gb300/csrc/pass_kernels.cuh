@@ -454,6 +454,16 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
             return;
         }
     }
+    // TMA-staged shapes: the propagator's y factor of every register this thread transforms (rows
+    // t + T r, the same in every tile) loaded once into registers
+    float2 pyr[E];
+    if constexpr (C::TMA && MODE == COL_STD) {
+        static_for<E>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            constexpr int cls = BL ? BandClass<Fwd, NY>::of(r, false) : BAND_MIXED;
+            if constexpr (cls != BAND_OUT) pyr[r] = __ldg(a.prop_y + Fwd::out_elem(r, t));
+        });
+    }
     if constexpr (MODE != COL_PROBE && C::STAGE) stage(blockIdx.x);
     // without persistence every CTA owns exactly one tile and there is no loop (a loop would let
     // the compiler hoist the loop-invariant twiddle loads and hold them in registers)
@@ -533,7 +543,8 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                     const int ky = Fwd::out_elem(r, t);
                     const int kys = ky < (NY >> 1) ? ky : ky - NY;
                     const int aky = kys < 0 ? -kys : kys;
-                    v[r] = aky <= kymax ? cmul(v[r], cmul(px, __ldg(a.prop_y + ky))) : make_float2(0.f, 0.f);
+                    const float2 py = C::TMA && MODE == COL_STD ? pyr[r] : __ldg(a.prop_y + ky);
+                    v[r] = aky <= kymax ? cmul(v[r], cmul(px, py)) : make_float2(0.f, 0.f);
                 }
             });
             if constexpr (MODE == COL_DETECT) {
