@@ -47,6 +47,10 @@ __global__ void __launch_bounds__(256) k_plane(const float2 *__restrict__ T0, fl
                                                const int *__restrict__ beam_mn, int beam0, int nb, int nx, int ny,
                                                int f, int f_y, int kx_half) {
     const int kept = kx_half > 0 ? 2 * kx_half - 1 : nx;  // kx = 0 .. kh-1 and nx-kh+1 .. nx-1
+    // with f even every beam's shift m f is even and the kept runs start on even columns (kh even,
+    // or no pruning), so rows go as 16-byte pixel pairs
+    const bool pairs = (f & 1) == 0 && (kx_half & 1) == 0 && (nx & 1) == 0;
+    const int npairs = kx_half > 0 ? kx_half : nx / 2;  // kh/2 low + kh/2 high pairs, or all
     for (int row = blockIdx.x; row < nb * ny; row += gridDim.x) {
         const int b = row / ny, y = row - b * ny;
         const int m = __ldg(beam_mn + 2 * (beam0 + b)), n = __ldg(beam_mn + 2 * (beam0 + b) + 1);
@@ -57,9 +61,23 @@ __global__ void __launch_bounds__(256) k_plane(const float2 *__restrict__ T0, fl
         const float2 *t0 = T0 + (size_t)y * nx;
         float2 *w = wave + (size_t)row * nx;
         const int shift = m * f;
-        for (int j = threadIdx.x; j < kept; j += blockDim.x) {
-            const int kx = kx_half > 0 && j >= kx_half ? nx - 2 * kx_half + 1 + j : j;
-            w[kx] = cmul(__ldg(t0 + ((kx - shift) & (nx - 1))), e);
+        if (pairs) {
+            // pixel pairs (kx, kx + 1), kx even: the low run [0, kh) and the high run from
+            // nx - kh, whose first column lies outside the kept band and is written as zero
+            const float4 *t4 = reinterpret_cast<const float4 *>(t0);
+            float4 *w4 = reinterpret_cast<float4 *>(w);
+            for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+                const int kx = kx_half > 0 && 2 * j >= kx_half ? nx - 2 * kx_half + 2 * j : 2 * j;
+                const float4 v = __ldg(t4 + (((kx - shift) & (nx - 1)) >> 1));  // shift even: an aligned pair
+                float2 lo = cmul(make_float2(v.x, v.y), e), hi = cmul(make_float2(v.z, v.w), e);
+                if (kx_half > 0 && kx == nx - kx_half) lo = make_float2(0.f, 0.f);
+                w4[kx >> 1] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            }
+        } else {
+            for (int j = threadIdx.x; j < kept; j += blockDim.x) {
+                const int kx = kx_half > 0 && j >= kx_half ? nx - 2 * kx_half + 1 + j : j;
+                w[kx] = cmul(__ldg(t0 + ((kx - shift) & (nx - 1))), e);
+            }
         }
     }
 }
