@@ -332,8 +332,9 @@ typedef struct prism_tune_entry {
 int prism_plan_autotune(prism_plan *plan);
 /* prism_plan_autotune with flags: PRISM_AUTOTUNE_FFT_RADIX also times the FFT radix variants
  * (prism_tune_shape_fft_variant) and may keep one, whose results agree with the default's to
- * rounding but not bit for bit; without it (prism_plan_autotune) the tuner keeps the default radix
- * and every result stays bitwise that of the untuned plan.  INVALID for unknown flags. */
+ * rounding but not bit for bit; without it (prism_plan_autotune) the tuner keeps the radix of the
+ * default launchers at the plan's N (both transforms radix-4 first at N = 2048, the default split
+ * elsewhere) and every result stays bitwise that of the untuned plan.  INVALID for unknown flags. */
 #define PRISM_AUTOTUNE_FFT_RADIX 1
 int prism_plan_autotune_flags(prism_plan *plan, int flags);
 /* The scan's contraction tile shape (the scan term of the Calculation Time section's cost model):

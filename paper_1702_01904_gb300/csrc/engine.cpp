@@ -1609,7 +1609,8 @@ extern "C" int prism_plan_autotune_flags(prism_plan *P, int flags) {
         double best_ms = 0;
         for (int v = 0; v < tune_shapes(kind) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
             if (!tune_shape_valid(kind, n, v) || (tune_shape_needs_map(kind, v) && !P->wave_map_ok) ||
-                (P->shared_sms && tune_shape_fills_sm(kind, v)) || (!radix && tune_shape_fft_variant(kind, v) != 0))
+                (P->shared_sms && tune_shape_fills_sm(kind, v)) ||
+                (!radix && tune_shape_fft_variant(kind, v) != tune_default_fft_variant(n)))
                 continue;
             RowArgs ra = row_args(P);
             ra.trans = P->t;

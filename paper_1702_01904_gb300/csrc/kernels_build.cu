@@ -106,10 +106,11 @@ cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigm
 template <int NX>
 static cudaError_t row_dispatch(RowMode mode, const RowArgs &a, cudaStream_t s) {
     if (a.n_rows <= 0) return cudaSuccess;
+    constexpr int T = row_default_threads<NX>(), RV = default_fft_variant(NX);
     switch (mode) {
-        case ROW_STD: return row_go<NX, ROW_STD>(a, s);
-        case ROW_PLANE: return row_go<NX, ROW_PLANE>(a, s);
-        case ROW_OUT: return row_go<NX, ROW_OUT>(a, s);
+        case ROW_STD: return row_go<NX, ROW_STD, T, false, false, RV>(a, s);
+        case ROW_PLANE: return row_go<NX, ROW_PLANE, T, false, false, RV>(a, s);
+        case ROW_OUT: return row_go<NX, ROW_OUT, T, false, false, RV>(a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -131,10 +132,12 @@ cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s) {
 template <int NY>
 static cudaError_t col_dispatch(ColMode mode, const ColArgs &a, cudaStream_t s) {
     if (a.batch <= 0) return cudaSuccess;
+    constexpr int W = col_default_w<NY>(), RV = default_fft_variant(NY);
+    constexpr bool STG = col_default_stg<NY>();
     switch (mode) {
-        case COL_STD: return col_go<NY, COL_STD>(a, s);
-        case COL_PROBE: return col_go<NY, COL_PROBE>(a, s);
-        case COL_DETECT: return col_go<NY, COL_DETECT>(a, s);
+        case COL_STD: return col_go<NY, COL_STD, W, STG, 0, false, RV>(a, s);
+        case COL_PROBE: return col_go<NY, COL_PROBE, W, STG, 0, false, RV>(a, s);
+        case COL_DETECT: return col_go<NY, COL_DETECT, W, STG, 0, false, RV>(a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -29,7 +29,8 @@ const char *ROW_NAMES[N_ROW] = {"128 thr",
                                 "384 thr, TMA, radix-4 first: forward",
                                 "384 thr, TMA, radix-4 first: inverse",
                                 "384 thr, TMA, radix-4 first: both",
-                                "128 thr, radix-4 first: both"};
+                                "128 thr, radix-4 first: both",
+                                "128 thr, staged, radix-4 first: both"};
 const char *COL_NAMES[N_COL] = {"W4, staged",
                                 "W8, staged",
                                 "W16, staged",
@@ -41,7 +42,9 @@ const char *COL_NAMES[N_COL] = {"W4, staged",
                                 "W4, TMA, 3/SM, radix-4 first: forward",
                                 "W4, TMA, 3/SM, radix-4 first: inverse",
                                 "W4, TMA, 3/SM, radix-4 first: both",
-                                "W8, staged, radix-4 first: both"};
+                                "W8, staged, radix-4 first: both",
+                                "W8, radix-4 first: both",
+                                "W4, staged, radix-4 first: both"};
 static_assert(sizeof(ROW_NAMES) / sizeof(ROW_NAMES[0]) == N_ROW && sizeof(COL_NAMES) / sizeof(COL_NAMES[0]) == N_COL, "one name per shape");
 
 }  // namespace
@@ -55,18 +58,23 @@ const char *tune_shape_name(int kind, int v) {
 }
 
 int tune_default_shape(int kind, int n) {
+    const int rv = default_fft_variant(n);
     if (kind == 0) {
         const int thr = n >= 512 ? 128 : 256;  // row_default_threads, unstaged
         for (int v = 0; v < N_ROW; ++v)
-            if (ROW_SHAPES[v].a == thr && !ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma && ROW_SHAPES[v].rv == 0) return v;
+            if (ROW_SHAPES[v].a == thr && !ROW_SHAPES[v].stg && !ROW_SHAPES[v].tma && ROW_SHAPES[v].rv == rv) return v;
     } else if (kind == 1) {
-        const int w = n >= 2048 ? 4 : n >= 1024 ? 8 : 16;  // col_default_w, staged
+        const int w = n >= 1024 ? 8 : 16;  // col_default_w
+        const bool stg = n < 2048;         // col_default_stg
         for (int v = 0; v < N_COL; ++v)
-            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg && COL_SHAPES[v].mb == 0 && !COL_SHAPES[v].tma && COL_SHAPES[v].rv == 0)
+            if (COL_SHAPES[v].a == w && COL_SHAPES[v].stg == stg && COL_SHAPES[v].mb == 0 && !COL_SHAPES[v].tma &&
+                COL_SHAPES[v].rv == rv)
                 return v;
     }
     return -1;
 }
+
+int tune_default_fft_variant(int n) { return default_fft_variant(n); }
 
 int tune_shape_fft_variant(int kind, int v) {
     if (kind == 0 && v >= 0 && v < N_ROW) return ROW_SHAPES[v].rv;

@@ -195,6 +195,7 @@ int tune_default_shape(int kind, int n);
 bool tune_shape_valid(int kind, int n, int v);
 bool tune_shape_needs_map(int kind, int v);  // the shape stages through TMA (ColArgs::wave_map)
 int tune_shape_fft_variant(int kind, int v);  // its FFT radix variant (DftSplit), -1 if unknown
+int tune_default_fft_variant(int n);          // the radix variant of the default launchers at N
 int tune_col_tma_shape(int w);                // the TMA-staged column shape of w columns per CTA, or -1
 int tune_row_find(int thr, bool stg, bool tma);  // the row shape of thr threads per CTA and that staging, or -1
 bool tune_shape_fills_sm(int kind, int v);    // 3 or more CTAs per SM, each with a third of its resources

@@ -18,10 +18,12 @@ struct Shape {
 constexpr Shape ROW_SHAPES[] = {{128, false, 0, false, 0}, {256, false, 0, false, 0}, {128, true, 0, false, 0},
                                 {256, true, 0, false, 0},  {128, false, 0, true, 0},  {256, false, 0, true, 0},
                                 {384, true, 0, false, 0},  {384, false, 0, true, 0},  {384, false, 0, true, 1},
-                                {384, false, 0, true, 2},  {384, false, 0, true, 3},  {128, false, 0, false, 3}};
+                                {384, false, 0, true, 2},  {384, false, 0, true, 3},  {128, false, 0, false, 3},
+                                {128, true, 0, false, 3}};
 constexpr Shape COL_SHAPES[] = {{4, true, 0, false, 0},  {8, true, 0, false, 0}, {16, true, 0, false, 0}, {4, false, 3, true, 0},
                                 {8, false, 0, false, 0}, {8, false, 0, true, 0}, {8, false, 2, false, 0}, {4, true, 3, false, 0},
-                                {4, false, 3, true, 1},  {4, false, 3, true, 2}, {4, false, 3, true, 3},  {8, true, 0, false, 3}};
+                                {4, false, 3, true, 1},  {4, false, 3, true, 2}, {4, false, 3, true, 3},  {8, true, 0, false, 3},
+                                {8, false, 0, false, 3}, {4, true, 0, false, 3}};
 constexpr int N_ROW = sizeof(ROW_SHAPES) / sizeof(Shape);
 constexpr int N_COL = sizeof(COL_SHAPES) / sizeof(Shape);
 

@@ -128,8 +128,9 @@ class PrismSimulation:
             out[label] = {"chosen": name(e.chosen), "default": name(e.default_shape),
                           "ms": {P.prism_tune_shape_name(kind, v): e.ms[v] for v in range(e.n_shapes) if e.ms[v] >= 0}}
             if kind != P.PRISM_TUNE_SCAN:
-                # FFT radix variant of the shape in use (the default launcher's is 0)
-                out[label]["fft_variant"] = max(P.prism_tune_shape_fft_variant(kind, e.chosen), 0)
+                # FFT radix variant of the shape in use (the default launcher: the default shape's)
+                v = e.chosen if e.chosen >= 0 else e.default_shape
+                out[label]["fft_variant"] = max(P.prism_tune_shape_fft_variant(kind, v), 0)
         return out
 
     # -- introspection
