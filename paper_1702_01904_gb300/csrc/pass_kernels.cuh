@@ -90,7 +90,12 @@ struct RowCfg {
     static constexpr int EXI = FS::N2 * (FS::N1 + 1);
     static constexpr int EX = EXF > EXI ? EXF : EXI;
     static constexpr int SLOT_F2 = (TMA ? NX / 2 : STAGE ? NX : 0) + EX;  // staging row + exchange, float2
-    static constexpr size_t SMEM = (size_t)(2 * NX + SLOTS * SLOT_F2) * sizeof(float2);
+    // at N = 2048 the two stage-twiddle tables (32 KB) would hold the CTAs to 2 per SM: there they are
+    // read through L1 (read-only path), interleaved with the exchange stores, for 3 CTAs per SM
+    static constexpr bool L1TW = NX >= 2048;
+    static constexpr int TW_MODE = L1TW ? TW_GLOBAL : TW_SMEM;
+    static constexpr int TWF2 = L1TW ? 0 : 2 * NX;  // float2 of twiddles in shared memory
+    static constexpr size_t SMEM = (size_t)(TWF2 + SLOTS * SLOT_F2) * sizeof(float2);
 };
 
 // bulk-staged rows give up after this many SM cycles (about a second) and report it
@@ -117,14 +122,20 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
         if (t == 0) tc::mbar_init(&rbar[slot], 1);
         tc::fence_mbar_init();
     }
-    // FFT stage twiddles (forward, inverse) in shared memory, then one region per slot
-    float2 *twf = smem, *twi = smem + NX;
-    for (int i = threadIdx.x; i < NX; i += C::THREADS) {
-        twf[i] = a.tw_fwd[i];
-        twi[i] = a.tw_inv[i];
+    // FFT stage twiddles (forward, inverse) in shared memory (or read through L1), then one region
+    // per slot
+    const float2 *twf = a.tw_fwd, *twi = a.tw_inv;
+    if constexpr (!C::L1TW) {
+        float2 *tf = smem, *ti = smem + NX;
+        for (int i = threadIdx.x; i < NX; i += C::THREADS) {
+            tf[i] = a.tw_fwd[i];
+            ti[i] = a.tw_inv[i];
+        }
+        __syncthreads();
+        twf = tf;
+        twi = ti;
     }
-    __syncthreads();
-    float2 *stg = smem + 2 * NX + slot * C::SLOT_F2;
+    float2 *stg = smem + C::TWF2 + slot * C::SLOT_F2;
     float2 *exbuf = stg + (C::TMA ? NX / 2 : C::STAGE ? NX : 0);
     WarpExchange<FS::N1, FS::N2, T> exF{exbuf};
     WarpExchange<FS::N2, FS::N1, T> exI{exbuf};
@@ -260,16 +271,16 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                     float2 tv[E];
 #pragma unroll
                     for (int r = 0; r < E; ++r) tv[r] = __ldcg(tp + Inv::out_elem(r, t));
-                    Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), C::TW_MODE, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], tv[r]);
                 } else {
-                    Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
+                    Inv::template run<decltype(exI), C::TW_MODE, ZIN>(v, t, twi, a.tw, exI);
 #pragma unroll
                     for (int r = 0; r < E; ++r) v[r] = cmul(v[r], __ldcg(tp + Inv::out_elem(r, t)));
                 }
             } else {
-                Inv::template run<decltype(exI), TW_SMEM, ZIN>(v, t, twi, a.tw, exI);
+                Inv::template run<decltype(exI), C::TW_MODE, ZIN>(v, t, twi, a.tw, exI);
             }
         }
         if constexpr (MODE == ROW_OUT) {
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(THR) k_row(const __grid_constant__ RowArgs a) 
                 }
             }
         } else {
-            Fwd::run(v, t, twf, a.tw, exF);
+            Fwd::template run<decltype(exF), C::TW_MODE>(v, t, twf, a.tw, exF);
             if (valid) {
                 float2 *w = a.wave + ((size_t)b * a.ny + y) * NX;
                 static_for<E>([&](auto rc) {
