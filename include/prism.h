@@ -338,7 +338,7 @@ int prism_plan_autotune(prism_plan *plan);
 #define PRISM_AUTOTUNE_FFT_RADIX 1
 int prism_plan_autotune_flags(prism_plan *plan, int flags);
 /* The scan's contraction tile shape (the scan term of the Calculation Time section's cost model):
- * raster blocks of 4 x 8, 8 x 4 or 2 x 16 probes and beam rings of 2 x 32 or 3 x 16, compiled for
+ * raster blocks of 4 x 8, 8 x 4 or 2 x 16 probes and beam rings of 2 x 33 (default), 2 x 32 or 3 x 16, compiled for
  * the FP32 GEMM scan with square windows of 16, 32 or 64 pixels.  Runs the given scan once per
  * shape (a warm-up and two timed launches, CUDA events on the plan's stream), keeps the fastest
  * for the plan's later scans (prism_plan_tune_result with PRISM_TUNE_SCAN) and leaves the detector

@@ -12,8 +12,8 @@ namespace prism {
 
 namespace {
 
-const char *GEMM_NAMES[N_GEMM_SHAPES] = {"4x8 blocks, 2 x 32 beams", "8x4 blocks, 2 x 32 beams", "2x16 blocks, 2 x 32 beams",
-                                         "4x8 blocks, 3 x 16 beams", "8x4 blocks, 3 x 16 beams"};
+const char *GEMM_NAMES[N_GEMM_SHAPES] = {"4x8 blocks, 2 x 33 beams", "8x4 blocks, 2 x 32 beams", "2x16 blocks, 2 x 32 beams",
+                                         "4x8 blocks, 3 x 16 beams", "8x4 blocks, 3 x 16 beams", "4x8 blocks, 2 x 32 beams"};
 
 template <int NW>
 int grid_nw(int shape, int n_beams, int px, int py) {
@@ -22,6 +22,7 @@ int grid_nw(int shape, int n_beams, int px, int py) {
         case 2: return gemm_grid<NW, NW, 2>(n_beams, px, py);
         case 3: return gemm_grid<NW, NW, 3>(n_beams, px, py);
         case 4: return gemm_grid<NW, NW, 4>(n_beams, px, py);
+        case 5: return gemm_grid<NW, NW, 5>(n_beams, px, py);
     }
     return 0;
 }
@@ -33,6 +34,7 @@ cudaError_t launch_nw(int shape, int grid, const ScanArgs &a, cudaStream_t s) {
         case 2: return gemm_launch<NW, NW, 2>(grid, a, s);
         case 3: return gemm_launch<NW, NW, 3>(grid, a, s);
         case 4: return gemm_launch<NW, NW, 4>(grid, a, s);
+        case 5: return gemm_launch<NW, NW, 5>(grid, a, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -165,7 +165,7 @@ def test_autotuned_batch_equals_untuned(fft_radix):
                                                 (512, 32.0, 4, 23, 17, 0.25)])
 def test_every_scan_contraction_shape_is_bitwise_identical(n, cell, f, px, py, step):
     # FP32 GEMM scan with 32-, 16- and 64-pixel windows: raster blocks 4 x 8, 8 x 4, 2 x 16 and beam
-    # rings 2 x 32, 3 x 16 sum every window pixel over the beams in the same order; ragged rasters
+    # rings 2 x 32, 3 x 16, 2 x 33 sum every window pixel over the beams in the same order; ragged rasters
     # (px, py not multiples of the block sides) cover partial blocks and the split last round
     grid = P.make_grid(n, n, 3, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0)
     V = rand_v(3, n, 21)
@@ -178,7 +178,7 @@ def test_every_scan_contraction_shape_is_bitwise_identical(n, cell, f, px, py, s
     assert nw == n // 2 // f
     ref = sim.scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy()
     n_shapes = P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes
-    assert n_shapes == 5
+    assert n_shapes == 6
     for v in range(n_shapes):
         sim.set_shape(P.PRISM_TUNE_SCAN, v)
         got = sim.scan(probe, x0, y0, DET, px=px, py=py).cpu().numpy()
@@ -203,6 +203,8 @@ def test_scan_shape_limits():
     assert P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes == 0
     sim.close()
     sim = PrismSimulation(P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0))
+    n = P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes
+    sim.set_shape(P.PRISM_TUNE_SCAN, n - 1)
     with pytest.raises(P.PrismError):
-        sim.set_shape(P.PRISM_TUNE_SCAN, 5)
+        sim.set_shape(P.PRISM_TUNE_SCAN, n)
     sim.close()
