@@ -1048,7 +1048,9 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
             *grid = 0;
             return PRISM_OK;
         }
-        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_gemm_win_bytes(P->nw, P->nwy, sh, *grid, a.scan_px, a.scan_py));
+        const size_t wb = scan_gemm_win_bytes(P->nw, P->nwy, sh, *grid, a.scan_px, a.scan_py);
+        if (!wb) return fail(PRISM_ERR_CUDA, "FP32 scan: no window scratch size for contraction shape " + std::to_string(sh));
+        int rc = grow(P->arena, (void **)&P->win, &P->win_cap, wb);
         if (rc) return rc;
         return split_counters(P, a, *grid);
     }

@@ -349,14 +349,7 @@ cudaError_t launch_scan_gemm(int nwx, int nwy, int shape, int grid, const ScanAr
 }
 
 size_t scan_gemm_win_bytes(int nwx, int nwy, int shape, int grid, int scan_px, int scan_py) {
-    switch (shape) {
-        case 0: return gemm_win_bytes<0>(nwx, nwy, grid, scan_px, scan_py);
-        case 1: return gemm_win_bytes<1>(nwx, nwy, grid, scan_px, scan_py);
-        case 2: return gemm_win_bytes<2>(nwx, nwy, grid, scan_px, scan_py);
-        case 3: return gemm_win_bytes<3>(nwx, nwy, grid, scan_px, scan_py);
-        case 4: return gemm_win_bytes<4>(nwx, nwy, grid, scan_px, scan_py);
-    }
-    return 0;
+    return gemm_win_bytes(shape, nwx, nwy, grid, scan_px, scan_py);
 }
 
 int scan_gemm_shapes() { return N_GEMM_SHAPES; }

@@ -302,15 +302,14 @@ static cudaError_t gemm_launch(int grid, const ScanArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// window scratch of a launch: one slot per block split over idle CTAs, one per CTA when some block
-// runs whole
-template <int SH>
-static size_t gemm_win_bytes(int nwx, int nwy, int grid, int scan_px, int scan_py) {
-    using C = GemmCfg<16, 16, SH>;
-    if (grid <= 0 || scan_px <= 0 || scan_py <= 0) return 0;
-    const long long groups = (long long)((scan_px + C::GX - 1) / C::GX) * ((scan_py + C::GY - 1) / C::GY);
+// window scratch of a launch of contraction shape `shape`: one slot of 32 windows per block split
+// over idle CTAs, one per CTA when some block runs whole (0 for an unknown shape or no work)
+static inline size_t gemm_win_bytes(int shape, int nwx, int nwy, int grid, int scan_px, int scan_py) {
+    if (shape < 0 || shape >= N_GEMM_SHAPES || grid <= 0 || scan_px <= 0 || scan_py <= 0) return 0;
+    const int gx = GEMM_SHAPES[shape].gx, gy = GEMM_SHAPES[shape].gy;
+    const long long groups = (long long)((scan_px + gx - 1) / gx) * ((scan_py + gy - 1) / gy);
     const long long tail = groups % grid, slots = tail + (groups > tail ? grid : 0);
-    return (size_t)slots * C::G * nwx * nwy * sizeof(float2);
+    return (size_t)slots * (gx * gy) * nwx * nwy * sizeof(float2);
 }
 
 }  // namespace prism

@@ -193,6 +193,36 @@ def test_every_scan_contraction_shape_is_bitwise_identical(n, cell, f, px, py, s
     sim.close()
 
 
+def test_every_scan_contraction_shape_sizes_its_own_scratch():
+    # a plan whose scans first ran small, pinned to each contraction shape in turn, then scanning a
+    # larger raster: the window scratch grows for that shape's blocks (the result equals the
+    # default shape's, bit for bit)
+    n, cell, f = 256, 16.0, 4
+    grid = P.make_grid(n, n, 2, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0)
+    V = rand_v(2, n, 22)
+    X, Y = np.meshgrid(0.3 + 0.35 * np.arange(21), 0.4 + 0.35 * np.arange(19))
+    x0, y0 = X.ravel(), Y.ravel()
+    probe = P.make_probe(20.0)
+    ref = None
+    n_shapes = None
+    for v in range(16):
+        sim = PrismSimulation(grid)
+        if n_shapes is None:
+            n_shapes = P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes
+        if v >= n_shapes:
+            sim.close()
+            break
+        sim.build(V)
+        sim.scan(probe, x0[:2], y0[:2], DET, px=2, py=1)  # a small first scan: a small scratch
+        sim.set_shape(P.PRISM_TUNE_SCAN, v)
+        out = sim.scan(probe, x0, y0, DET, px=21, py=19).cpu().numpy()
+        sim.close()
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), P.prism_tune_shape_name(P.PRISM_TUNE_SCAN, v)
+    assert n_shapes == 6
+
+
 def test_scan_shape_limits():
     # 16-bit plans have one (tensor-core) scan shape; shapes past the list are refused
     grid = P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0, precision=P.PRISM_PRECISION_FP16)
