@@ -8,9 +8,9 @@
 //   4. 2-D FFT of the window in shared memory (row then column two-level FFTs);
 //   5. |Psi|^2 and the annular bins, fixed summation order, FP64 scale.
 // Three kernels: k_scan_gemm (4 x 8 raster blocks, the beam sum as a register-tiled complex GEMM on
-// the union tile of their windows; the default), k_scan_grouped (4 consecutive probes, used when the
-// GEMM's coefficient block does not fit shared memory or for 8-pixel windows) and k_scan (one probe
-// per CTA, for 128-pixel windows and very large beam sets).
+// the union tile of their windows; the default for windows of 16 to 128 pixels), k_scan_grouped (4
+// consecutive probes, used when the GEMM's coefficient block does not fit shared memory or for
+// 8-pixel windows) and k_scan (one probe per CTA, for very large beam sets).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -165,7 +165,7 @@ static cudaError_t scan_dispatch(const ScanArgs &a, cudaStream_t s) {
     const int n = a.n_probes - a.probe0;
     if (n <= 0) return cudaSuccess;
     const size_t smem = C::SMEM_FIXED + (size_t)a.n_beams * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_scan<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_scan<NW>);
     if (e != cudaSuccess) return e;
     k_scan<NW><<<n, C::BLOCK, smem, s>>>(a);
     return cudaGetLastError();
@@ -314,7 +314,7 @@ static cudaError_t scan_grouped_dispatch(const ScanArgs &a, cudaStream_t s) {
     const int n = a.n_probes - a.probe0;
     if (n <= 0) return cudaSuccess;
     const size_t smem = C::SMEM_FIXED + (size_t)C::G * a.n_beams * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_grouped<NWX, NWY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_scan_grouped<NWX, NWY>);
     if (e != cudaSuccess) return e;
     k_scan_grouped<NWX, NWY><<<(n + C::G - 1) / C::G, C::BLOCK, smem, s>>>(a);
     return cudaGetLastError();
@@ -325,8 +325,10 @@ static bool grouped_fits(int n_beams) {
     return GroupCfg<NWX, NWY>::SMEM_FIXED + (size_t)GroupCfg<NWX, NWY>::G * n_beams * sizeof(float2) <= 227 * 1024;
 }
 
+// (128-pixel windows: one CTA per SM, the coefficients of up to about 630 beams in shared memory;
+// larger beam sets go to k_scan)
 #define PRISM_GEMM_SIDES(X)                                                                                                  \
-    X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64)
+    X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64) X(128, 128)
 
 // shape 0 here; the others (square windows) in kernels_tune_scan.cu
 int scan_gemm_grid(int nwx, int nwy, int shape, int n_beams, int scan_px, int scan_py) {

@@ -559,7 +559,7 @@ static int tc_grid(int kp, int scan_px, int scan_py) {
     using C = TcCfg<NW, MODE == TC_SPLIT>;
     const size_t smem = C::smem(kp);
     if (smem > 227 * 1024) return 0;
-    if (cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (allow_max_dynamic_smem(k_scan_tc<NW, MODE>) != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
         cudaSuccess)
         return 0;
@@ -616,7 +616,7 @@ template <int NW, int MODE>
 static cudaError_t tc_launch(int grid, const ScanArgs &a, cudaStream_t s) {
     using C = TcCfg<NW, MODE == TC_SPLIT>;
     const size_t smem = C::smem(a.kp);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_scan_tc<NW, MODE>);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_scan_tc<NW, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;

@@ -9,6 +9,26 @@
 
 namespace prism {
 
+// The dynamic shared memory limit of a scan kernel whose launches differ in size (with the beam
+// count): the device's opt-in maximum less the kernel's static shared memory.  The attribute
+// belongs to the kernel, not to a launch, so plans scanning from several host threads set this same
+// value every time instead of their own sizes, which a concurrent smaller setting would undercut
+// between another thread's setting and its launch.
+template <class K>
+static cudaError_t allow_max_dynamic_smem(K kernel) {
+    static const int optin = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 0;
+        return v;
+    }();
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (optin <= (int)fa.sharedSizeBytes) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
@@ -214,7 +234,9 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
         }
     }
     __syncthreads();
-    constexpr int LNW = NWX == 8 ? 3 : NWX == 16 ? 4 : NWX == 32 ? 5 : 6;  // u = ky * NWX + kx
+    // u = ky * NWX + kx: the row is u >> LNW, LNW = log2(NWX)
+    constexpr int LNW = NWX == 8 ? 3 : NWX == 16 ? 4 : NWX == 32 ? 5 : NWX == 64 ? 6 : NWX == 128 ? 7 : -1;
+    static_assert(LNW > 0 && (1 << LNW) == NWX, "window widths 8 ... 128");
     constexpr int NP = NWX * NWY;
     if (a.cbed) {
         const float fnorm = (float)a.inv_norm;

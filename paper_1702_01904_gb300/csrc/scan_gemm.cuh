@@ -59,7 +59,7 @@ struct GemmCfg {
     static constexpr int RING = STAGES * KB * MT;    // float2
     static constexpr int PW = NWX + 4;                        // window row pitch (bank spread)
     static constexpr int NWM = NWX > NWY ? NWX : NWY;
-    static constexpr int EW = NWM >= 64 ? 2 : NWM == 32 ? 8 : 16;  // windows per epilogue pass
+    static constexpr int EW = NWM >= 128 ? 1 : NWM >= 64 ? 2 : NWM == 32 ? 8 : 16;  // windows per epilogue pass
     static constexpr int EX = ExSize<NWX, NWY, BLOCK>::value;
     static constexpr size_t EPI = (size_t)(EW * NWY * PW + EX) * sizeof(float2);
     static constexpr int META = 256;
@@ -274,7 +274,7 @@ static int gemm_grid(int n_beams, int scan_px, int scan_py) {
     using C = GemmCfg<NWX, NWY, SH>;
     const size_t smem = C::smem(n_beams);
     if (smem > 227 * 1024 || scan_px <= 0 || scan_py <= 0) return 0;
-    if (cudaFuncSetAttribute(k_scan_gemm<NWX, NWY, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (allow_max_dynamic_smem(k_scan_gemm<NWX, NWY, SH>) != cudaSuccess)
         return 0;
     if (cudaFuncSetAttribute(k_scan_gemm<NWX, NWY, SH>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
         cudaSuccess)
@@ -294,7 +294,7 @@ static cudaError_t gemm_launch(int grid, const ScanArgs &a, cudaStream_t s) {
     // the ring's 16-byte copies read pixel pairs of the S-matrix
     if (reinterpret_cast<uintptr_t>(a.S) & 15) return cudaErrorMisalignedAddress;
     const size_t smem = C::smem(a.n_beams);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_gemm<NWX, NWY, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_scan_gemm<NWX, NWY, SH>);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_scan_gemm<NWX, NWY, SH>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
