@@ -585,6 +585,8 @@ def main():
                     continue
                 s2 = PrismSimulation(PR.grid_from_workload(w, precision=PREC[name]), 0, stream)
                 o2 = torch.empty_like(out)
+                if not args.no_autotune:
+                    s2.autotune(fft_radix=True)
 
                 def step2():
                     s2.build(V)
@@ -592,6 +594,11 @@ def main():
 
                 for _ in range(2):
                     step2()
+                tune2 = None
+                if not args.no_autotune:
+                    # the scan's shape: contraction tiles (FP32) or the tensor-core ring (16-bit)
+                    s2.autotune_scan(probe, x0, y0, det, out=o2, px=w.scan_px, py=w.scan_py)
+                    tune2 = {k: v["chosen"] for k, v in s2.tune_result().items()}
                 stream.synchronize()
                 s2.reset_stats()
                 s2.set_profiling(True)
@@ -615,7 +622,7 @@ def main():
                 scan2 = st2["scan"][1] / max(st2["scan"][0], 1)
                 prec_leg[name] = {"value": P / (t2 / 1000.0), "unit": UNIT, "ms_per_step": t2, "scan_ms": scan2,
                                   "build_ms": t2 - scan2, "smatrix_bytes": PR.prism_plan_smatrix_bytes(s2.plan),
-                                  "deviation_from_headline": dev}
+                                  "deviation_from_headline": dev, "autotune": tune2}
                 s2.close()
         sim.close()
 

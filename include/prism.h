@@ -322,6 +322,8 @@ void prism_server_destroy(prism_server *server);
 #define PRISM_TUNE_ROW 0
 #define PRISM_TUNE_COL 1
 #define PRISM_TUNE_SCAN 2  /* contraction tile shape of the FP32 GEMM scan (prism_plan_autotune_scan) */
+#define PRISM_TUNE_SCAN_TC 3  /* ring shape of the tensor-core scan of a 16-bit plan: stages x K values of
+                                 its A operand (3 x 96 default, 2 x 128, 4 x 64; split mode 2 x 32 only) */
 #define PRISM_TUNE_MAX_SHAPES 16
 typedef struct prism_tune_entry {
     int n_shapes;                     /* shapes listed for the pass                              */
@@ -343,7 +345,9 @@ int prism_plan_autotune_flags(prism_plan *plan, int flags);
  * shape (a warm-up and two timed launches, CUDA events on the plan's stream), keeps the fastest
  * for the plan's later scans (prism_plan_tune_result with PRISM_TUNE_SCAN) and leaves the detector
  * stack in out_dev: every shape sums each pixel over the beams in the same order, so all give
- * bitwise the same stack.  Other plans (16-bit modes, other windows) just run the scan.  Arguments
+ * bitwise the same stack.  A 16-bit plan times the ring shapes of its tensor-core scan the same way
+ * (PRISM_TUNE_SCAN_TC; the K = 16 MMAs of a pixel tile go in the same order in every shape, so the
+ * stacks are bitwise equal too).  Other plans (other windows) just run the scan.  Arguments
  * and errors as prism_scan_run; synchronous.  No counterpart in the paper. */
 int prism_plan_autotune_scan(prism_plan *plan, const prism_probe *probe, const prism_scan *scan,
                              const prism_detector *det, float *out_dev);
@@ -357,7 +361,7 @@ int prism_tune_shape_fft_variant(int kind, int shape);
 /* Pin the launch shape of one pass (or the scan's contraction shape, PRISM_TUNE_SCAN) for the
  * plan's later builds (scans) without timing: `shape` indexes the kind's list
  * (prism_tune_shape_name), -1 restores the default.  PRISM_ERR_INVALID for a NULL plan or a kind
- * outside {PRISM_TUNE_ROW, PRISM_TUNE_COL, PRISM_TUNE_SCAN}; PRISM_ERR_UNSUPPORTED for a shape not
+ * outside {PRISM_TUNE_ROW, PRISM_TUNE_COL, PRISM_TUNE_SCAN, PRISM_TUNE_SCAN_TC}; PRISM_ERR_UNSUPPORTED for a shape not
  * compiled for the plan's N (window), or one that stages through TMA when the plan holds no tensor
  * map of its wave scratch.  Shapes of the default's FFT radix variant compute bitwise the same
  * result; the other variant agrees to rounding. */

@@ -22,10 +22,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh",
-                                           "tune_shapes.cuh", "tune_pass.cuh", "scan_gemm.cuh")] + \
+                                           "tune_shapes.cuh", "tune_pass.cuh", "scan_gemm.cuh", "scan_tc.cuh")] + \
     [os.path.join(INCLUDE, "prism.h")]
 CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_256.cu", "kernels_tune_512.cu", "kernels_tune_1024.cu",
-              "kernels_tune_2048.cu", "kernels_scan.cu", "kernels_tune_scan.cu", "kernels_tc.cu", "noalloc.cu"]
+              "kernels_tune_2048.cu", "kernels_scan.cu", "kernels_tune_scan.cu", "kernels_tc.cu", "kernels_tc_tune.cu",
+              "noalloc.cu"]
 HOST_UNITS = ["engine.cpp", "server.cpp"]
 
 

@@ -401,6 +401,9 @@ struct prism_plan {
     int scan_shape = 0;            // contraction tile shape of the FP32 GEMM scan (0: default)
     double scan_ms[PRISM_TUNE_MAX_SHAPES];
     bool scan_tuned = false;
+    int tc_shape = 0;              // ring shape of the tensor-core scan (16-bit modes; 0: default)
+    double tc_ms[PRISM_TUNE_MAX_SHAPES];
+    bool tc_tuned = false;
     float2 *prop_x = nullptr, *prop_y = nullptr;
     int *aa_kmax = nullptr;
     float2 *twr_f = nullptr, *twr_i = nullptr, *twc_f = nullptr, *twc_i = nullptr, *tww_f = nullptr, *tww_fy = nullptr;
@@ -606,7 +609,7 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
         return fail(PRISM_ERR_INVALID, "empty beam set");
     }
     P->kp = 2 * ((P->nbeams + 7) / 8 * 8);
-    if (half ? scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), 1, 1) <= 0
+    if (half ? scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), 0, 1, 1) <= 0
              : nwx == nwy ? scan_smem_bytes(P->nw, P->nbeams) > 227 * 1024 : !scan_rect_supported(nwx, nwy, P->nbeams)) {
         delete P;
         return fail(PRISM_ERR_UNSUPPORTED, "too many beams for the scan kernel's shared memory");
@@ -1039,6 +1042,11 @@ static int gemm_shape(const prism_plan *P) {
     return P->scan_shape > 0 && scan_gemm_shape_valid(P->nw, P->nwy, P->scan_shape) ? P->scan_shape : 0;
 }
 
+// the tensor-core scan's ring shape in use: the tuned or pinned one, else the default
+static int tc_shape(const prism_plan *P) {
+    return P->tc_shape > 0 && P->tc_shape < scan_tc_shapes(tc_mode(P->prec)) ? P->tc_shape : 0;
+}
+
 static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
     *grid = 0;
     if (P->prec == PRISM_PRECISION_FP32) {
@@ -1054,7 +1062,7 @@ static int scan_setup(prism_plan *P, ScanArgs &a, int *grid) {
         if (rc) return rc;
         return split_counters(P, a, *grid);
     }
-    *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), a.scan_px, a.scan_py);
+    *grid = scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), tc_shape(P), a.scan_px, a.scan_py);
     if (*grid <= 0) return fail(PRISM_ERR_CUDA, "tensor-core scan: no resident launch configuration");
     int rc = grow(P->arena, (void **)&P->win, &P->win_cap, scan_tc_win_bytes(P->nw, *grid, a.scan_px, a.scan_py));
     if (rc) return rc;
@@ -1067,7 +1075,7 @@ static int scan_go(prism_plan *P, const ScanArgs &a, int grid) {
             return grid > 0 ? launch_scan_gemm(P->nw, P->nwy, gemm_shape(P), grid, a, P->stream)
                             : launch_scan_rect(P->nw, P->nwy, a, P->stream);
         });
-    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), grid, a, P->stream); });
+    return plan_launch(P, PRISM_K_SCAN, [&] { return launch_scan_tc(P->nw, tc_mode(P->prec), tc_shape(P), grid, a, P->stream); });
 }
 
 static int scan_launch(prism_plan *P, ScanArgs &a) {
@@ -1570,7 +1578,15 @@ extern "C" int prism_plan_set_tune_shape(prism_plan *P, int kind, int shape) {
         P->scan_shape = shape < 0 ? 0 : shape;
         return PRISM_OK;
     }
-    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "kind must be PRISM_TUNE_ROW, PRISM_TUNE_COL or PRISM_TUNE_SCAN");
+    if (kind == PRISM_TUNE_SCAN_TC) {
+        if (shape >= 0 && (P->prec == PRISM_PRECISION_FP32 || shape >= scan_tc_shapes(tc_mode(P->prec))))
+            return fail(PRISM_ERR_UNSUPPORTED, std::string("ring shape ") + std::to_string(shape) +
+                                                   " is not compiled for this plan's scan (tensor-core scan of a 16-bit plan; split mode has one)");
+        P->tc_shape = shape < 0 ? 0 : shape;
+        return PRISM_OK;
+    }
+    if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL)
+        return fail(PRISM_ERR_INVALID, "kind must be PRISM_TUNE_ROW, PRISM_TUNE_COL, PRISM_TUNE_SCAN or PRISM_TUNE_SCAN_TC");
     if (shape >= 0) {
         const int n = kind == PRISM_TUNE_ROW ? P->g.nx : P->g.ny;
         if (shape >= tune_shapes(kind) || !tune_shape_valid(kind, n, shape))
@@ -1666,6 +1682,14 @@ extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_
         for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) out->ms[v] = P->scan_tuned ? P->scan_ms[v] : -1.0;
         return PRISM_OK;
     }
+    if (kind == PRISM_TUNE_SCAN_TC) {
+        const bool tc = P->prec != PRISM_PRECISION_FP32;
+        out->n_shapes = tc ? std::min(scan_tc_shapes(tc_mode(P->prec)), PRISM_TUNE_MAX_SHAPES) : 0;
+        out->chosen = tc ? tc_shape(P) : -1;
+        out->default_shape = tc ? 0 : -1;
+        for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) out->ms[v] = P->tc_tuned ? P->tc_ms[v] : -1.0;
+        return PRISM_OK;
+    }
     if (kind != PRISM_TUNE_ROW && kind != PRISM_TUNE_COL) return fail(PRISM_ERR_INVALID, "bad tune kind");
     const int n = kind == 0 ? P->g.nx : P->g.ny;
     out->n_shapes = std::min(tune_shapes(kind), PRISM_TUNE_MAX_SHAPES);
@@ -1677,11 +1701,54 @@ extern "C" int prism_plan_tune_result(const prism_plan *P, int kind, prism_tune_
 }
 
 extern "C" const char *prism_tune_shape_name(int kind, int shape) {
-    return kind == PRISM_TUNE_SCAN ? scan_gemm_shape_name(shape) : tune_shape_name(kind, shape);
+    return kind == PRISM_TUNE_SCAN      ? scan_gemm_shape_name(shape)
+           : kind == PRISM_TUNE_SCAN_TC ? scan_tc_shape_name(shape)
+                                        : tune_shape_name(kind, shape);
 }
 
 extern "C" int prism_tune_shape_fft_variant(int kind, int shape) {
     return kind == PRISM_TUNE_ROW || kind == PRISM_TUNE_COL ? tune_shape_fft_variant(kind, shape) : -1;
+}
+
+// 16-bit plans: time the caller's scan with each ring shape of the tensor-core scan (a warm-up and
+// two timed launches each) and keep the fastest; every shape gives bitwise the same stack, which
+// is left in a.out
+static int autotune_scan_tc(prism_plan *P, ScanArgs &a) {
+    for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->tc_ms[v] = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int rc = PRISM_OK, best = 0;
+    double best_ms = -1.0;
+    for (int v = 0; v < scan_tc_shapes(tc_mode(P->prec)) && v < PRISM_TUNE_MAX_SHAPES && !rc; ++v) {
+        P->tc_shape = v;
+        int grid = 0;
+        if (scan_tc_grid(P->nw, P->kp, tc_mode(P->prec), v, a.scan_px, a.scan_py) <= 0) continue;  // does not fit
+        if ((rc = scan_setup(P, a, &grid))) break;
+        if ((rc = scan_go(P, a, grid))) break;
+        cudaError_t e = cudaEventRecord(e0, P->stream);
+        for (int r = 0; r < 2 && e == cudaSuccess && !rc; ++r) rc = scan_go(P, a, grid);
+        if (rc) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(PRISM_ERR_CUDA, std::string("scan autotune ") + scan_tc_shape_name(v) + ": " + cudaGetErrorString(e));
+            break;
+        }
+        P->tc_ms[v] = ms / 2.0;
+        if (best_ms < 0 || ms / 2.0 < best_ms) {
+            best = v;
+            best_ms = ms / 2.0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->tc_shape = best;
+    P->tc_tuned = !rc;
+    if (rc) return rc;
+    return scan_launch(P, a);
 }
 
 // The scan's contraction tile shape (Calculation Time section: the scan term P B N^2 / (4 f^4) is
@@ -1697,7 +1764,7 @@ extern "C" int prism_plan_autotune_scan(prism_plan *P, const prism_probe *probe,
     if (a.n_probes == 0) return PRISM_OK;
     if ((rc = check_dev_ptr(out_dev, 4, "out_dev"))) return rc;
     a.out = out_dev;
-    if (P->prec != PRISM_PRECISION_FP32) return scan_launch(P, a);  // one shape: just the scan
+    if (P->prec != PRISM_PRECISION_FP32) return autotune_scan_tc(P, a);
     for (int v = 0; v < PRISM_TUNE_MAX_SHAPES; ++v) P->scan_ms[v] = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));

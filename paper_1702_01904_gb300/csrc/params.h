@@ -181,11 +181,17 @@ cudaError_t launch_wait_selftest(int *status, long long limit_cycles, int arrive
 cudaError_t launch_quantize(const QuantArgs &a, cudaStream_t s);
 cudaError_t launch_dequantize(const void *S16, const float *scale, float2 *out, int n_beams, int npix, int kp,
                               int mode, cudaStream_t s);
-cudaError_t launch_scan_tc(int nw, int mode, int grid, const ScanArgs &a, cudaStream_t s);
+cudaError_t launch_scan_tc(int nw, int mode, int shape, int grid, const ScanArgs &a, cudaStream_t s);
 bool scan_tc_supported(int nw);
 // persistent grid of the tensor-core scan (resident CTAs, at most the probe groups), 0 if it does
 // not fit; window scratch bytes for that grid
-int scan_tc_grid(int nw, int kp, int mode, int scan_px, int scan_py);
+int scan_tc_grid(int nw, int kp, int mode, int shape, int scan_px, int scan_py);
+// ring shapes of the tensor-core scan's A operand (scan_tc.cuh): count for a mode, name; the
+// non-default shapes (kernels_tc_tune.cu)
+int scan_tc_shapes(int mode);
+const char *scan_tc_shape_name(int shape);
+int scan_tc_grid_tuned(int nw, int kp, int mode, int shape, int scan_px, int scan_py);
+cudaError_t launch_scan_tc_tuned(int nw, int mode, int shape, int grid, const ScanArgs &a, cudaStream_t s);
 // window scratch of the tensor-core scan: one slot per CTA plus one per split block of the last round
 size_t scan_tc_win_bytes(int nw, int grid, int scan_px, int scan_py);
 // autotuner launch shapes of ROW_STD (kind 0) and COL_STD (kind 1), N = 256 ... 2048 (kernels_tune.cu)

@@ -35,6 +35,7 @@ PRISM_PRECISION_FP16X2 = 3
 PRISM_TUNE_ROW = 0
 PRISM_TUNE_COL = 1
 PRISM_TUNE_SCAN = 2
+PRISM_TUNE_SCAN_TC = 3
 PRISM_TUNE_MAX_SHAPES = 16
 PRISM_BATCH_AUTOTUNE = 1
 PRISM_BATCH_AUTOTUNE_FFT_RADIX = 2

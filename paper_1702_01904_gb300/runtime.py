@@ -122,12 +122,13 @@ class PrismSimulation:
 
     def tune_result(self):
         out = {}
-        for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col"), (P.PRISM_TUNE_SCAN, "scan")):
+        for kind, label in ((P.PRISM_TUNE_ROW, "row"), (P.PRISM_TUNE_COL, "col"), (P.PRISM_TUNE_SCAN, "scan"),
+                            (P.PRISM_TUNE_SCAN_TC, "scan_tc")):
             e = P.prism_plan_tune_result(self.plan, kind)
             name = (lambda v: P.prism_tune_shape_name(kind, v) if v >= 0 else "default")
             out[label] = {"chosen": name(e.chosen), "default": name(e.default_shape),
                           "ms": {P.prism_tune_shape_name(kind, v): e.ms[v] for v in range(e.n_shapes) if e.ms[v] >= 0}}
-            if kind != P.PRISM_TUNE_SCAN:
+            if kind in (P.PRISM_TUNE_ROW, P.PRISM_TUNE_COL):
                 # FFT radix variant of the shape in use (the default launcher: the default shape's)
                 v = e.chosen if e.chosen >= 0 else e.default_shape
                 out[label]["fft_variant"] = max(P.prism_tune_shape_fft_variant(kind, v), 0)

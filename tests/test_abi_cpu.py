@@ -160,6 +160,8 @@ def test_tune_shapes_list_both_fft_radix_variants():
         assert all(n.endswith({1: "forward", 2: "inverse", 3: "both"}[r]) for n, r in rv.items() if r)
     assert rv["W4, TMA, 3/SM"] == 0 and rv["W8, staged"] == 0
     assert P.prism_tune_shape_fft_variant(P.PRISM_TUNE_SCAN, 0) == -1
+    assert [P.prism_tune_shape_name(P.PRISM_TUNE_SCAN_TC, v) for v in range(4)] == [
+        "3 x 96 K ring", "2 x 128 K ring", "4 x 64 K ring", "?"]
     with pytest.raises(P.PrismError) as e:
         P.prism_plan_autotune_flags(None, P.PRISM_AUTOTUNE_FFT_RADIX)
     assert e.value.status == P.PRISM_ERR_INVALID

@@ -223,6 +223,47 @@ def test_every_scan_contraction_shape_sizes_its_own_scratch():
     assert n_shapes == 6
 
 
+@pytest.mark.parametrize("prec", [P.PRISM_PRECISION_FP16, P.PRISM_PRECISION_BF16])
+def test_every_tensor_core_ring_shape_is_bitwise_identical(prec):
+    # 16-bit plans: the tensor-core scan's A-operand ring (3 x 96, 2 x 128, 4 x 64 K values) issues the
+    # K = 16 MMAs of a pixel tile in the same order in every shape, so the detector stacks are equal
+    # bit for bit; the autotuner keeps the fastest and leaves the same stack
+    n, cell, f = 512, 32.0, 8
+    grid = P.make_grid(n, n, 2, cell, cell, 2.0, 300.0, f, 2, 0.5, 20.0, precision=prec)
+    V = rand_v(2, n, 23)
+    X, Y = np.meshgrid(0.5 + 0.3 * np.arange(17), cell - 2.0 + 0.3 * np.arange(13))  # wraps in y
+    x0, y0 = X.ravel(), Y.ravel()
+    probe = P.make_probe(20.0, c1=10.0)
+    sim = PrismSimulation(grid)
+    sim.build(V)
+    ref = sim.scan(probe, x0, y0, DET, px=17, py=13).cpu().numpy()
+    res = P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN_TC)
+    assert res.n_shapes == 3 and res.chosen == 0
+    assert P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN).n_shapes == 0
+    for v in range(res.n_shapes):
+        sim.set_shape(P.PRISM_TUNE_SCAN_TC, v)
+        got = sim.scan(probe, x0, y0, DET, px=17, py=13).cpu().numpy()
+        assert np.array_equal(got, ref), P.prism_tune_shape_name(P.PRISM_TUNE_SCAN_TC, v)
+    with pytest.raises(P.PrismError) as e:
+        sim.set_shape(P.PRISM_TUNE_SCAN_TC, 3)
+    assert e.value.status == P.PRISM_ERR_UNSUPPORTED
+    sim.set_shape(P.PRISM_TUNE_SCAN_TC, -1)
+    out = sim.autotune_scan(probe, x0, y0, DET, px=17, py=13).cpu().numpy()
+    assert np.array_equal(out, ref)
+    tr = sim.tune_result()["scan_tc"]
+    assert len(tr["ms"]) == 3 and tr["ms"][tr["chosen"]] == min(tr["ms"].values())
+    sim.close()
+    # an FP32 plan has no ring shapes; split mode has one
+    sim = PrismSimulation(P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0))
+    assert P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN_TC).n_shapes == 0
+    with pytest.raises(P.PrismError):
+        sim.set_shape(P.PRISM_TUNE_SCAN_TC, 0)
+    sim.close()
+    sim = PrismSimulation(P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0, precision=P.PRISM_PRECISION_FP16X2))
+    assert P.prism_plan_tune_result(sim.plan, P.PRISM_TUNE_SCAN_TC).n_shapes == 1
+    sim.close()
+
+
 def test_scan_shape_limits():
     # 16-bit plans have one (tensor-core) scan shape; shapes past the list are refused
     grid = P.make_grid(256, 256, 1, 16.0, 16.0, 2.0, 300.0, 4, 2, 0.5, 20.0, precision=P.PRISM_PRECISION_FP16)
