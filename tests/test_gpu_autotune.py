@@ -279,3 +279,45 @@ def test_scan_shape_limits():
     with pytest.raises(P.PrismError):
         sim.set_shape(P.PRISM_TUNE_SCAN, n)
     sim.close()
+
+
+def test_concurrent_scans_of_different_beam_counts():
+    # plans of different beam counts (so different shared memory for the same scan kernel) scanning
+    # from four host threads at once: every launch keeps its resources and each result equals the
+    # plan's own result scanned alone
+    import threading
+    cases = [(256, 16.0, 4, 20.0), (256, 16.0, 4, 12.0), (256, 16.0, 4, 28.0), (256, 16.0, 4, 16.0)]
+    sims, inputs, refs = [], [], []
+    for i, (n, cell, f, amax) in enumerate(cases):
+        g = P.make_grid(n, n, 2, cell, cell, 2.0, 300.0, f, 2, 0.5, amax)
+        sim = PrismSimulation(g)
+        sim.build(rand_v(2, n, 30 + i))
+        X, Y = np.meshgrid(0.2 + 0.4 * np.arange(15), 0.3 + 0.4 * np.arange(11))
+        x0, y0 = X.ravel(), Y.ravel()
+        probe = P.make_probe(min(amax, 20.0))
+        refs.append(sim.scan(probe, x0, y0, DET, px=15, py=11).cpu().numpy())
+        sims.append(sim)
+        inputs.append((probe, x0, y0))
+    assert len({s.info.n_beams for s in sims}) == len(sims)
+    outs, errors = [None] * len(sims), []
+
+    def worker(i):
+        try:
+            probe, x0, y0 = inputs[i]
+            for _ in range(5):
+                o = sims[i].scan(probe, x0, y0, DET, px=15, py=11)
+                sims[i].sync()
+            outs[i] = o.cpu().numpy()
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(sims))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o, r)
+    for s in sims:
+        s.close()
