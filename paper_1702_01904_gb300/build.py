@@ -22,11 +22,13 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HEADERS = [os.path.join(CSRC, h) for h in ("fft.cuh", "params.h", "internal.h", "tc.cuh", "scan_common.cuh", "pass_kernels.cuh",
-                                           "tune_shapes.cuh", "tune_pass.cuh", "scan_gemm.cuh", "scan_tc.cuh")] + \
+                                           "tune_shapes.cuh", "tune_pass.cuh", "scan_gemm.cuh", "scan_tc.cuh",
+                                           "pass_default.cuh")] + \
     [os.path.join(INCLUDE, "prism.h")]
-CUDA_UNITS = ["kernels_build.cu", "kernels_tune.cu", "kernels_tune_256.cu", "kernels_tune_512.cu", "kernels_tune_1024.cu",
-              "kernels_tune_2048.cu", "kernels_scan.cu", "kernels_tune_scan.cu", "kernels_tc.cu", "kernels_tc_tune.cu",
-              "noalloc.cu"]
+CUDA_UNITS = ["kernels_build.cu", "kernels_pass_512.cu", "kernels_pass_1024.cu", "kernels_pass_2048.cu", "kernels_tune.cu",
+              "kernels_tune_256.cu", "kernels_tune_512_row.cu", "kernels_tune_512_col.cu", "kernels_tune_1024_row.cu",
+              "kernels_tune_1024_col.cu", "kernels_tune_2048_row.cu", "kernels_tune_2048_col.cu", "kernels_scan.cu",
+              "kernels_tune_scan.cu", "kernels_tc.cu", "kernels_tc_tune.cu", "noalloc.cu"]
 HOST_UNITS = ["engine.cpp", "server.cpp"]
 
 
@@ -69,7 +71,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         src, obj = os.path.join(CSRC, u), os.path.join(BUILD, u + ".o")
         objs.append(obj)
         if force or _stale(src, obj):
-            cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *inc, "-c", src, "-o", obj]
+            # every unit's device code compressed in its fatbinary (by default only the larger ones are):
+            # the library is about a fifth of the size, and the driver decompresses a module when it loads it
+            cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xfatbin=-compress-all", "-Xcompiler", "-fPIC", *inc, "-c",
+                   src, "-o", obj]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

@@ -1,10 +1,11 @@
 // kernels_build.cu -- multislice kernels for sm_103a: slice transmission, the row and column
-// passes at their default launch shapes (templates in pass_kernels.cuh), probe shift phases and
-// detector bins; used both by the compact S-matrix build and by the per-probe multislice baseline.
+// passes at their default launch shapes (pass_default.cuh; N >= 512 in kernels_pass_<N>.cu), probe
+// shift phases and detector bins; used both by the compact S-matrix build and by the per-probe multislice baseline.
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
 #include "params.h"
+#include "pass_default.cuh"
 #include "pass_kernels.cuh"
 
 namespace prism {
@@ -103,18 +104,6 @@ cudaError_t launch_transmission(const float *V, float2 *t, size_t n, double sigm
 }
 
 // ------------------------------------------------------------------ default launch shapes
-template <int NX>
-static cudaError_t row_dispatch(RowMode mode, const RowArgs &a, cudaStream_t s) {
-    if (a.n_rows <= 0) return cudaSuccess;
-    constexpr int T = row_default_threads<NX>(), RV = default_fft_variant(NX);
-    switch (mode) {
-        case ROW_STD: return row_go<NX, ROW_STD, T, false, false, RV>(a, s);
-        case ROW_PLANE: return row_go<NX, ROW_PLANE, T, false, false, RV>(a, s);
-        case ROW_OUT: return row_go<NX, ROW_OUT, T, false, false, RV>(a, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
 cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s) {
     switch (nx) {
         case 16: return row_dispatch<16>(mode, a, s);
@@ -122,24 +111,11 @@ cudaError_t launch_row(int nx, RowMode mode, const RowArgs &a, cudaStream_t s) {
         case 64: return row_dispatch<64>(mode, a, s);
         case 128: return row_dispatch<128>(mode, a, s);
         case 256: return row_dispatch<256>(mode, a, s);
-        case 512: return row_dispatch<512>(mode, a, s);
-        case 1024: return row_dispatch<1024>(mode, a, s);
-        case 2048: return row_dispatch<2048>(mode, a, s);
+        case 512: return launch_row_n512(mode, a, s);
+        case 1024: return launch_row_n1024(mode, a, s);
+        case 2048: return launch_row_n2048(mode, a, s);
         default: return cudaErrorInvalidValue;
     }
-}
-
-template <int NY>
-static cudaError_t col_dispatch(ColMode mode, const ColArgs &a, cudaStream_t s) {
-    if (a.batch <= 0) return cudaSuccess;
-    constexpr int W = col_default_w<NY>(), RV = default_fft_variant(NY);
-    constexpr bool STG = col_default_stg<NY>();
-    switch (mode) {
-        case COL_STD: return col_go<NY, COL_STD, W, STG, 0, false, RV>(a, s);
-        case COL_PROBE: return col_go<NY, COL_PROBE, W, STG, 0, false, RV>(a, s);
-        case COL_DETECT: return col_go<NY, COL_DETECT, W, STG, 0, false, RV>(a, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s) {
@@ -149,9 +125,9 @@ cudaError_t launch_col(int ny, ColMode mode, const ColArgs &a, cudaStream_t s) {
         case 64: return col_dispatch<64>(mode, a, s);
         case 128: return col_dispatch<128>(mode, a, s);
         case 256: return col_dispatch<256>(mode, a, s);
-        case 512: return col_dispatch<512>(mode, a, s);
-        case 1024: return col_dispatch<1024>(mode, a, s);
-        case 2048: return col_dispatch<2048>(mode, a, s);
+        case 512: return launch_col_n512(mode, a, s);
+        case 1024: return launch_col_n1024(mode, a, s);
+        case 2048: return launch_col_n2048(mode, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,7 +1,8 @@
 // tune_pass.cuh -- the autotuner's shapes of the two multislice passes (tune_shapes.cuh) as kernel
 // instantiations for one N: validity (compile-time, from the launch configuration alone) and the
-// launch of shape v.  Each kernels_tune_<N>.cu unit instantiates one N, so that the units compile
-// in parallel; kernels_tune.cu holds the tables and dispatches on N.
+// launch of shape v.  Each kernels_tune_<N>.cu unit instantiates one N (from N = 512 on, the row and
+// the column shapes in units of their own, kernels_tune_<N>_row.cu and _col.cu), so that the units
+// compile in parallel; kernels_tune.cu holds the tables and dispatches on N.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -87,11 +88,17 @@ cudaError_t col_launch_n2048(int v, const ColArgs &a, cudaStream_t s);
 }  // namespace tune
 }  // namespace prism
 
-// body of a kernels_tune_<N>.cu unit
-#define PRISM_TUNE_UNIT(N)                                                                                 \
+// bodies of the kernels_tune_<N>*.cu units: the row shapes, the column shapes, or both of one N
+#define PRISM_TUNE_ROW_UNIT(N)                                                                             \
     namespace prism {                                                                                      \
     namespace tune {                                                                                       \
     cudaError_t row_launch_n##N(int v, const RowArgs &a, cudaStream_t s) { return row_launch<N>(v, a, s, RowSeq{}); } \
+    }                                                                                                      \
+    }
+#define PRISM_TUNE_COL_UNIT(N)                                                                             \
+    namespace prism {                                                                                      \
+    namespace tune {                                                                                       \
     cudaError_t col_launch_n##N(int v, const ColArgs &a, cudaStream_t s) { return col_launch<N>(v, a, s, ColSeq{}); } \
     }                                                                                                      \
     }
+#define PRISM_TUNE_UNIT(N) PRISM_TUNE_ROW_UNIT(N) PRISM_TUNE_COL_UNIT(N)
