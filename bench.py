@@ -185,7 +185,7 @@ def oracle_sample(w, V, budget_s=20.0):
 # device code of the row and column pass kernels (the ones profiles/dram_traffic.json measures):
 # the kernel templates and their helpers, the compiled launch shapes, and the parameter blocks the
 # kernels read (host-only declarations in params.h do not enter the hash)
-PASS_SOURCES = ("fft.cuh", "pass_kernels.cuh", "tc.cuh", "kernels_build.cu", "tune_shapes.cuh")
+PASS_SOURCES = ("fft.cuh", "pass_kernels.cuh", "pass_default.cuh", "tc.cuh", "kernels_build.cu", "tune_shapes.cuh")
 PASS_STRUCTS = ("struct Tw64", "struct RowArgs", "struct ColArgs")
 
 
