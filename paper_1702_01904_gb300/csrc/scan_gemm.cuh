@@ -155,25 +155,41 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             }
             // loader: thread -> tile pixel pair m = 2 (tid % (MT/2)), beams kk = tid / (MT/2), + 4, ...
             // (tw, tx0 and the M tile bounds even: the pair lies in one row, on an even column)
+            // (the loader takes the steps in order: it counts its M tile and beam chunk, and finds its
+            // pixel pair in the S-matrix only when the tile changes)
             constexpr int PAIRS = MT / 2, KSTEP = BLOCK / PAIRS;
             const int lm = 2 * (tid & (PAIRS - 1)), lk = tid / PAIRS;
-            auto load = [&](int ls) {
-                if (ls < ls1) {
-                    const int mt = ls / nkc, c = ls - mt * nkc;
-                    const int b0 = c * kcs, bn = min(kcs, nb - b0);
-                    const int idx = mt * MT + lm;
-                    if (idx < npx) {
-                        const int ty = idx / tw, tx = idx - ty * tw;
-                        const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
-                        float2 *dst = ring + (ls % S) * (KB * MT) + lm;
-                        const float2 *src = a.S + (size_t)(b0 + lk) * npix_s + gp;
+            const int mt0 = uni ? part * nmt / np : 0;  // ls0 = mt0 nkc
+            int l_step = ls0, l_mt = mt0, l_c = 0, l_tile = -1;
+            const float2 *l_pix = nullptr;  // the pair's pixel in beam lk (nullptr: past the union tile)
+            auto load = [&]() {
+                if (l_step < ls1) {
+                    if (l_mt != l_tile) {
+                        l_tile = l_mt;
+                        const int idx = l_mt * MT + lm;
+                        l_pix = nullptr;
+                        if (idx < npx) {
+                            const int ty = idx / tw, tx = idx - ty * tw;
+                            const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
+                            l_pix = a.S + (size_t)lk * npix_s + gp;
+                        }
+                    }
+                    if (l_pix) {
+                        const int b0 = l_c * kcs, bn = min(kcs, nb - b0);
+                        float2 *dst = ring + (l_step % S) * (KB * MT) + lm;
+                        const float2 *src = l_pix + (size_t)b0 * npix_s;
                         for (int kk = lk; kk < bn; kk += KSTEP, src += (size_t)KSTEP * npix_s) cp_async16(dst + kk * MT, src);
                     }
+                    if (++l_c == nkc) {
+                        l_c = 0;
+                        ++l_mt;
+                    }
                 }
+                ++l_step;
                 cp_async_commit();
             };
 #pragma unroll
-            for (int l = 0; l < S - 1; ++l) load(ls0 + l);
+            for (int l = 0; l < S - 1; ++l) load();
             // psi = sum_b S_b Re(alpha_b) + i sum_b S_b Im(alpha_b): two complex accumulators per
             // (pixel, probe), each advanced by one packed FP32x2 FMA of the S value with a real
             // coefficient (accr += S Re a, acci += S Im a), combined when the M tile is done
@@ -182,12 +198,13 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = make_float2(0.f, 0.f);
+            int mt = mt0, c = 0;  // the M tile and beam chunk of step ls
+            bool need = false;    // this warp computes M tile mt
             for (int ls = ls0; ls < ls1; ++ls) {
-                const int mt = ls / nkc, c = ls - mt * nkc;
                 cp_async_wait<S - 2>();
                 __syncthreads();
-                load(ls + S - 1);  // its slot was last read in step ls - 1, which every thread has left
-                const bool need = busy && (mt * MT + MT - 1) / tw >= wy0 && (mt * MT) / tw <= wy1;
+                load();  // step ls + S - 1: its slot was last read in step ls - 1, which every thread has left
+                if (c == 0) need = busy && (mt * MT + MT - 1) / tw >= wy0 && (mt * MT) / tw <= wy1;
                 if (need) {
                     const float2 *cur = ring + (ls % S) * (KB * MT);
                     const int b0 = c * kcs, bn = min(kcs, nb - b0);
@@ -230,6 +247,10 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                             }
                         }
                     }
+                }
+                if (++c == nkc) {
+                    c = 0;
+                    ++mt;
                 }
             }
             cp_async_wait<0>();

@@ -106,7 +106,8 @@ struct TcCfg {
     static constexpr int META = 256;                        // ints
     static constexpr int META_LAST = META - 1;              // flag: this CTA completed a split block
     static constexpr int MAXP = 16;                         // parts per split block at most
-    static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16;
+    // twiddles, meta, the ring's mbarriers, the TMEM address (16 B), the probes' packed window origins
+    static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16 + G * sizeof(int);
     static constexpr uint32_t TMEM_COLS = 2 * N;            // two accumulators
     __host__ __device__ static constexpr size_t bmat_bytes(int kp) { return (size_t)PARTS * kp * N * 2; }
     __host__ __device__ static constexpr size_t region0(int kp) {
@@ -133,6 +134,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
     int *meta = reinterpret_cast<int *>(twf + NW);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(meta + C::META);
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(mbar + S);
+    int *wofs = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(tmem_base) + 16);  // [G]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint16_t *S16 = reinterpret_cast<const uint16_t *>(a.S16);
 
@@ -224,27 +226,49 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
             const int m0 = uni ? part * nmt / np : 0, m1 = uni ? (part + 1) * nmt / np : nmt;
             const int nsteps = (m1 - m0) * nkc;
             if (nsteps == 0) continue;
+            // each probe's window origin in the tile, packed (oy << 16 | ox; both >= 0 and small), or
+            // one that no tile pixel reaches for the probes not computed here; the drains read it after
+            // the step loop's first barrier, and the previous sub-group's drains ended at a barrier
+            if (tid < G) {
+                const bool act = uni ? meta[136 + tid] >= 0 : tid == sg;
+                wofs[tid] = !act ? 0x7fff7fff : uni ? (meta[104 + tid] << 16) | meta[72 + tid] : 0;
+            }
             const uint32_t st0 = st;
             // A chunk of local step ls: thread -> pixel m = 16 warp + lane/2 of the M tile, K cores
             // kc = lane%2, lane%2 + 2, ...  (a lane pair reads one 32-byte sector of a pixel; a warp
             // writes 2 x 256 contiguous shared-memory bytes)
-            auto load = [&](int ls) {
-                if (ls < nsteps) {
-                    const int mt = m0 + ls / nkc, c = ls % nkc;
-                    const int k0 = c * kcs, kn = min(kcs, kp - k0);
-                    const int m = warp * 16 + (lane >> 1);
-                    const int idx = mt * 128 + m;
-                    if (idx < npx) {
-                        const int ty = idx / tw, tx = idx - ty * tw;
-                        const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
-                        const uint16_t *src = S16 + gp * (C::PARTS * kp) + k0;
-                        unsigned char *dst = ring + ((st0 + ls) % S) * C::STAGE_BYTES + (m >> 3) * 128 + (m & 7) * 16;
+            // The loader takes the steps in order (step ls: M tile m0 + ls / nkc, K chunk ls % nkc), so
+            // it counts its tile and chunk, and finds its pixel's row of S16 only when the tile changes.
+            const int lm = warp * 16 + (lane >> 1);
+            int l_step = 0, l_mt = m0, l_c = 0, l_tile = -1;
+            const uint16_t *l_row = nullptr;  // the pixel's K row (nullptr: past the union tile)
+            auto load = [&]() {
+                if (l_step < nsteps) {
+                    if (l_mt != l_tile) {
+                        l_tile = l_mt;
+                        const int idx = l_mt * 128 + lm;
+                        l_row = nullptr;
+                        if (idx < npx) {
+                            const int ty = idx / tw, tx = idx - ty * tw;
+                            const size_t gp = (size_t)((ty0 + ty) & (a.ny_s - 1)) * a.nx_s + ((tx0 + tx) & (a.nx_s - 1));
+                            l_row = S16 + gp * (C::PARTS * kp);
+                        }
+                    }
+                    if (l_row) {
+                        const int k0 = l_c * kcs, kn = min(kcs, kp - k0);
+                        const uint16_t *src = l_row + k0;
+                        unsigned char *dst = ring + ((st0 + l_step) % S) * C::STAGE_BYTES + (lm >> 3) * 128 + (lm & 7) * 16;
                         for (int kc = lane & 1; kc < kn / 8; kc += 2) {
                             cp_async16(dst + kc * 2048, src + kc * 8);
                             if constexpr (SPLIT) cp_async16(dst + C::PART_BYTES + kc * 2048, src + kp + kc * 8);
                         }
                     }
+                    if (++l_c == nkc) {
+                        l_c = 0;
+                        ++l_mt;
+                    }
                 }
+                ++l_step;
                 cp_async_commit();
             };
             // accumulator of M tile mt -> window scratch of every probe whose window holds the pixel
@@ -253,6 +277,7 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 const int q = warp & 3, h = warp >> 2;  // lane quarter, half of the N columns
                 const int idx = mt * 128 + 32 * q + lane;
                 const int ty = idx / tw, tx = idx - ty * tw;
+                float2 *wh = a.win + ((size_t)slot * G + h * (G / 2)) * (NW * NW);  // this half's windows
 #pragma unroll
                 for (int c16 = 0; c16 < N / 32; ++c16) {
                     float v[16];
@@ -260,18 +285,19 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                     if (idx < npx) {
 #pragma unroll
                         for (int pp = 0; pp < 8; ++pp) {
-                            const int p = h * (G / 2) + c16 * 8 + pp;
-                            const bool act = uni ? meta[136 + p] >= 0 : p == sg;
-                            const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : 0);
-                            if (act && (unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
-                                a.win[((size_t)slot * G + p) * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
+                            const int pl = c16 * 8 + pp;  // probe h G/2 + pl
+                            const int o = wofs[h * (G / 2) + pl];
+                            const int wy = ty - (o >> 16), wx = tx - (o & 0xffff);
+                            if ((unsigned)wy < (unsigned)NW && (unsigned)wx < (unsigned)NW)
+                                wh[pl * (NW * NW) + wy * NW + wx] = make_float2(v[2 * pp], v[2 * pp + 1]);
                         }
                     }
                 }
                 tc::fence_before_sync();
             };
 #pragma unroll
-            for (int l = 0; l < S - 1; ++l) load(l);
+            for (int l = 0; l < S - 1; ++l) load();
+            int mt = m0, c = 0;  // the M tile and K chunk of step ls
             for (int ls = 0; ls < nsteps; ++ls) {
                 const uint32_t s = st0 + ls;
                 cp_async_wait<S - 2>();
@@ -280,7 +306,6 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                     dead = true;
                     break;
                 }
-                const int mt = m0 + ls / nkc, c = ls % nkc;
                 if (tid == 0) {
                     tc::fence_after_sync();
                     const int k0 = c * kcs, kn = min(kcs, kp - k0);
@@ -301,8 +326,12 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 }
                 // ring slot (s + S - 1) % S was read by step s - 1: wait for its MMAs before refilling it
                 if (ls >= 1 && !tc::mbar_wait_bounded(&mbar[(s - 1) % S], ((s - 1) / S) & 1, TC_WAIT_CYCLES)) fail();
-                load(ls + S - 1);
+                load();  // step ls + S - 1
                 if (c == 0 && mt > m0) drain(mt - 1);  // the previous tile of this unit
+                if (++c == nkc) {
+                    c = 0;
+                    ++mt;
+                }
             }
             st = st0 + nsteps;
             if (dead) break;
