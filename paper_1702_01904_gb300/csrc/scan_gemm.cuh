@@ -69,8 +69,9 @@ struct GemmCfg {
         const size_t r = ((size_t)RING + (size_t)n_beams * G) * sizeof(float2);
         return ((r > EPI ? r : EPI) + 127) & ~(size_t)127;
     }
+    // region0, the window twiddles, meta, the probes' packed window origins
     __host__ __device__ static constexpr size_t smem(int n_beams) {
-        return region0(n_beams) + (size_t)(NWX + NWY) * sizeof(float2) + META * sizeof(int);
+        return region0(n_beams) + (size_t)(NWX + NWY) * sizeof(float2) + META * sizeof(int) + G * sizeof(int);
     }
 };
 
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
     float2 *twx = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(smf) + C::region0(nb));
     float2 *twy = twx + NWX;
     int *meta = reinterpret_cast<int *>(twy + NWY);
+    int *wofs = meta + C::META;  // [G], 16-byte aligned
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < NWX; i += BLOCK) twx[i] = a.tw_fwd[i];
     for (int i = tid; i < NWY; i += BLOCK) twy[i] = a.tw_fwd_y[i];
@@ -134,6 +136,13 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             const int tw = uni ? meta[1] : NWX + 2 * ox, th = uni ? meta[2] : NWY;
             const int tx0 = uni ? meta[3] : meta[8 + sg] - ox, ty0 = uni ? meta[4] : meta[40 + sg];
             const int npx = tw * th, nmt = (npx + MT - 1) / MT;
+            // each probe's window origin in the tile, packed (oy << 16 | ox; both >= 0 and small), or
+            // one that no tile pixel reaches for the probes not computed here; read by the scatters
+            // after a step's barrier (the previous sub-group's ended at a barrier)
+            if (tid < G) {
+                const bool act = uni ? meta[136 + tid] >= 0 : tid == sg;
+                wofs[tid] = !act ? 0x7fff7fff : uni ? (meta[104 + tid] << 16) | meta[72 + tid] : ox;
+            }
             // ring steps (M tile, beam chunk) of this unit: all, or a split block's share of M tiles
             const int ls0 = uni ? part * nmt / np * nkc : 0, ls1 = uni ? (part + 1) * nmt / np * nkc : nmt * nkc;
             const bool busy = uni || (sg >> 2) == warp;  // warps whose probes are computed
@@ -230,19 +239,20 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
                 if (c == nkc - 1) {
                     // M tile done: scatter tile pixel (ty, tx) to pixel (ty - oy_p, tx - ox_p) of probe p
                     if (need) {
+                        const int4 o4 = *reinterpret_cast<const int4 *>(wofs + 4 * warp);  // this warp's probes
+                        const int oo[4] = {o4.x, o4.y, o4.z, o4.w};
+                        float2 *wp = a.win + ((size_t)slot * G + 4 * warp) * (NWX * NWY);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int idx = mt * MT + lane + 32 * i;
                             const int ty = idx / tw, tx = idx - ty * tw;
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                const int p = 4 * warp + j;
-                                const bool act = uni ? meta[136 + p] >= 0 : p == sg;
-                                const int wy = ty - (uni ? meta[104 + p] : 0), wx = tx - (uni ? meta[72 + p] : ox);
+                                const int wy = ty - (oo[j] >> 16), wx = tx - (oo[j] & 0xffff);
                                 // psi = accr + i acci
                                 const float2 v = make_float2(accr[i][j].x - acci[i][j].y, accr[i][j].y + acci[i][j].x);
-                                if (act && idx < npx && (unsigned)wy < (unsigned)NWY && (unsigned)wx < (unsigned)NWX)
-                                    __stcs(a.win + ((size_t)slot * G + p) * (NWX * NWY) + wy * NWX + wx, v);
+                                if (idx < npx && (unsigned)wy < (unsigned)NWY && (unsigned)wx < (unsigned)NWX)
+                                    __stcs(wp + j * (NWX * NWY) + wy * NWX + wx, v);
                                 accr[i][j] = acci[i][j] = make_float2(0.f, 0.f);
                             }
                         }
