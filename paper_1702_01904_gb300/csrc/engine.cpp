@@ -388,7 +388,7 @@ struct prism_plan {
     int kp = 0;
     float2 *win = nullptr;     // scan window scratch (GEMM and tensor-core scans)
     size_t win_cap = 0;
-    int *win_cnt = nullptr;    // FP32 GEMM scan: completion counters of split groups
+    int *win_cnt = nullptr;    // scans: completion counters of split groups, work-unit counters
     size_t cnt_cap = 0;
     CUtensorMap wave_map, wave_map4;  // the wave stack for the TMA-staged column pass (8 / 4 columns per box)
     CUtensorMap out_map, out_map4;    // its stores (ColArgs::out_map)
@@ -1019,8 +1019,8 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     return PRISM_OK;
 }
 
-// completion counters of the blocks a scan splits over idle CTAs: int[grid], zeroed when allocated;
-// every launch leaves them at zero
+// the scan's counters (completion counters of the blocks it splits over idle CTAs, int[grid], then its
+// work-unit counters, int[2]), zeroed when allocated; every launch leaves them at zero
 static int split_counters(prism_plan *P, ScanArgs &a, int grid) {
     const size_t cb = scan_gemm_cnt_bytes(grid);
     const bool fresh = !P->win_cnt || cb > P->cnt_cap;

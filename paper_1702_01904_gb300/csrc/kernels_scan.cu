@@ -356,7 +356,8 @@ size_t scan_gemm_win_bytes(int nwx, int nwy, int shape, int grid, int scan_px, i
 
 int scan_gemm_shapes() { return N_GEMM_SHAPES; }
 
-size_t scan_gemm_cnt_bytes(int grid) { return (size_t)(grid > 0 ? grid : 1) * sizeof(int); }
+// the split blocks' completion counters (one per CTA at most), the next work unit, the CTAs done
+size_t scan_gemm_cnt_bytes(int grid) { return (size_t)((grid > 0 ? grid : 1) + 2) * sizeof(int); }
 
 // rectangular windows (separate interpolation factors f_x != f_y): grouped kernel only
 template <int NWX>

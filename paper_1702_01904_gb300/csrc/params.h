@@ -109,7 +109,8 @@ struct ScanArgs {
                                // (split mode: [ny_s * nx_s][2][kp], value row then remainder row)
     const float *beam_scale;   // [B] power of two: S_b = S16_b * beam_scale[b]
     float2 *win;               // window scratch [slots][probes per group][nw][nw]
-    int *win_cnt;              // parts finished per split block (zero between launches)
+    int *win_cnt;              // [gridDim.x] parts finished per split block, then the next work unit and
+                               // the CTAs done (all zero between launches)
     int *err;                  // device error word (a bounded wait that ran out sets bit 0)
     int kp;                    // K = 2 * roundup(B, 8)
     int scan_px, scan_py;      // probe raster, probe index = row * scan_px + col
@@ -171,7 +172,8 @@ bool scan_gemm_shape_valid(int nwx, int nwy, int shape);
 const char *scan_gemm_shape_name(int shape);
 int scan_gemm_grid_tuned(int nwx, int nwy, int shape, int n_beams, int scan_px, int scan_py);
 cudaError_t launch_scan_gemm_tuned(int nwx, int nwy, int shape, int grid, const ScanArgs &a, cudaStream_t s);
-// completion counters of the split groups (int[grid]; zeroed once, each launch leaves them zero)
+// scan counters: completion counters of the split groups (int[grid]), the next work unit and the
+// CTAs done (int[2]); zeroed once, each launch leaves them zero
 size_t scan_gemm_cnt_bytes(int grid);
 cudaError_t launch_shift(const ShiftArgs &a, cudaStream_t s);
 cudaError_t launch_bins(const BinArgs &a, cudaStream_t s);

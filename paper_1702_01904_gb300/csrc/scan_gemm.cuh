@@ -64,6 +64,7 @@ struct GemmCfg {
     static constexpr size_t EPI = (size_t)(EW * NWY * PW + EX) * sizeof(float2);
     static constexpr int META = 256;
     static constexpr int META_LAST = META - 1;       // flag: this CTA completed a split block
+    static constexpr int META_UNIT = META - 2;       // the work unit this CTA took
     static constexpr int MAXP = 16;                  // parts per split block at most
     __host__ __device__ static constexpr size_t region0(int n_beams) {
         const size_t r = ((size_t)RING + (size_t)n_beams * G) * sizeof(float2);
@@ -100,7 +101,17 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
     const int tail = n_groups % gridDim.x, full = n_groups - tail;
     const int parts = tail ? min(C::MAXP, (int)gridDim.x / tail) : 1;
 
-    for (int u = blockIdx.x; u < full + tail * parts; u += gridDim.x) {
+    // Work units come from a counter (after the split counters: the next unit, then the CTAs done),
+    // not by a fixed stride: the two CTAs that share an SM are not issued equally, and with fixed
+    // shares the favoured one finished its blocks early and left the other to finish alone.  Which
+    // CTA computes a unit changes no result.
+    int *next_unit = a.win_cnt + gridDim.x, *ctas_done = next_unit + 1;
+    const int n_units = full + tail * parts;
+    for (;;) {
+        if (tid == 0) meta[C::META_UNIT] = atomicAdd(next_unit, 1);
+        __syncthreads();  // every thread read the previous unit before the barriers of its body
+        const int u = meta[C::META_UNIT];
+        if (u >= n_units) break;
         // unit u: block u whole (scratch slot = this CTA), or part `part` of split block full + tg
         int grp = u, part = 0, np = 1, slot = tail + blockIdx.x;
         if (u >= full) {
@@ -297,6 +308,11 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             window_epilogue<NWX, NWY, BLOCK, C::EW, PW>(a, win, ex, twx, twy, ne, meta + 200 + e0, tid);
             __syncthreads();
         }
+    }
+    // the last CTA to finish has seen every unit taken: it zeroes both counters for the next launch
+    if (tid == 0 && atomicAdd(ctas_done, 1) == (int)gridDim.x - 1) {
+        *next_unit = 0;
+        *ctas_done = 0;
     }
 }
 

@@ -105,6 +105,7 @@ struct TcCfg {
     static constexpr size_t EPI = (size_t)(EW * NW * PW + EX) * sizeof(float2);
     static constexpr int META = 256;                        // ints
     static constexpr int META_LAST = META - 1;              // flag: this CTA completed a split block
+    static constexpr int META_UNIT = META - 2;              // the work unit this CTA took
     static constexpr int MAXP = 16;                         // parts per split block at most
     // twiddles, meta, the ring's mbarriers, the TMEM address (16 B), the probes' packed window origins
     static constexpr size_t MISC = (size_t)NW * sizeof(float2) + META * sizeof(int) + STAGES * 8 + 16 + G * sizeof(int);
@@ -170,7 +171,15 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
     // CTAs; a split block's windows in a scratch slot of its own ([0, tail)), the CTA slots after
     const int tail = ngroups % gridDim.x, full = ngroups - tail;
     const int parts = tail ? min(C::MAXP, (int)gridDim.x / tail) : 1;
-    for (int u = blockIdx.x; u < full + tail * parts && !dead; u += gridDim.x) {
+    // work units from a counter, as in the FP32 GEMM scan (the next unit, then the CTAs done, after
+    // the split counters)
+    int *next_unit = a.win_cnt + gridDim.x, *ctas_done = next_unit + 1;
+    const int n_units = full + tail * parts;
+    while (!dead) {
+        if (tid == 0) meta[C::META_UNIT] = atomicAdd(next_unit, 1);
+        __syncthreads();  // every thread read the previous unit before the barriers of its body
+        const int u = meta[C::META_UNIT];
+        if (u >= n_units) break;
         int grp = u, part = 0, np = 1, slot = tail + blockIdx.x;
         if (u >= full) {
             const int tg = (u - full) / parts;
@@ -370,6 +379,12 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
             window_epilogue<NW, NW, BLOCK, C::EW, PW>(a, win, ex, twf, twf, ne, meta + 200 + e0, tid);
             __syncthreads();
         }
+    }
+    // the last CTA to finish has seen every unit taken (or a wait ran out, and the host zeroes the
+    // counters): it zeroes both counters for the next launch
+    if (tid == 0 && atomicAdd(ctas_done, 1) == (int)gridDim.x - 1) {
+        *next_unit = 0;
+        *ctas_done = 0;
     }
     cp_async_wait<0>();
     __syncthreads();
