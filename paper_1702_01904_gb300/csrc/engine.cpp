@@ -416,6 +416,8 @@ struct prism_plan {
     int *bin_buf = nullptr;    // window detector: CSR offsets, CSR indices, indices by rank
     size_t bin_cap = 0;
     size_t bin_t_off = 0;      // element offset of the by-rank table in bin_buf
+    size_t bin_16_off = 0;     // element offset of the 16-bit lists in bin_buf (a multiple of 4)
+    size_t bin_n = 0;          // entries of the lists
     float *out_stage = nullptr;
     size_t out_cap = 0;
     float *v_stage = nullptr;
@@ -979,6 +981,16 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
         std::vector<int> all(off);
         all.insert(all.end(), idx.begin(), idx.end());
         all.insert(all.end(), idx_t.begin(), idx_t.end());
+        // the lists once more as 16-bit entries (window pixels < 2^16), from a 16-byte boundary and
+        // padded to 16 bytes, for the scans that stage them in shared memory
+        while (all.size() % 4) all.push_back(0);
+        P->bin_16_off = all.size();
+        P->bin_n = idx.size();
+        std::vector<uint16_t> i16((idx.size() + 7) / 8 * 8, 0);
+        for (size_t i = 0; i < idx.size(); ++i) i16[i] = (uint16_t)idx[i];
+        const size_t w16 = i16.size() / 2;
+        all.resize(all.size() + w16);
+        std::memcpy(all.data() + P->bin_16_off, i16.data(), i16.size() * sizeof(uint16_t));
         if ((rc = grow(P->arena, (void **)&P->bin_buf, &P->bin_cap, all.size() * sizeof(int)))) return rc;
         CUDA_TRY(cudaMemcpyAsync(P->bin_buf, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
         P->det_nbins = det->nbins;
@@ -997,6 +1009,8 @@ static int scan_prepare(prism_plan *P, const prism_probe *probe, const prism_sca
     a.bin_off = det ? P->bin_buf : nullptr;
     a.bin_idx = det ? P->bin_buf + det->nbins + 1 : nullptr;
     a.bin_idx_t = det ? P->bin_buf + P->bin_t_off : nullptr;
+    a.bin_idx16 = det ? reinterpret_cast<const uint16_t *>(P->bin_buf + P->bin_16_off) : nullptr;
+    a.n_bin_idx = det ? (int)P->bin_n : 0;
     a.px_s = pxs;
     a.py_s = pys;
     a.shift_x = tl.sx;

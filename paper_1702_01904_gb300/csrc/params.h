@@ -92,6 +92,9 @@ struct ScanArgs {
     const int *bin_idx;        // window pixel indices (ky*nw + kx) grouped by bin
     const int *bin_idx_t;      // the same lists by rank: entry i of bin k at [i * nbins + k] (rows of
                                // the longest bin; bin k's list ends at bin_off[k+1] - bin_off[k])
+    const uint16_t *bin_idx16; // bin_idx as 16-bit entries, 16-byte aligned and padded to 16 bytes (the
+                               // copy a scan stages in shared memory where it fits), or NULL
+    int n_bin_idx;             // entries of bin_idx (bin_off[nbins])
     float *out;                // [P][nbins] annular bins, or NULL
     float *cbed;               // [P][nw][nw] full window diffraction patterns (FFT order), or NULL
     float acc_w;               // accumulate: out += acc_w * I (else out = I)

@@ -184,7 +184,7 @@ struct ExSize {
 
 template <int NWX, int NWY, int BLOCK, int G, int PW>
 __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, const float2 *twx, const float2 *twy,
-                                int nwin, const int *oidx, int tid) {
+                                int nwin, const int *oidx, int tid, const uint16_t *sidx = nullptr) {
     {
         using FS = FftShape<NWX>;
         using Fwd = FwdFft<NWX>;
@@ -250,20 +250,23 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
     // FP32 partial sums of the FP32 intensities (fixed order; each partial carries a relative error
     // <= (n/4) 2^-24 for n pixels), then adds the four partials and applies the normalisation in
     // FP64 (the final accumulation of the bin), rounding once to FP32.
-    // The lists are read by rank (entry i of bin k at bin_idx_t[i * nbins + k]), so the threads of
-    // consecutive bins read consecutive words.
+    // The lists come from shared memory where the caller staged them (sidx, bin_idx as 16-bit
+    // entries), else from global memory by rank (entry i of bin k at bin_idx_t[i * nbins + k], so
+    // that the threads of consecutive bins read consecutive words); the same entries either way.
     if (a.out) {
         const int nb = a.nbins;
         for (int j = tid; j < nwin * nb; j += BLOCK) {
             const int p = j / nb, k = j - p * nb;
             const float2 *w = win + p * NWY * PW;
-            const int e = __ldg(a.bin_off + k + 1) - __ldg(a.bin_off + k);
+            const int o0 = __ldg(a.bin_off + k), e = __ldg(a.bin_off + k + 1) - o0;
             const int *ix = a.bin_idx_t + k;
+            const uint16_t *sx = sidx ? sidx + o0 : nullptr;
+            auto entry = [&](int i) { return sx ? (int)sx[i] : __ldg(ix + i * nb); };
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             int i = 0;
             for (; i + 4 <= e; i += 4) {
-                const int u0 = __ldg(ix + i * nb), u1 = __ldg(ix + (i + 1) * nb);
-                const int u2 = __ldg(ix + (i + 2) * nb), u3 = __ldg(ix + (i + 3) * nb);
+                const int u0 = entry(i), u1 = entry(i + 1);
+                const int u2 = entry(i + 2), u3 = entry(i + 3);
                 const float2 z0 = w[(u0 >> LNW) * PW + (u0 & (NWX - 1))], z1 = w[(u1 >> LNW) * PW + (u1 & (NWX - 1))];
                 const float2 z2 = w[(u2 >> LNW) * PW + (u2 & (NWX - 1))], z3 = w[(u3 >> LNW) * PW + (u3 & (NWX - 1))];
                 s0 = fmaf(z0.x, z0.x, fmaf(z0.y, z0.y, s0));
@@ -272,7 +275,7 @@ __device__ void window_epilogue(const ScanArgs &a, float2 *win, float2 *ex, cons
                 s3 = fmaf(z3.x, z3.x, fmaf(z3.y, z3.y, s3));
             }
             for (; i < e; ++i) {
-                const int u = __ldg(ix + i * nb);
+                const int u = entry(i);
                 const float2 z = w[(u >> LNW) * PW + (u & (NWX - 1))];
                 s0 = fmaf(z.x, z.x, fmaf(z.y, z.y, s0));
             }

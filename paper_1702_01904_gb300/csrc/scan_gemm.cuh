@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(256, 2) k_scan_gemm(const __grid_constant__ Sc
             if (!meta[C::META_LAST]) continue;
         }
         // epilogue: EW windows at a time through shared memory (the window scratch written above is
-        // visible to the whole CTA after the barrier)
+        // visible to the whole CTA after the barrier).  The bins read their pixel lists from global
+        // memory: staging them in shared memory (as the tensor-core scan does) cost this kernel, at
+        // its register limit, more than it saved (5.09 against 5.03 ms on the carbon scan).
         const int nvalid = meta[5];
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
             const int ne = min(C::EW, nvalid - e0);

@@ -366,6 +366,15 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
         }
         // epilogue: EW windows at a time through shared memory
         const int nvalid = meta[5];
+        // the bins' pixel lists (16-bit) in the shared memory past the windows and the exchange, where
+        // the ring and the coefficient operand were, when they fit there: loaded with the first windows,
+        // read by every pass of this unit instead of global memory (2.11 -> 2.08 ms on the FP16
+        // carbon scan)
+        constexpr size_t EPI16 = (C::EPI + 15) & ~(size_t)15;
+        const int n16 = a.out && a.bin_idx16 ? (a.n_bin_idx + 7) / 8 : 0;  // 16-byte pieces
+        const uint16_t *sidx = n16 > 0 && EPI16 + (size_t)n16 * 16 <= C::region0(kp)
+                                   ? reinterpret_cast<const uint16_t *>(sm + EPI16)
+                                   : nullptr;
         for (int e0 = 0; e0 < nvalid; e0 += C::EW) {
             const int ne = min(C::EW, nvalid - e0);
             // the windows in 16-byte pieces (two pixels of a row), every piece in flight at once
@@ -373,10 +382,12 @@ __global__ void __maxnreg__(112) k_scan_tc(const __grid_constant__ ScanArgs a) {
                 const int e = i / (NW * NW / 2), u = 2 * (i - e * (NW * NW / 2));
                 cp_async16(win + (e * NW + u / NW) * PW + (u & (NW - 1)), a.win + ((size_t)slot * G + meta[168 + e0 + e]) * (NW * NW) + u);
             }
+            if (sidx && e0 == 0)
+                for (int i = tid; i < n16; i += BLOCK) cp_async16(sm + EPI16 + (size_t)i * 16, a.bin_idx16 + (size_t)i * 8);
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            window_epilogue<NW, NW, BLOCK, C::EW, PW>(a, win, ex, twf, twf, ne, meta + 200 + e0, tid);
+            window_epilogue<NW, NW, BLOCK, C::EW, PW>(a, win, ex, twf, twf, ne, meta + 200 + e0, tid, sidx);
             __syncthreads();
         }
     }
