@@ -311,6 +311,30 @@ def test_scan_partition_invariant():
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [P.PRISM_PRECISION_FP32, P.PRISM_PRECISION_FP16])
+def test_scans_of_other_grid_sizes_leave_the_unit_counters_zero(prec):
+    # the scans take their work units from a counter placed after one split counter per CTA, so its
+    # place moves with the grid; a full-grid scan (160 x 64 raster) and a one-block scan (4 x 8
+    # probes: a grid of 16 CTAs, one split block) alternate on one plan, and every repeat equals the
+    # first run bitwise (a counter left non-zero would skip units)
+    g = grid_dict(64, 64, 8.0, 8.0, 2, 2.0, 2)
+    V = rand_v(2, 64, 64, 37)
+    xs, ys = np.meshgrid(np.arange(160) * 0.05, 0.5 + np.arange(64) * 0.11)
+    xb, yb = xs.ravel(), ys.ravel()
+    xs1, ys1 = np.meshgrid(1.0 + np.arange(4) * 0.25, 2.0 + np.arange(8) * 0.25)
+    xt, yt = xs1.ravel(), ys1.ravel()
+    probe = P.make_probe(20.0)
+    sim = PrismSimulation(P.make_grid(64, 64, 2, 8.0, 8.0, 2.0, 300.0, 2, 2, 0.5, 20.0, precision=prec))
+    sim.build(torch.from_numpy(V).cuda())
+    big = sim.scan(probe, xb, yb, det_c(DET), px=160, py=64).cpu().numpy()
+    small = sim.scan(probe, xt, yt, det_c(DET), px=4, py=8).cpu().numpy()
+    for _ in range(2):
+        assert np.array_equal(sim.scan(probe, xb, yb, det_c(DET), px=160, py=64).cpu().numpy(), big)
+        assert np.array_equal(sim.scan(probe, xt, yt, det_c(DET), px=4, py=8).cpu().numpy(), small)
+    assert np.all(np.isfinite(small)) and small.sum() > 0
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", [P.PRISM_PRECISION_FP32, P.PRISM_PRECISION_FP16, P.PRISM_PRECISION_FP16X2])
 def test_smatrix_checkpoint_resume(prec, tmp_path):
     # an S-matrix saved to a file and loaded into a fresh plan scans like the plan that built it:
