@@ -395,6 +395,7 @@ struct prism_plan {
     bool shared_sms = false;   // a batch runs this plan's kernels beside other cells' (see col_default_shape)
     bool wave_map_ok = false;
     int *dev_err = nullptr;    // device error word
+    int *col_ctr = nullptr;    // the TMA-staged column pass's tile counter and CTAs done (int[2])
     int tune_shape[2] = {-1, -1};  // autotuned launch shape of ROW_STD / COL_STD (-1: default launcher)
     double tune_ms[2][PRISM_TUNE_MAX_SHAPES];
     bool tuned[2] = {false, false};
@@ -671,6 +672,8 @@ extern "C" int prism_plan_create(const prism_grid *grid, size_t hbm_budget_bytes
     }
     if ((rc = A.alloc((void **)&P->dev_err, sizeof(int)))) return bail(rc);
     CUDA_TRY(cudaMemsetAsync(P->dev_err, 0, sizeof(int), P->stream));
+    if ((rc = A.alloc((void **)&P->col_ctr, 2 * sizeof(int)))) return bail(rc);
+    CUDA_TRY(cudaMemsetAsync(P->col_ctr, 0, 2 * sizeof(int), P->stream));
     if ((rc = A.alloc((void **)&P->wave, (size_t)batch * w_bytes))) return bail(rc);
     if ((rc = A.alloc((void **)&P->t0f, px * 8))) return bail(rc);
     if ((rc = A.alloc((void **)&P->zero_mn, 2 * sizeof(int)))) return bail(rc);
@@ -725,8 +728,9 @@ extern "C" int prism_sync(prism_plan *P) {
     CUDA_TRY(cudaMemcpy(&err, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         CUDA_TRY(cudaMemset(P->dev_err, 0, sizeof(int)));
-        // a scan whose wait ran out may have left split-block counters mid-count
+        // a scan or column pass whose wait ran out may have left its counters mid-count
         if (P->win_cnt) CUDA_TRY(cudaMemset(P->win_cnt, 0, P->cnt_cap));
+        CUDA_TRY(cudaMemset(P->col_ctr, 0, 2 * sizeof(int)));
         return fail(PRISM_ERR_DEVICE, "a kernel's bounded wait ran out (device error word " + std::to_string(err) + ")");
     }
     return PRISM_OK;
@@ -802,6 +806,7 @@ static void col_wave_map(const prism_plan *P, ColArgs &ca) {
     ca.out_map = P->out_map;
     ca.out_map4 = P->out_map4;
     ca.wave_map_ok = P->wave_map_ok ? 1 : 0;
+    ca.tile_ctr = P->col_ctr;
     ca.err = P->dev_err;
 }
 
@@ -1973,6 +1978,9 @@ extern "C" int prism_batch_sync(prism_batch *B) {
         CUDA_TRY(cudaMemcpy(&err, B->plans[i]->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (err) {
             CUDA_TRY(cudaMemset(B->plans[i]->dev_err, 0, sizeof(int)));
+            // a scan or column pass whose wait ran out may have left its counters mid-count
+            if (B->plans[i]->win_cnt) CUDA_TRY(cudaMemset(B->plans[i]->win_cnt, 0, B->plans[i]->cnt_cap));
+            CUDA_TRY(cudaMemset(B->plans[i]->col_ctr, 0, 2 * sizeof(int)));
             return fail(PRISM_ERR_DEVICE, "cell " + std::to_string(i) + ": a kernel's bounded wait ran out");
         }
     }

@@ -73,6 +73,9 @@ struct ColArgs {
                                // the column transforms may drop that band's complement at compile
                                // time (STD, DETECT)
     int wave_map_ok;           // 1: the four maps describe `wave` (the TMA-staged shapes may run)
+    int *tile_ctr;             // TMA-staged shapes: [2] the next tile and the CTAs done (zero between
+                               // launches; the launch that ends last zeroes them), or NULL: tiles by a
+                               // fixed stride
     int *err;                  // device error word: a TMA wait that ran out sets bit 1
     Tw64 tw;
 };

@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
     extern __shared__ __align__(128) float2 smem_c[];
     float2 *smem = smem_c;
     __shared__ __align__(8) uint64_t tbar;  // TMA staging: the tile's boxes have landed
+    __shared__ int s_next;                  // TMA staging with a tile counter: the next tile
     uint32_t tphase = 0;
     if constexpr (C::TMA) {
         if (threadIdx.x == 0) {
@@ -484,12 +485,25 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
             if constexpr (cls != BAND_OUT) pyr[r] = __ldg(a.prop_y + Fwd::out_elem(r, t));
         });
     }
-    if constexpr (MODE != COL_PROBE && C::STAGE) stage(blockIdx.x);
+    // TMA-staged shapes given a tile counter take their tiles from it, each one tile ahead (the
+    // tile the prefetch loads), instead of by a fixed stride: the CTAs sharing an SM are not issued
+    // equally, and with fixed shares the favoured ones finished early (per-CTA times of 170 to
+    // 204 us in one launch).  Which CTA transforms a tile changes no result.
+    const bool dyn = C::TMA && a.tile_ctr != nullptr;
+    int cur = blockIdx.x;
+    if (dyn) {
+        if (threadIdx.x == 0) s_next = atomicAdd(a.tile_ctr, 1);
+        __syncthreads();
+        cur = s_next;
+    }
+    if constexpr (MODE != COL_PROBE && C::STAGE) {
+        if (cur < ntiles) stage(cur);
+    }
     // without persistence every CTA owns exactly one tile and there is no loop (a loop would let
     // the compiler hoist the loop-invariant twiddle loads and hold them in registers)
     const int n_it = C::PERSIST || C::STAGE ? iters : 1;
-    for (int it = 0; it < n_it; ++it) {
-        const int tile = blockIdx.x + it * gridDim.x;
+    for (int it = 0; dyn ? cur < ntiles : it < n_it; ++it) {
+        const int tile = dyn ? cur : blockIdx.x + it * gridDim.x;
         const bool valid = tile < ntiles;
         int b, kx0;
         locate(tile, b, kx0);
@@ -545,7 +559,16 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
                 // before its writes here (no leading barrier), and the barrier after them is the
                 // point where every thread has read the staging buffer: its refill starts there
                 Fwd::template run<decltype(exF), C::TW_MODE, 0ull, false>(v, t, twf, a.tw, exF, [&] {
-                    if (it + 1 < iters) stage(tile + gridDim.x);
+                    if (dyn) {
+                        // the next tile, read by every thread after the inverse transform's barriers
+                        if (threadIdx.x == 0) {
+                            const int nt = atomicAdd(a.tile_ctr, 1);
+                            s_next = nt;
+                            if (nt < ntiles) stage(nt);
+                        }
+                    } else if (it + 1 < iters) {
+                        stage(tile + gridDim.x);
+                    }
                 });
             } else {
                 Fwd::template run<decltype(exF), C::TW_MODE>(v, t, twf, a.tw, exF);
@@ -605,9 +628,15 @@ __global__ void __launch_bounds__(ColCfg<NY, WC, STG, MB, TM>::THREADS, ColCfg<N
 #pragma unroll
             for (int r = 0; r < E; ++r) col[(size_t)Inv::out_elem(r, t) * a.nx] = v[r];
         }
+        if (dyn) cur = s_next;
     }
     if constexpr (C::TMA) {
         if (lane == 0) tc::bulk_wait_all();  // the last stores complete before the CTA leaves
+        // the last CTA to finish has seen every tile taken: it zeroes the counter for the next launch
+        if (dyn && threadIdx.x == 0 && atomicAdd(a.tile_ctr + 1, 1) == (int)gridDim.x - 1) {
+            a.tile_ctr[0] = 0;
+            a.tile_ctr[1] = 0;
+        }
     }
 }
 
