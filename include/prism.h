@@ -24,9 +24,12 @@
  *     results are valid after prism_sync() (or any later synchronisation of that stream).
  *   - Status: every int-returning call returns PRISM_OK (0) or a negative PRISM_ERR_* code;
  *     prism_last_error() then describes the failure (thread-local string).
- *   - Determinism: the same inputs give bitwise-identical outputs (no order-dependent
- *     atomics; fixed reduction trees), autotuned or not; only a plan tuned with the FFT radix
+ *   - Determinism: the same inputs give bitwise-identical outputs (fixed reduction trees; the
+ *     only atomics hand out work units -- rows, column tiles, probe blocks -- and which CTA
+ *     computes a unit changes no result), autotuned or not; only a plan tuned with the FFT radix
  *     variants (PRISM_AUTOTUNE_FFT_RADIX) may pick another rounding by timing.
+ *   - A plan's calls run on its stream, one after another: its scratch and its work-unit
+ *     counters are the plan's, so calls on one plan must not overlap (different plans may).
  *   - Memory: the caller owns every pointer it passes in; the plan owns the transmission
  *     functions, the S-matrix, its wave scratch and small tables, allocated with
  *     stream-ordered cudaMallocAsync and released by prism_plan_destroy().
