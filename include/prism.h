@@ -25,7 +25,7 @@
  *   - Status: every int-returning call returns PRISM_OK (0) or a negative PRISM_ERR_* code;
  *     prism_last_error() then describes the failure (thread-local string).
  *   - Determinism: the same inputs give bitwise-identical outputs (fixed reduction trees; the
- *     only atomics hand out work units -- rows, column tiles, probe blocks -- and which CTA
+ *     only atomics hand out work units -- column tiles, probe blocks -- and which CTA
  *     computes a unit changes no result), autotuned or not; only a plan tuned with the FFT radix
  *     variants (PRISM_AUTOTUNE_FFT_RADIX) may pick another rounding by timing.
  *   - A plan's calls run on its stream, one after another: its scratch and its work-unit
